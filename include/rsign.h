@@ -1,0 +1,174 @@
+/*
+ * rsign.h -- C ABI of the GB300 shifted matrix-sign reflector library.
+ *
+ * Problem (Sec. 2.1, Prop. 2.1): H is a real symmetric d x d matrix with
+ * ordered eigenvalues lam_1 <= ... <= lam_d and eigenvectors q_i; for a target
+ * index k in {1, ..., d-1} the prescribed-index reflector is
+ *     R_k = I - 2 P_k,   P_k = sum_{i<=k} q_i q_i^T          (Eq. Pk, Eq. Rk_intro)
+ * and for every shift s in (lam_k, lam_{k+1})
+ *     R_k = sign(H - s I).                                   (Prop. 2.1)
+ * The library computes sign(H - sI) with the scaled Newton-Schulz iteration
+ *     X_0 = alpha (H - s I),  X_{m+1} = 1/2 X_m (3 I - X_m^2)  (Eq. NS)
+ * with alpha <= 1/rho(H - sI) (Cor. 3.5), and certifies the result through
+ * trace(R) = d - 2k (the sign pattern of Prop. 2.1 / Lemma 3.4).
+ *
+ * Conventions for every call:
+ *   - matrices are dense, row-major, leading dimension d, IEEE binary64;
+ *   - a matrix pointer may address device memory or host memory (pageable
+ *     or pinned); host buffers are copied in and out on `stream` inside the
+ *     call.  The caller owns every buffer; the library never frees them;
+ *   - only the symmetric part 1/2 (H + H^T) of H is used; H is read-only;
+ *   - workspace is allocated inside the call (stream-ordered) and released
+ *     before it returns; no state survives a call;
+ *   - calls are blocking: they return once `info` (if given) is filled, since
+ *     the certificate is part of the result;
+ *   - errors are reported through the return value only: the library never
+ *     prints, never aborts, and leaves no sticky CUDA error behind for
+ *     argument errors; RSIGN_ERR_CUDA reports a failed CUDA call;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ */
+#ifndef RSIGN_H
+#define RSIGN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RSIGN_OK = 0,
+  RSIGN_ERR_ARG = 1,         /* invalid argument: d < 1, k outside [1, d-1], NULL, tol <= 0,
+                                non-finite entry in H, bad policy                        */
+  RSIGN_ERR_NOCONV = 2,      /* step budget exhausted before the tolerance was met        */
+  RSIGN_ERR_CERT = 3,        /* trace certificate failed: |trace R - (d - 2k)| >= 1/2,
+                                i.e. the shift is not in (lam_k, lam_{k+1}) or alpha*rho
+                                exceeded sqrt(3); R holds the iterate for diagnosis      */
+  RSIGN_ERR_GAP = 4,         /* automatic shift: target gap not resolved                  */
+  RSIGN_ERR_CUDA = 5,        /* a CUDA runtime call failed                                */
+  RSIGN_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up                        */
+  RSIGN_ERR_UNSUPPORTED = 7  /* device is not sm_103 or the size exceeds a limit          */
+} rsign_status;
+
+/* Precision policy of the Newton-Schulz steps. */
+typedef enum {
+  RSIGN_FP64 = 0,         /* every step in FP64 (native FP64 pipe)                       */
+  RSIGN_FP16 = 1,         /* FP16 operands, FP32 tensor accumulation, no FP64 stage:
+                             accuracy floor ~ u_fp16 ||H|| / gap                         */
+  RSIGN_BF16 = 2,         /* BF16 operands, FP32 tensor accumulation, no FP64 stage      */
+  RSIGN_FP16_POLISH = 3,  /* FP16 steps followed by `polish_steps` FP64 NS steps          */
+  RSIGN_BF16_POLISH = 4,  /* BF16 steps followed by `polish_steps` FP64 NS steps          */
+  RSIGN_FP16_REFINE = 5,  /* FP16 steps, then commutator refinement sweeps with
+                             FP64-grade products until the correction falls below tol   */
+  RSIGN_BF16_REFINE = 6   /* BF16 steps, then the same refinement                        */
+} rsign_policy;
+
+/* Scaling rule for alpha (Sec. 4.3 scaling discussion). */
+typedef enum {
+  RSIGN_ALPHA_INF = 0,    /* alpha = 1/||H - sI||_inf (Gershgorin bound on rho)          */
+  RSIGN_ALPHA_POWER = 1   /* alpha = 1/(1.02 rho_est), rho_est from power steps on H - sI
+                             followed by a Gershgorin-safe clamp                         */
+} rsign_alpha_mode;
+
+/* Per-call report, filled on the host when `info` is not NULL. */
+typedef struct {
+  int32_t steps_low;       /* Newton-Schulz steps in FP16/BF16                         */
+  int32_t steps_fp64;      /* Newton-Schulz steps in FP64 or FP64-grade arithmetic     */
+  int32_t sweeps_refine;   /* commutator refinement sweeps                             */
+  int32_t cert_ok;         /* 1 iff |trace - (d-2k)| < 1/2 and resid_fro <= tol_fro    */
+  double alpha;            /* scaling used, X_0 = alpha (H - sI)                       */
+  double shift;            /* shift s used                                             */
+  double gamma_est;        /* alpha * estimated margin min |lam_i - s| (auto shift) or
+                              NaN when the margin is not known                         */
+  double resid_fro;        /* ||R^2 - I||_F of the returned R                          */
+  double trace;            /* trace(R)                                                 */
+  double correction_fro;   /* ||last refinement correction||_F (REFINE policies)       */
+  double commutator_fro;   /* ||R A - A R||_F / ||A||_F at the last check (REFINE)     */
+  double tol_fro;          /* the residual threshold applied: max(tol, 16 d u_64)      */
+  double ms_total;         /* device time of the call, ms (CUDA events on `stream`)    */
+  double ms_low;           /* device time of the low-precision stage, ms               */
+  double ms_fp64;          /* device time of the FP64 / FP64-grade stages, ms          */
+  double flops_low;        /* algorithmic flops of the low-precision stage (2 d^3 per
+                              NS step: SYRK X^2 plus the symmetric product)           */
+  int64_t launches;        /* kernels this call launched                               */
+  int64_t workspace_bytes; /* device workspace the call allocated                      */
+} rsign_info;
+
+/* Optional knobs; rsign_options_default() fills the defaults. */
+typedef struct {
+  int32_t max_steps;        /* NS step budget per stage (default 100)                   */
+  int32_t polish_steps;     /* FP64 polish steps for *_POLISH policies (default 2)      */
+  int32_t max_sweeps;       /* refinement sweep budget (default 4)                      */
+  int32_t alpha_mode;       /* rsign_alpha_mode (default RSIGN_ALPHA_INF)               */
+  int32_t power_steps;      /* power steps for RSIGN_ALPHA_POWER (default 12)           */
+  int32_t timing;           /* 1: fill ms_* fields with CUDA events (default 1)        */
+} rsign_options;
+
+void rsign_options_default(rsign_options* opt);
+
+/*
+ * rsign_reflector -- R = sign(H - sI) = I - 2 P_k  (Prop. 2.1, Eq. NS).
+ *   H      d x d, symmetric part used; device or host memory.
+ *   d      matrix order, 2 <= d <= 16384.
+ *   k      target index, 1 <= k <= d-1 (Sec. 2.1); used by the trace certificate.
+ *   s      shift, expected in (lam_k, lam_{k+1}); the midpoint (Prop. 4.1) is the
+ *          recommended choice.  NaN requests an automatic midpoint shift from
+ *          Lanczos estimates of lam_k, lam_{k+1} (Sec. 4.3, Prop. 4.2).
+ *   tol    target: FP64 policy stops when ||X^2 - I||_F < max(tol, 16 d u_64);
+ *          REFINE policies stop when the refinement correction is below tol.
+ *   policy rsign_policy.
+ *   R      d x d output (device or host), fully written on RSIGN_OK and
+ *          RSIGN_ERR_CERT / RSIGN_ERR_NOCONV (last iterate).
+ *   info   optional report.
+ * Returns RSIGN_OK when the trace certificate holds and the tolerance was met.
+ */
+rsign_status rsign_reflector(const double* H, int64_t d, int32_t k, double s, double tol,
+                             rsign_policy policy, double* R, rsign_info* info, void* stream);
+
+/* Same as rsign_reflector with explicit options (NULL = defaults). */
+rsign_status rsign_reflector_ex(const double* H, int64_t d, int32_t k, double s, double tol,
+                                rsign_policy policy, const rsign_options* opt, double* R,
+                                rsign_info* info, void* stream);
+
+/*
+ * rsign_apply -- out = R V, the reflected directions d = -R g of Eq. discrete_step
+ * are -rsign_apply(R, g).  Prop. 3.3 bounds ||R~ g - R g|| by ||R~ - R||_2 ||g||.
+ *   R   d x d (row-major), V d x nv (row-major, ld nv), out d x nv (row-major).
+ *   FP64 arithmetic.  Device or host pointers.
+ */
+rsign_status rsign_apply(const double* R, int64_t d, const double* V, int64_t nv, double* out,
+                         void* stream);
+
+/*
+ * rsign_reflector_batched -- n independent reflectors R_i = sign(H_i - s_i I)
+ * (the batched regime of Sec. 4.5).  Arrays H, d, k, s, R, infos have n
+ * entries; H[i] and R[i] are d[i] x d[i].  s[i] = NaN requests the automatic
+ * shift for that matrix.  Returns the first non-OK status (all are attempted).
+ */
+rsign_status rsign_reflector_batched(int32_t n, const double* const* H, const int64_t* d,
+                                     const int32_t* k, const double* s, double tol,
+                                     rsign_policy policy, double* const* R, rsign_info* infos,
+                                     void* stream);
+
+/*
+ * rsign_reflector_backward -- adjoint of R = p_m(alpha (H - sI)) (Eq. NS
+ * unrolled) with s and alpha held fixed: given Rbar = dL/dR (d x d),
+ * returns Hbar = dL/dH (symmetrised, d x d).  The recurrence is run backward
+ * over checkpoints of the forward iterates taken every `ckpt_every` steps.
+ * The policy selects the arithmetic of the forward and backward steps.
+ */
+rsign_status rsign_reflector_backward(const double* H, int64_t d, int32_t k, double s,
+                                      rsign_policy policy, const double* Rbar, double* Hbar,
+                                      int32_t ckpt_every, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* rsign_status_str(rsign_status st);
+
+/* Library version string, e.g. "rsign 0.1 sm_103a". */
+const char* rsign_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSIGN_H */

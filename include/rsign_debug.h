@@ -1,0 +1,42 @@
+/*
+ * rsign_debug.h -- kernel-level entry points of librsign, for testing the
+ * individual GPU products against a reference.  They are not part of the
+ * reflector method itself; the paper has no counterpart of them.
+ *
+ * All pointers are device pointers; `stream` is a cudaStream_t as void*.
+ * The calls are asynchronous on `stream` and return RSIGN_ERR_CUDA when a
+ * launch fails, RSIGN_ERR_ARG for bad sizes.
+ */
+#ifndef RSIGN_DEBUG_H
+#define RSIGN_DEBUG_H
+
+#include <stdint.h>
+#include "rsign.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Tensor-core product on the tcgen05 path: out = A * B^T (FP32 accumulate),
+ * A, B dp x dp row-major FP16 (fmt 0) or BF16 (fmt 1), out dp x dp FP32.
+ * dp must be a multiple of 256.  sym = 1 computes only the tiles that meet
+ * the upper triangle and mirrors them (valid when A B^T is symmetric).
+ * `status` is a device int (initialised to 0 by the caller) that receives
+ * RSIGN_ERR_TIMEOUT if a bounded pipeline wait gave up.
+ */
+rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t fmt, int32_t sym,
+                               float* out, int* status, void* stream);
+
+/*
+ * FP64 product on the FP64 pipe: out = A * B, all dp x dp row-major FP64,
+ * dp a multiple of 64; sym = 1 as above.
+ */
+rsign_status rsign_dbg_f64_gemm(const double* A, const double* B, int64_t dp, int32_t sym,
+                                double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSIGN_DEBUG_H */

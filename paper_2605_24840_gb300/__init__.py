@@ -1,0 +1,313 @@
+"""Python binding of librsign, the GB300 shifted matrix-sign reflector library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``librsign.so`` (built from ``csrc/`` for sm_103a).  There is no
+CPU fallback; importing the binding without the built library raises.
+
+Tensors may be torch tensors (CUDA or CPU) or numpy arrays; float64,
+C-contiguous.  CUDA tensors are passed as device pointers on the current
+torch stream; host arrays are passed as host pointers and the library copies
+them in and out itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import math
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librsign.so")
+HEADERS = [os.path.join(_HERE, "..", "include", h) for h in ("rsign.h", "rsign_debug.h")]
+
+
+class Policy(enum.IntEnum):
+    FP64 = 0
+    FP16 = 1
+    BF16 = 2
+    FP16_POLISH = 3
+    BF16_POLISH = 4
+    FP16_REFINE = 5
+    BF16_REFINE = 6
+
+
+class Status(enum.IntEnum):
+    OK = 0
+    ERR_ARG = 1
+    ERR_NOCONV = 2
+    ERR_CERT = 3
+    ERR_GAP = 4
+    ERR_CUDA = 5
+    ERR_TIMEOUT = 6
+    ERR_UNSUPPORTED = 7
+
+
+class AlphaMode(enum.IntEnum):
+    INF = 0
+    POWER = 1
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("steps_low", ctypes.c_int32), ("steps_fp64", ctypes.c_int32),
+        ("sweeps_refine", ctypes.c_int32), ("cert_ok", ctypes.c_int32),
+        ("alpha", ctypes.c_double), ("shift", ctypes.c_double), ("gamma_est", ctypes.c_double),
+        ("resid_fro", ctypes.c_double), ("trace", ctypes.c_double),
+        ("correction_fro", ctypes.c_double), ("commutator_fro", ctypes.c_double),
+        ("tol_fro", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_low", ctypes.c_double),
+        ("ms_fp64", ctypes.c_double), ("flops_low", ctypes.c_double),
+        ("launches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("max_steps", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
+        ("max_sweeps", ctypes.c_int32), ("alpha_mode", ctypes.c_int32),
+        ("power_steps", ctypes.c_int32), ("timing", ctypes.c_int32),
+    ]
+
+
+class RsignError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = Status(status)
+        super().__init__("%s (%s)%s" % (self.status.name, status_str(status), (": " + msg) if msg else ""))
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of every function declared in include/*.h (the exported C ABI)."""
+    names = []
+    for h in HEADERS:
+        with open(h) as f:
+            txt = f.read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"\b(rsign_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def load():
+    """Load librsign.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("librsign.so not built: run __graft_entry__.build() (expected at %s)" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    dp, vp, i64, i32, dbl = (ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.c_int32, ctypes.c_double)
+    lib.rsign_options_default.argtypes = [ctypes.POINTER(Options)]
+    lib.rsign_options_default.restype = None
+    lib.rsign_reflector.argtypes = [vp, i64, i32, dbl, dbl, ctypes.c_int, vp, ctypes.POINTER(Info), vp]
+    lib.rsign_reflector.restype = ctypes.c_int
+    lib.rsign_reflector_ex.argtypes = [vp, i64, i32, dbl, dbl, ctypes.c_int, ctypes.POINTER(Options), vp,
+                                       ctypes.POINTER(Info), vp]
+    lib.rsign_reflector_ex.restype = ctypes.c_int
+    lib.rsign_apply.argtypes = [vp, i64, vp, i64, vp, vp]
+    lib.rsign_apply.restype = ctypes.c_int
+    lib.rsign_reflector_batched.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                            ctypes.POINTER(dbl), dbl, ctypes.c_int, ctypes.POINTER(vp),
+                                            ctypes.POINTER(Info), vp]
+    lib.rsign_reflector_batched.restype = ctypes.c_int
+    lib.rsign_reflector_backward.argtypes = [vp, i64, i32, dbl, ctypes.c_int, vp, vp, i32, vp]
+    lib.rsign_reflector_backward.restype = ctypes.c_int
+    lib.rsign_status_str.argtypes = [ctypes.c_int]
+    lib.rsign_status_str.restype = ctypes.c_char_p
+    lib.rsign_version.argtypes = []
+    lib.rsign_version.restype = ctypes.c_char_p
+    lib.rsign_dbg_tc_gemm.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp]
+    lib.rsign_dbg_tc_gemm.restype = ctypes.c_int
+    lib.rsign_dbg_f64_gemm.argtypes = [vp, vp, i64, i32, vp, vp]
+    lib.rsign_dbg_f64_gemm.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_str(code) -> str:
+    return load().rsign_status_str(int(code)).decode()
+
+
+def version() -> str:
+    return load().rsign_version().decode()
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().rsign_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+# ----------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr_of(x, name, shape=None, dtype="float64"):
+    """(pointer, keepalive, is_cuda) of a float64 C-contiguous array/tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.dtype(dtype) or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("%s must be a C-contiguous %s numpy array" % (name, dtype))
+        if shape is not None and tuple(x.shape) != tuple(shape):
+            raise ValueError("%s has shape %s, expected %s" % (name, x.shape, shape))
+        return x.ctypes.data, x, False
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        tdt = getattr(torch, dtype)
+        if x.dtype != tdt or not x.is_contiguous():
+            raise TypeError("%s must be a contiguous torch.%s tensor" % (name, dtype))
+        if shape is not None and tuple(x.shape) != tuple(shape):
+            raise ValueError("%s has shape %s, expected %s" % (name, tuple(x.shape), shape))
+        return x.data_ptr(), x, x.is_cuda
+    raise TypeError("%s: expected a numpy array or torch tensor" % name)
+
+
+def _stream_ptr(stream, any_cuda):
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    if any_cuda:
+        return int(_torch().cuda.current_stream().cuda_stream)
+    return 0
+
+
+def _like(x, shape):
+    if isinstance(x, np.ndarray):
+        return np.empty(shape, dtype=np.float64)
+    torch = _torch()
+    return torch.empty(shape, dtype=torch.float64, device=x.device)
+
+
+# ----------------------------------------------------------------------------
+# public calls (same names as the C ABI, without the prefix)
+# ----------------------------------------------------------------------------
+def reflector(H, k, s, tol=1e-12, policy=Policy.FP64, out=None, options=None, stream=None,
+              check=True):
+    """R = sign(H - sI) = I - 2 P_k via rsign_reflector_ex.  Returns (R, Info, Status).
+
+    With check=True a status other than OK raises RsignError (R and info are
+    attached to the exception as .R and .info).
+    """
+    lib = load()
+    d = int(H.shape[0])
+    hp, hk, hc = _ptr_of(H, "H", (d, d))
+    if out is None:
+        out = _like(H, (d, d))
+    rp, rk, rc = _ptr_of(out, "out", (d, d))
+    info = Info()
+    opt = options if options is not None else default_options()
+    st = lib.rsign_reflector_ex(hp, d, int(k), float("nan") if s is None else float(s), float(tol),
+                                int(policy), ctypes.byref(opt), rp, ctypes.byref(info),
+                                _stream_ptr(stream, hc or rc))
+    st = Status(st)
+    if check and st != Status.OK:
+        e = RsignError(st)
+        e.R, e.info = out, info
+        raise e
+    return out, info, st
+
+
+def apply(R, V, out=None, stream=None):
+    """out = R V (rsign_apply); V is d x nv."""
+    lib = load()
+    d = int(R.shape[0])
+    if V.ndim == 1:
+        V = V.reshape(d, 1)
+    nv = int(V.shape[1])
+    rp, rk, rc = _ptr_of(R, "R", (d, d))
+    vp, vk, vc = _ptr_of(V, "V", (d, nv))
+    if out is None:
+        out = _like(V, (d, nv))
+    op, ok, oc = _ptr_of(out, "out", (d, nv))
+    st = Status(lib.rsign_apply(rp, d, vp, nv, op, _stream_ptr(stream, rc or vc or oc)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return out
+
+
+def reflector_batched(Hs, ks, ss, tol=1e-12, policy=Policy.FP64, outs=None, stream=None):
+    """Independent reflectors for a list of matrices (rsign_reflector_batched)."""
+    lib = load()
+    n = len(Hs)
+    outs = outs if outs is not None else [_like(H, H.shape) for H in Hs]
+    keep = []
+    hp = (ctypes.c_void_p * n)()
+    rp = (ctypes.c_void_p * n)()
+    dd = (ctypes.c_int64 * n)()
+    kk = (ctypes.c_int32 * n)()
+    sv = (ctypes.c_double * n)()
+    any_cuda = False
+    for i, (H, R) in enumerate(zip(Hs, outs)):
+        d = int(H.shape[0])
+        p, kp, c1 = _ptr_of(H, "H[%d]" % i, (d, d))
+        q, kq, c2 = _ptr_of(R, "R[%d]" % i, (d, d))
+        keep += [kp, kq]
+        any_cuda |= c1 or c2
+        hp[i], rp[i], dd[i], kk[i] = p, q, d, int(ks[i])
+        sv[i] = float("nan") if ss[i] is None else float(ss[i])
+    infos = (Info * n)()
+    st = Status(lib.rsign_reflector_batched(n, hp, dd, kk, sv, float(tol), int(policy), rp, infos,
+                                            _stream_ptr(stream, any_cuda)))
+    return outs, list(infos), st
+
+
+def reflector_backward(H, k, s, Rbar, policy=Policy.FP64, ckpt_every=4, out=None, stream=None):
+    """Hbar = dL/dH given Rbar = dL/dR (rsign_reflector_backward)."""
+    lib = load()
+    d = int(H.shape[0])
+    hp, hk, hc = _ptr_of(H, "H", (d, d))
+    bp, bk, bc = _ptr_of(Rbar, "Rbar", (d, d))
+    if out is None:
+        out = _like(H, (d, d))
+    op, ok, oc = _ptr_of(out, "out", (d, d))
+    st = Status(lib.rsign_reflector_backward(hp, d, int(k), float(s), int(policy), bp, op, int(ckpt_every),
+                                             _stream_ptr(stream, hc or bc or oc)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return out
+
+
+# debug products (kernel-level tests)
+def dbg_tc_gemm(A, B, fmt=0, sym=0, out=None, stream=None):
+    """out = A B^T on the tcgen05 path (A, B: dp x dp CUDA fp16/bf16 tensors)."""
+    torch = _torch()
+    lib = load()
+    dp = int(A.shape[0])
+    if out is None:
+        out = torch.empty((dp, dp), dtype=torch.float32, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    st = Status(lib.rsign_dbg_tc_gemm(A.data_ptr(), B.data_ptr(), dp, int(fmt), int(sym), out.data_ptr(),
+                                      status.data_ptr(), _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return out, status
+
+
+def dbg_f64_gemm(A, B, sym=0, out=None, stream=None):
+    torch = _torch()
+    lib = load()
+    dp = int(A.shape[0])
+    if out is None:
+        out = torch.empty((dp, dp), dtype=torch.float64, device=A.device)
+    st = Status(lib.rsign_dbg_f64_gemm(A.data_ptr(), B.data_ptr(), dp, int(sym), out.data_ptr(),
+                                       _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return out
+
+
+def build(force=False, verbose=False):
+    """Compile librsign.so (sm_103a) in-tree."""
+    from . import buildlib
+    return buildlib.build(force=force, verbose=verbose)

@@ -1,0 +1,407 @@
+// f64_kernels.cu -- FP64 products (DMMA m8n8k4 on the FP64 pipe) and the
+// bandwidth-bound elementwise / reduction kernels of the reflector path.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rsign {
+namespace {
+
+// ------------------------------------------------------------------ FP64 GEMM
+// 64x64 output tile per 128-thread block (2x2 warps, 32x32 per warp as 4x4
+// fragments of m8n8), K step 16 staged through shared memory.
+constexpr int FT = 64, FK = 16, FPAD = 72;
+
+struct F64Sched {
+  int nb, sym, n;
+  __host__ __device__ F64Sched(int dp, int s) : nb(dp / FT), sym(s) {
+    n = s ? nb * (nb + 1) / 2 : nb * nb;
+  }
+  __device__ __forceinline__ void decode(int t, int& bi, int& bj) const {
+    if (!sym) { bi = t / nb; bj = t % nb; return; }
+    int b = 0;
+    for (;;) {
+      const int cnt = nb - b;
+      if (t < cnt) break;
+      t -= cnt;
+      ++b;
+    }
+    bi = b;
+    bj = b + t;
+  }
+};
+
+__device__ __forceinline__ void dmma(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) f64_gemm_kernel(const F64GemmArgs a) {
+  if (a.skip != nullptr && *a.skip != 0) return;
+  __shared__ double As[2][FK][FPAD];  // As[k][m]
+  __shared__ double Bs[2][FK][FPAD];  // Bs[k][n]
+  const F64Sched sched(a.dp, a.sym);
+  int bi, bj;
+  sched.decode(blockIdx.x, bi, bj);
+  const int m0 = bi * FT, n0 = bj * FT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int ld = a.dp;
+
+  double acc[4][4][2];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y][0] = acc[x][y][1] = 0.0;
+
+  // global -> register staging: A tile 64 rows x 16 k, B tile 16 k x 64 cols
+  double ra[8], rb[8];
+  auto gload = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * 128;          // 0..1023
+      const int am = e >> 4, ak = e & 15;   // A: row am, col k0+ak
+      ra[q] = a.A[(size_t)(m0 + am) * ld + k0 + ak];
+      const int bk = e >> 6, bn = e & 63;   // B: row k0+bk, col n0+bn
+      rb[q] = a.B[(size_t)(k0 + bk) * ld + n0 + bn];
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * 128;
+      As[buf][e & 15][e >> 4] = ra[q];
+      Bs[buf][e >> 6][e & 63] = rb[q];
+    }
+  };
+
+  const int nk = a.dp / FK;
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < nk) gload((kt + 1) * FK);
+#pragma unroll
+    for (int kk = 0; kk < FK; kk += 4) {
+      double af[4], bf[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) af[x] = As[buf][kk + (lane & 3)][wm * 32 + x * 8 + (lane >> 2)];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) bf[y] = Bs[buf][kk + (lane & 3)][wn * 32 + y * 8 + (lane >> 2)];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) dmma(acc[x][y][0], acc[x][y][1], af[x], bf[y]);
+    }
+    if (kt + 1 < nk) sstore(buf ^ 1);
+    __syncthreads();
+  }
+
+  // epilogue: thread holds rows (lane>>2) and columns 2*(lane&3)+{0,1} of each fragment
+  double part = 0.0;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int i = m0 + wm * 32 + x * 8 + (lane >> 2);
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = n0 + wn * 32 + y * 8 + 2 * (lane & 3) + h;
+        double v = acc[x][y][h];
+        if constexpr (EPI == F64_EPI_STORE) {
+          v *= a.scale;
+        } else if constexpr (EPI == F64_EPI_NS_SYRK) {
+          const bool real = i < a.d_real && j < a.d_real;
+          v = real ? ((i == j ? 1.0 : 0.0) - v) : 0.0;
+          if (real && (!a.sym || j >= i)) part += ((a.sym && j > i) ? 2.0 : 1.0) * v * v;
+        } else {  // F64_EPI_NS_UPDATE
+          v = a.xin[(size_t)i * ld + j] + 0.5 * v;
+          if (i == j && i < a.d_real) part += v;
+        }
+        if (!a.sym || j >= i) a.out[(size_t)i * ld + j] = v;
+        if (a.sym && j > i) a.out[(size_t)j * ld + i] = v;
+      }
+    }
+  }
+  if constexpr (EPI != F64_EPI_STORE) {
+    part = warp_sum(part);
+    if (lane == 0) a.partials[(size_t)blockIdx.x * 4 + warp] = part;
+  }
+}
+
+// ------------------------------------------------------------------ ingest
+// A = 1/2 (H + H^T) - s I (zero padded to dp), row partial sums of |A| per
+// 32-column block, non-finite detection.
+__global__ void ingest_kernel(const double* __restrict__ H, int d, int dp, double s,
+                              double* __restrict__ A, double* __restrict__ rowpart, int* flags) {
+  __shared__ double t1[32][33], t2[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;  // A tile (bi, bj): rows bi*32.., cols bj*32..
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  bool bad = false;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi * 32 + r, j = bj * 32 + tx;
+    double h1 = 0.0, h2 = 0.0;
+    if (i < d && j < d) h1 = H[(size_t)i * d + j];
+    const int i2 = bj * 32 + r, j2 = bi * 32 + tx;  // transposed tile
+    if (i2 < d && j2 < d) h2 = H[(size_t)i2 * d + j2];
+    if (!isfinite(h1) || !isfinite(h2)) bad = true;
+    t1[r][tx] = h1;
+    t2[r][tx] = h2;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi * 32 + r, j = bj * 32 + tx;
+    double v = 0.0;
+    if (i < d && j < d) v = 0.5 * (t1[r][tx] + t2[tx][r]) - (i == j ? s : 0.0);
+    A[(size_t)i * dp + j] = v;
+    t1[r][tx] = fabs(v);
+  }
+  if (bad) atomicOr(flags, 1);
+  __syncthreads();
+  // row partial sums over the 32 columns of this tile
+  if (ty == 0) {
+    double sum = 0.0;
+    for (int c = 0; c < 32; ++c) sum += t1[tx][c];
+    rowpart[(size_t)bj * dp + bi * 32 + tx] = sum;
+  }
+}
+
+__global__ void rowsum_kernel(const double* __restrict__ rowpart, int dp, double* rowsum) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= dp) return;
+  double s = 0.0;
+  const int nb = dp / 32;
+  for (int b = 0; b < nb; ++b) s += rowpart[(size_t)b * dp + i];
+  rowsum[i] = s;
+}
+
+__global__ void max_kernel(const double* __restrict__ x, int n, double* out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, x[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      out[0] = m;
+      out[1] = m > 0.0 ? 1.0 / m : 0.0;
+    }
+  }
+}
+
+// Deterministic single-block sum (fixed order: strided per thread, then tree).
+__global__ void sum_kernel(const double* __restrict__ x, int n, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) {
+      out[0] = s;
+      out[1] = sqrt(fmax(s, 0.0));
+    }
+  }
+}
+
+__global__ void ns_check_kernel(const double* __restrict__ x, int n, double* hist, int m, double tol_abs,
+                                double floor_lo, double floor_hi, double ratio, int* done, int* steps) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) {
+      const double r = sqrt(fmax(s, 0.0));
+      if (*done == 0) {  // after a stop the partials are stale: leave hist alone
+        hist[m] = r;
+        bool stop = r < tol_abs || r <= floor_lo;
+        if (!stop && m >= 1 && r <= floor_hi && r >= ratio * hist[m - 1]) stop = true;
+        if (stop) {
+          *done = 1;
+          *steps = m;
+        }
+      }
+    }
+  }
+}
+
+__global__ void trace_kernel(const double* __restrict__ X, int dp, int d, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) s += X[(size_t)i * dp + i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) out[0] = s;
+  }
+}
+
+template <typename T>
+__global__ void scale_convert_kernel(const double* __restrict__ src, size_t n, const double* scale_dev,
+                                     double mult, T* __restrict__ dst) {
+  const double sc = (scale_dev ? *scale_dev : 1.0) * mult;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = src[i] * sc;
+    if constexpr (sizeof(T) == 8) dst[i] = v;
+    else if constexpr (sizeof(T) == 4) dst[i] = (float)v;
+    else dst[i] = from_f64<T>(v);
+  }
+}
+
+template <typename T>
+__global__ void to_f64_kernel(const T* __restrict__ src, size_t n, double* __restrict__ dst) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 4) dst[i] = (double)src[i];
+    else dst[i] = (double)to_f32<T>(src[i]);
+  }
+}
+
+// y = A x, one warp per row.
+__global__ void gemv_kernel(const double* __restrict__ A, int dp, const double* __restrict__ x,
+                            double* __restrict__ y) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= dp) return;
+  double s = 0.0;
+  const double* a = A + (size_t)row * dp;
+  for (int j = lane; j < dp; j += 32) s += a[j] * x[j];
+  s = warp_sum(s);
+  if (lane == 0) y[row] = s;
+}
+
+__global__ void normalize_kernel(double* y, int n, double* x, double* nrm) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += y[i] * y[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) sh[0] = sqrt(s);
+  }
+  __syncthreads();
+  const double nr = sh[0];
+  if (threadIdx.x == 0) nrm[0] = nr;
+  const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i] * inv;
+}
+
+__global__ void copy_unpad_kernel(const double* __restrict__ src, int dp, double* __restrict__ dst, int d) {
+  const size_t n = (size_t)d * d;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / d, j = e % d;
+    dst[e] = src[i * dp + j];
+  }
+}
+
+int grid_for(size_t n) {
+  size_t g = (n + 255) / 256;
+  if (g > 8192) g = 8192;
+  return (int)(g ? g : 1);
+}
+
+}  // namespace
+
+int f64_num_tiles(int dp, int sym) { return F64Sched(dp, sym).n; }
+
+cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t st) {
+  if (a.dp % FT) return cudaErrorInvalidValue;
+  const int n = f64_num_tiles(a.dp, a.sym);
+  switch (a.epi) {
+    case F64_EPI_STORE: f64_gemm_kernel<F64_EPI_STORE><<<n, 128, 0, st>>>(a); break;
+    case F64_EPI_NS_SYRK: f64_gemm_kernel<F64_EPI_NS_SYRK><<<n, 128, 0, st>>>(a); break;
+    case F64_EPI_NS_UPDATE: f64_gemm_kernel<F64_EPI_NS_UPDATE><<<n, 128, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t ingest(const double* H, int d, int dp, double s, double* A, double* rowpart, int* flags,
+                   cudaStream_t st) {
+  dim3 grid(dp / 32, dp / 32), block(32, 8);
+  ingest_kernel<<<grid, block, 0, st>>>(H, d, dp, s, A, rowpart, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t inf_norm_finish(const double* rowpart, int dp, double* rowsum, double* scal, cudaStream_t st) {
+  rowsum_kernel<<<(dp + 255) / 256, 256, 0, st>>>(rowpart, dp, rowsum);
+  max_kernel<<<1, 1024, 0, st>>>(rowsum, dp, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_convert(const double* src, size_t n, const double* scale_dev, double mult, void* dst,
+                          int fmt, cudaStream_t st) {
+  const int g = grid_for(n);
+  switch (fmt) {
+    case 0: scale_convert_kernel<__half><<<g, 256, 0, st>>>(src, n, scale_dev, mult, (__half*)dst); break;
+    case 1: scale_convert_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(src, n, scale_dev, mult, (__nv_bfloat16*)dst); break;
+    case 2: scale_convert_kernel<double><<<g, 256, 0, st>>>(src, n, scale_dev, mult, (double*)dst); break;
+    case 3: scale_convert_kernel<float><<<g, 256, 0, st>>>(src, n, scale_dev, mult, (float*)dst); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t to_f64(const void* src, int fmt, size_t n, double* dst, cudaStream_t st) {
+  const int g = grid_for(n);
+  switch (fmt) {
+    case 0: to_f64_kernel<__half><<<g, 256, 0, st>>>((const __half*)src, n, dst); break;
+    case 1: to_f64_kernel<__nv_bfloat16><<<g, 256, 0, st>>>((const __nv_bfloat16*)src, n, dst); break;
+    case 3: to_f64_kernel<float><<<g, 256, 0, st>>>((const float*)src, n, dst); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_t st) {
+  sum_kernel<<<1, 1024, 0, st>>>(partials, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t ns_check(const double* partials, int n, double* hist, int m, double tol_abs, double floor_lo,
+                     double floor_hi, double ratio, int* done, int* steps, cudaStream_t st) {
+  ns_check_kernel<<<1, 1024, 0, st>>>(partials, n, hist, m, tol_abs, floor_lo, floor_hi, ratio, done, steps);
+  return cudaGetLastError();
+}
+
+cudaError_t trace_f64(const double* X, int dp, int d, double* out, cudaStream_t st) {
+  trace_kernel<<<1, 1024, 0, st>>>(X, dp, d, out);
+  return cudaGetLastError();
+}
+
+cudaError_t gemv_f64(const double* A, int dp, const double* x, double* y, cudaStream_t st) {
+  gemv_kernel<<<(dp + 7) / 8, 256, 0, st>>>(A, dp, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t normalize(double* y, int n, double* x, double* nrm, cudaStream_t st) {
+  normalize_kernel<<<1, 1024, 0, st>>>(y, n, x, nrm);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_unpad(const double* src, int dp, double* dst, int d, cudaStream_t st) {
+  copy_unpad_kernel<<<grid_for((size_t)d * d), 256, 0, st>>>(src, dp, dst, d);
+  return cudaGetLastError();
+}
+
+}  // namespace rsign

@@ -1,0 +1,452 @@
+// tc_gemm.cu -- persistent tcgen05 GEMM for the Newton-Schulz products.
+//
+// One CTA per SM (persistent, static round-robin over tiles), 6 warps:
+//   warp 0      TMA producer: 128x64 A and 256x64 B tiles (128B swizzle) into
+//               a 4-stage shared-memory ring, completion on mbarriers;
+//   warp 1      TMEM allocator and MMA issuer: tcgen05.mma kind::f16,
+//               M=128 N=256 K=16, FP32 accumulators in TMEM, two
+//               accumulators (512 columns) so the epilogue of one tile
+//               overlaps the main loop of the next;
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator (one TMEM lane
+//               quadrant per warp), fused elementwise work, global stores.
+// The symmetric schedule (`sym`) visits only tiles that meet the upper
+// triangle and mirrors each strictly-upper element, which halves the work
+// of X^2 (SYRK) and of the symmetric product X (I - X^2) of a Newton-Schulz
+// step (Eq. NS).
+#include "common.cuh"
+#include "kernels.h"
+
+#include <mutex>
+
+namespace rsign {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NUM_THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+struct TileSched {
+  int nbm, nbn, sym, n;
+  __device__ __host__ TileSched(int dp, int s) : nbm(dp / BM), nbn(dp / BN), sym(s) {
+    if (!s) {
+      n = nbm * nbn;
+    } else {
+      n = 0;
+      for (int bm = 0; bm < nbm; ++bm) n += nbn - bm / 2;
+    }
+  }
+  __device__ __forceinline__ void decode(int t, int& bm, int& bn) const {
+    if (!sym) {
+      bm = t / nbn;
+      bn = t % nbn;
+      return;
+    }
+    int b = 0;
+    for (;;) {
+      const int cnt = nbn - b / 2;
+      if (t < cnt) break;
+      t -= cnt;
+      ++b;
+    }
+    bm = b;
+    bn = b / 2 + t;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void store32_lp(T* dst, const float* v) {
+  // 32 consecutive elements, 64 bytes, 16-byte aligned
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      T lo = from_f32<T>(v[q * 8 + 2 * h]);
+      T hi = from_f32<T>(v[q * 8 + 2 * h + 1]);
+      w[h] = (uint32_t)(*reinterpret_cast<uint16_t*>(&lo)) |
+             ((uint32_t)(*reinterpret_cast<uint16_t*>(&hi)) << 16);
+    }
+    d4[q] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load32_lp(const T* src, float* v) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4 u = s4[q];
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      uint16_t lo = (uint16_t)(w[h] & 0xFFFFu), hi = (uint16_t)(w[h] >> 16);
+      v[q * 8 + 2 * h] = to_f32<T>(*reinterpret_cast<T*>(&lo));
+      v[q * 8 + 2 * h + 1] = to_f32<T>(*reinterpret_cast<T*>(&hi));
+    }
+  }
+}
+
+// Epilogue for one 32-column chunk held by one thread (row i, columns j0..j0+31).
+template <int EPI, typename T>
+__device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j0, int g,
+                                               float* v, bool above, double& acc1) {
+  const int ld = a.dp;
+  const size_t row = (size_t)i * ld;
+  if constexpr (EPI == TC_EPI_STORE_F32) {
+    float* out = reinterpret_cast<float*>(a.out);
+    if (!a.sym) {
+      float4* d4 = reinterpret_cast<float4*>(out + row + j0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        d4[q] = make_float4(v[4 * q] * a.scale, v[4 * q + 1] * a.scale, v[4 * q + 2] * a.scale,
+                            v[4 * q + 3] * a.scale);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = j0 + jj;
+        const float x = v[jj] * a.scale;
+        if (j >= i) out[row + j] = x;
+        if (j > i) out[(size_t)j * ld + i] = x;
+      }
+    }
+  } else if constexpr (EPI == TC_EPI_STORE_LP) {
+    T* out = reinterpret_cast<T*>(a.out);
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) v[jj] *= a.scale;
+    if (!a.sym || above) {
+      store32_lp<T>(out + row + j0, v);
+      if (a.sym) {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = j0 + jj;
+        const T x = from_f32<T>(v[jj]);
+        if (j >= i) out[row + j] = x;
+        if (j > i) out[(size_t)j * ld + i] = x;
+      }
+    }
+  } else if constexpr (EPI == TC_EPI_NS_SYRK) {
+    // E = I - X^2 restricted to the logical d x d block; residual ||X^2 - I||_F^2
+    T* out = reinterpret_cast<T*>(a.out);
+    const bool row_real = i < a.d_real;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = j0 + jj;
+      const bool real = row_real && (j < a.d_real);
+      const float e = real ? ((i == j ? 1.0f : 0.0f) - v[jj]) : 0.0f;
+      v[jj] = e;
+      if (real && j >= i) acc1 += (j > i ? 2.0 : 1.0) * (double)e * (double)e;
+    }
+    if (above) {
+      store32_lp<T>(out + row + j0, v);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = j0 + jj;
+        const T x = from_f32<T>(v[jj]);
+        if (j >= i) out[row + j] = x;
+        if (j > i) out[(size_t)j * ld + i] = x;
+      }
+    }
+  } else if constexpr (EPI == TC_EPI_NS_UPDATE) {
+    // X+ = X + 1/2 X (I - X^2); trace of the rounded iterate
+    T* out = reinterpret_cast<T*>(a.out);
+    const T* xin = reinterpret_cast<const T*>(a.xin);
+    float x[32];
+    load32_lp<T>(xin + row + j0, x);
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) v[jj] = x[jj] + 0.5f * v[jj];
+    if (above) {
+      store32_lp<T>(out + row + j0, v);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = j0 + jj;
+        const T xt = from_f32<T>(v[jj]);
+        if (j >= i) out[row + j] = xt;
+        if (j > i) out[(size_t)j * ld + i] = xt;
+        if (j == i && i < a.d_real) acc1 += (double)to_f32<T>(xt);
+      }
+    }
+  } else {  // TC_EPI_OZAKI
+    double* out = reinterpret_cast<double*>(a.out);
+    const double ri = a.rs[i] * a.group_scale[g];
+    const bool first = (g == 0);
+#pragma unroll 4
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = j0 + jj;
+      const double x = (double)v[jj] * ri * a.cs[j];
+      if (!a.sym || j >= i) {
+        double* p = out + row + j;
+        *p = first ? x : (*p + x);
+      }
+      if (a.sym && j > i) {
+        double* p = out + (size_t)j * ld + i;
+        *p = first ? x : (*p + x);
+      }
+    }
+  }
+}
+
+template <int EPI, typename T>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ TcGemmArgs args, const uint32_t idesc) {
+  if (args.skip != nullptr && *args.skip != 0) return;  // uniform across the grid
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;                 // [STAGES]
+  uint64_t* empty = bars + STAGES;       // [STAGES]
+  uint64_t* tfull = bars + 2 * STAGES;   // [2]
+  uint64_t* tempty = bars + 2 * STAGES + 2;  // [2]
+  uint64_t* drain = bars + 2 * STAGES + 4;   // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* status = args.status;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&tfull[s]), 1);
+      mbar_init(smem_u32(&tempty[s]), 128);
+    }
+    mbar_init(smem_u32(drain), 1);
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    prefetch_tensormap(&tmA);
+    prefetch_tensormap(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const TileSched sched(args.dp, args.sym);
+  const int n_kb = args.dp / BK;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < sched.n; t += gridDim.x) {
+        int bm, bn;
+        sched.decode(t, bm, bn);
+        for (int g = 0; ok && g < args.n_groups; ++g) {
+          for (int pi = args.group_start[g]; ok && pi < args.group_start[g + 1]; ++pi) {
+            for (int kb = 0; kb < n_kb; ++kb) {
+              if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, status)) { ok = false; break; }
+              const uint32_t fb = smem_u32(&full[stage]);
+              mbar_arrive_expect_tx(fb, STAGE_BYTES);
+              tma_load_3d(smem_u32(sA + stage * A_BYTES), &tmA, fb, kb * BK, bm * BM, args.pair_a[pi]);
+              tma_load_3d(smem_u32(sB + stage * B_BYTES), &tmB, fb, kb * BK, bn * BN, args.pair_b[pi]);
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+          }
+        }
+      }
+      // make sure no bulk copy is still writing shared memory when the CTA
+      // leaves: wait (bounded) for the last fill of every stage
+      for (int s = 0; s < STAGES; ++s) {
+        // the most recent fill of slot s used parity (phase ^ 1) if s >= stage, else phase
+        const uint32_t par = (s >= stage) ? (phase ^ 1u) : phase;
+        mbar_wait_drain(smem_u32(&full[s]), par);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ----------------------------------------------------------- MMA issue
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc_it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < sched.n; t += gridDim.x) {
+        for (int g = 0; ok && g < args.n_groups; ++g) {
+          const int acc = acc_it & 1;
+          const uint32_t aph = (acc_it >> 1) & 1;
+          if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u, status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+          uint32_t accumulate = 0;
+          for (int pi = args.group_start[g]; ok && pi < args.group_start[g + 1]; ++pi) {
+            for (int kb = 0; kb < n_kb; ++kb) {
+              if (!mbar_wait(smem_u32(&full[stage]), phase, status)) { ok = false; break; }
+              tc_fence_after();
+              const uint64_t ad = smem_desc_k128(smem_u32(sA + stage * A_BYTES));
+              const uint64_t bd = smem_desc_k128(smem_u32(sB + stage * B_BYTES));
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+                // advance 16 elements (32 bytes) along K inside the swizzle atom
+                tc_mma_f16(d_tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accumulate);
+                accumulate = 1;
+              }
+              tc_commit(smem_u32(&empty[stage]));
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+          }
+          if (ok) tc_commit(smem_u32(&tfull[acc]));
+          ++acc_it;
+        }
+      }
+      // retire every MMA issued by this thread before TMEM is released
+      tc_commit(smem_u32(drain));
+      mbar_wait_drain(smem_u32(drain), 0);
+    }
+  } else {
+    // -------------------------------------------------------------- epilogue
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;
+    int acc_it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; ok && t < sched.n; t += gridDim.x) {
+      int bm, bn;
+      sched.decode(t, bm, bn);
+      const int i = bm * BM + r;
+      double acc1 = 0.0;
+      for (int g = 0; g < args.n_groups; ++g) {
+        const int acc = acc_it & 1;
+        const uint32_t aph = (acc_it >> 1) & 1;
+        // one lane waits, the warp follows: the TMEM loads below are warp-collective
+        int got = 1;
+        if (lane == 0) got = mbar_wait(smem_u32(&tfull[acc]), aph, status) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        __syncwarp();
+        if (!got) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN);
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+          tmem_ld32(taddr + (uint32_t)(c * 32), v);
+          const int j0 = bn * BN + c * 32;
+          // chunk lies strictly above the diagonal for every row of this warp
+          const bool above = (j0 > bm * BM + BM - 1);
+          epilogue_chunk<EPI, T>(args, i, j0, g, v, above, acc1);
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&tempty[acc]));
+        ++acc_it;
+      }
+      if (!ok) break;
+      if constexpr (EPI == TC_EPI_NS_SYRK || EPI == TC_EPI_NS_UPDATE) {
+        const double s = warp_sum(acc1);
+        if (lane == 0) args.partials[(size_t)t * 4 + quad] = s;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* ptr, int dp, int slices, int box_rows, int lp_fmt) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)dp, (cuuint64_t)dp, (cuuint64_t)slices};
+  const cuuint64_t strides[2] = {(cuuint64_t)dp * 2, (cuuint64_t)dp * dp * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(m, lp_fmt ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                         3, const_cast<void*>(ptr), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int EPI, typename T>
+cudaError_t launch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
+                   uint32_t idesc, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<EPI, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  tc_gemm_kernel<EPI, T><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, a, idesc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
+                     uint32_t idesc, cudaStream_t st) {
+  switch (a.epi) {
+    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_OZAKI: return launch<TC_EPI_OZAKI, T>(a, ma, mb, grid, idesc, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+int tc_num_tiles(int dp, int sym) { return TileSched(dp, sym).n; }
+
+cudaError_t tc_gemm(const TcGemmArgs& args, const void* A, int a_slices, const void* B, int b_slices,
+                    int lp_fmt, int num_sms, cudaStream_t st) {
+  if (args.dp % BN != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
+      args.group_start[args.n_groups] > kTcMaxPairs)
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) || !make_map(&mb, B, args.dp, b_slices, BN, lp_fmt))
+    return cudaErrorInvalidValue;
+  const int n = tc_num_tiles(args.dp, args.sym);
+  const int grid = n < num_sms ? n : num_sms;
+  const uint32_t idesc = idesc_f16(lp_fmt ? 1u : 0u, BM, BN);
+  return lp_fmt ? dispatch<__nv_bfloat16>(args, ma, mb, grid, idesc, st)
+                : dispatch<__half>(args, ma, mb, grid, idesc, st);
+}
+
+}  // namespace rsign

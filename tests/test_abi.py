@@ -1,0 +1,99 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+function that include/*.h declares; host logic of the binding.  No GPU calls."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import paper_2605_24840_gb300 as rs
+    rs.build()
+    return rs
+
+
+def test_library_exports_every_header_function(rs):
+    names = rs.header_functions()
+    assert "rsign_reflector" in names and "rsign_apply" in names
+    assert "rsign_reflector_batched" in names and "rsign_reflector_backward" in names
+    lib = rs.load()
+    for n in names:
+        assert hasattr(lib, n), "librsign.so does not export %s" % n
+    # and nothing exported is undeclared (C symbols of the ABI)
+    out = subprocess.run(["nm", "-D", "--defined-only", rs.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (rsign_\w+)$", out, flags=re.M))
+    assert exported == set(names)
+
+
+def test_header_is_plain_c(tmp_path):
+    # the headers compile as C99 with no CUDA or torch types
+    src = tmp_path / "t.c"
+    src.write_text('#include "rsign.h"\n#include "rsign_debug.h"\nint main(void){rsign_options o;'
+                   'rsign_options_default(&o);return (int)sizeof(rsign_info);}\n')
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I",
+                        os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_struct_layouts_match_header(rs, tmp_path):
+    src = tmp_path / "s.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rsign.h"\nint main(void){'
+                   'printf("%zu %zu %zu %zu\\n", sizeof(rsign_info), offsetof(rsign_info, launches),'
+                   'sizeof(rsign_options), offsetof(rsign_info, ms_total));return 0;}\n')
+    exe = tmp_path / "s"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sz, off_l, osz, off_ms = map(int, subprocess.check_output([str(exe)]).split())
+    assert sz == ctypes.sizeof(rs.Info)
+    assert off_l == rs.Info.launches.offset
+    assert off_ms == rs.Info.ms_total.offset
+    assert osz == ctypes.sizeof(rs.Options)
+
+
+def test_status_strings_and_defaults(rs):
+    for st in rs.Status:
+        assert isinstance(rs.status_str(st), str) and rs.status_str(st)
+    o = rs.default_options()
+    assert o.max_steps == 100 and o.polish_steps == 2 and o.timing == 1
+    assert "sm_103a" in rs.version()
+
+
+def test_argument_errors_need_no_gpu(rs):
+    # validation happens before any device work, so these run on a CPU-only host
+    H = np.eye(4)
+    R = np.empty((4, 4))
+    lib = rs.load()
+    info = rs.Info()
+    bad = [
+        (H.ctypes.data, 4, 0, 0.0, 1e-12, 0),    # k < 1
+        (H.ctypes.data, 4, 4, 0.0, 1e-12, 0),    # k > d-1
+        (H.ctypes.data, 1, 1, 0.0, 1e-12, 0),    # d < 2
+        (H.ctypes.data, 4, 1, 0.0, -1.0, 0),     # tol <= 0
+        (H.ctypes.data, 4, 1, 0.0, 1e-12, 99),   # policy
+        (None, 4, 1, 0.0, 1e-12, 0),             # NULL H
+        (H.ctypes.data, 4, 1, float("inf"), 1e-12, 0),  # infinite shift
+    ]
+    for (hp, d, k, s, tol, pol) in bad:
+        st = lib.rsign_reflector(hp, d, k, s, tol, pol, R.ctypes.data, ctypes.byref(info), None)
+        assert st == rs.Status.ERR_ARG, (d, k, s, tol, pol, st)
+    assert lib.rsign_apply(None, 4, H.ctypes.data, 1, R.ctypes.data, None) == rs.Status.ERR_ARG
+
+
+def test_binding_rejects_wrong_dtype(rs):
+    with pytest.raises(TypeError):
+        rs.reflector(np.eye(4, dtype=np.float32), 1, 0.0)
+    with pytest.raises(ValueError):
+        rs.reflector(np.eye(4), 1, 0.0, out=np.empty((3, 3)))
+
+
+def test_missing_library_fails_loudly(rs, monkeypatch, tmp_path):
+    import paper_2605_24840_gb300 as pkg
+    monkeypatch.setattr(pkg, "_lib", None)
+    monkeypatch.setattr(pkg, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(ImportError):
+        pkg.load()

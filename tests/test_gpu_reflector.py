@@ -1,0 +1,153 @@
+"""GPU parity of rsign_reflector / rsign_apply against the CPU oracle.
+
+Each case runs the CUDA path through the C ABI on seeded inputs and compares
+with the oracle's definition R = I - 2 Q_k Q_k^T (Jacobi, or the eigenbasis
+known by construction) element by element / in the spectral norm.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import cuda_or_skip, lib_or_fail, spec_norm_sym
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(rs, torch, H, k, s, policy, tol=1e-12, **opt):
+    Hd = torch.from_numpy(np.ascontiguousarray(H)).cuda()
+    o = rs.default_options(**opt)
+    R, info, st = rs.reflector(Hd, k, s, tol=tol, policy=policy, options=o, check=False)
+    torch.cuda.synchronize()
+    return R.cpu().numpy(), info, st
+
+
+def test_plain_method_fp64_d256():
+    # d = 256, k = 4, midpoint shift, Gershgorin alpha, NS to 1e-12 / 80 steps
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.split_spectrum_config(seed=0)
+    s = oracle.midpoint(*spec.gap)
+    R_or, _ = oracle.reflector(spec.H, spec.k)
+    R, info, st = _run(rs, torch, spec.H, spec.k, s, rs.Policy.FP64, tol=1e-12, max_steps=80)
+    assert st == rs.Status.OK
+    assert spec_norm_sym(R - R_or) <= 1e-12
+    assert np.array_equal(R, R.T)
+    assert info.cert_ok == 1 and abs(info.trace - 248) < 1e-9
+    # iterate-level agreement with the oracle's naive loop: same stopping step
+    A = oracle.shifted(spec.H, s)
+    alpha = oracle.gershgorin_alpha(A)
+    assert info.alpha == pytest.approx(alpha, rel=1e-14)
+    X, steps, hist, conv = oracle.newton_schulz(alpha * A, 1e-12, 80)
+    assert info.steps_fp64 == steps
+    assert np.max(np.abs(R - X)) <= 1e-12
+
+
+@pytest.mark.parametrize("d,k", [(33, 1), (33, 32), (300, 7), (513, 256)])
+def test_fp64_ragged_sizes(d, k):
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.controlled_spectrum(d, k, 0.05, seed=100 + d + k)
+    R, info, st = _run(rs, torch, spec.H, k, 0.0, rs.Policy.FP64, tol=1e-12)
+    assert st == rs.Status.OK
+    R_ex = oracle.reflector_from_basis(spec.Q, k)
+    assert spec_norm_sym(R - R_ex) <= 1e-11
+    assert abs(info.trace - (d - 2 * k)) < 1e-8
+
+
+@pytest.mark.parametrize("policy,floor", [("FP16", 2e-2), ("BF16", 2e-1)])
+def test_low_precision_stage(policy, floor):
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 1024, 16
+    spec = workloads.controlled_spectrum(d, k, 0.1, seed=7)
+    R, info, st = _run(rs, torch, spec.H, k, 0.0, rs.Policy[policy])
+    R_ex = oracle.reflector_from_basis(spec.Q, k)
+    err = spec_norm_sym(R - R_ex)
+    assert st == rs.Status.OK, (st, info.as_dict())
+    assert info.steps_low > 5 and info.cert_ok == 1
+    assert abs(info.trace - (d - 2 * k)) < 0.5
+    assert err < floor, err
+
+
+def test_low_stage_then_fp64_polish():
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 768, 10
+    spec = workloads.controlled_spectrum(d, k, 0.1, seed=9)
+    R, info, st = _run(rs, torch, spec.H, k, 0.0, rs.Policy.FP16_POLISH, polish_steps=2)
+    assert st == rs.Status.OK
+    assert info.steps_fp64 == 2
+    R_ex = oracle.reflector_from_basis(spec.Q, k)
+    # the polish restores R^2 = I but keeps the low-precision subspace error
+    assert info.resid_fro < 1e-6
+    assert spec_norm_sym(R - R_ex) < 2e-2
+
+
+def test_host_pointers_roundtrip():
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.controlled_spectrum(64, 3, 0.2, seed=1)
+    R, info, st = rs.reflector(np.ascontiguousarray(spec.H), 3, 0.0, tol=1e-12, policy=rs.Policy.FP64)
+    assert isinstance(R, np.ndarray) and st == rs.Status.OK
+    assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, 3)) < 1e-12
+
+
+def test_shift_outside_gap_fails_certificate():
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.controlled_spectrum(128, 4, 0.1, seed=3)
+    lam = spec.lam
+    s_bad = 0.5 * (lam[5] + lam[6])  # admissible for k = 6, not for k = 4
+    R, info, st = _run(rs, torch, spec.H, 4, s_bad, rs.Policy.FP64)
+    assert st == rs.Status.ERR_CERT
+    assert abs(info.trace - (128 - 12)) < 1e-6
+
+
+def test_nonfinite_input_rejected():
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    H = np.eye(40)
+    H[3, 7] = np.nan
+    R, info, st = _run(rs, torch, H, 2, 0.0, rs.Policy.FP64)
+    assert st == rs.Status.ERR_ARG
+
+
+def test_diagonal_input_exact():
+    # Q = I: the reflector is diag(+-1) exactly (Prop. 2.1 proof)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    h = np.linspace(-1.0, 1.0, 50) + 0.01
+    k = int((h < 0).sum())
+    R, info, st = _run(rs, torch, np.diag(h), k, 0.0, rs.Policy.FP64, tol=1e-14)
+    assert st == rs.Status.OK
+    assert np.max(np.abs(R - np.diag(np.sign(h)))) < 1e-13
+
+
+@pytest.mark.parametrize("nv", [1, 3, 16])
+def test_apply_matches_numpy(nv):
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d = 777
+    rng = np.random.default_rng(nv)
+    Rm = rng.standard_normal((d, d))
+    V = rng.standard_normal((d, nv))
+    out = rs.apply(torch.from_numpy(Rm).cuda(), torch.from_numpy(V).cuda()).cpu().numpy()
+    assert np.max(np.abs(out - Rm @ V)) < 1e-11
+    out_h = rs.apply(Rm, V)  # host buffers
+    assert np.max(np.abs(out_h - Rm @ V)) < 1e-11
+
+
+def test_direction_error_bound():
+    # Prop. 3.3: ||R~ g - R g|| <= ||R~ - R||_2 ||g||
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.controlled_spectrum(256, 8, 0.1, seed=4)
+    R_lo, _, _ = _run(rs, torch, spec.H, 8, 0.0, rs.Policy.BF16)
+    R_ex = oracle.reflector_from_basis(spec.Q, 8)
+    g = np.random.default_rng(0).standard_normal(256)
+    dt = rs.apply(R_lo, g.reshape(-1, 1)).ravel()
+    de = R_ex @ g
+    assert np.linalg.norm(dt - de) <= spec_norm_sym(R_lo - R_ex) * np.linalg.norm(g) * (1 + 1e-12)
