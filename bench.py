@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 shifted matrix-sign reflector.
+
+Headline: milliseconds to R = sign(H - sI) = I - 2 P_k with ||R - R_exact||_2
+<= 1e-6 for a dense symmetric H of order d = 8192 (controlled spectrum, k = 16,
+half-gap delta = 1e-2, midpoint shift), FP16 tensor-core Newton-Schulz steps
+plus commutator refinement, compared with FP64 Newton-Schulz on the same GPU.
+
+One step = one rsign_reflector call on an H already resident in HBM (the
+whole hot path: ingest and scaling, low-precision steps, refinement, polish,
+certificate).  H is 512 MiB, larger than L2, so no flush is needed between
+steps.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rsign|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the single-matrix path does not shard); value = elapsed (max over ranks) /
+(K N).  --impl reference times the CPU oracle (naive FP64 Newton-Schulz,
+OpenMP over the host cores) on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms to sign(H−sI) at err≤1e-6, d=8192, mixed vs FP64 NS; tensor TFLOP/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="rsign", choices=["rsign", "reference"])
+    p.add_argument("--d", type=int, default=8192)
+    p.add_argument("--k", type=int, default=16)
+    p.add_argument("--delta", type=float, default=1e-2)
+    p.add_argument("--theta", type=float, default=0.5)
+    p.add_argument("--policy", default="FP16_REFINE")
+    p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 Newton-Schulz comparator")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device_id)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def smi_device_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def spectral_error(torch, R, Q, k, iters=200):
+    """||R - (I - 2 Q_k Q_k^T)||_2 (power iteration, a lower bound converging from below)
+    and the Frobenius norm (an upper bound)."""
+    D = R.clone()
+    D.diagonal().sub_(1.0)
+    Qk = Q[:, :k]
+    D.addmm_(Qk, Qk.T, alpha=2.0)
+    fro = float(torch.linalg.matrix_norm(D).item())
+    g = torch.Generator(device=D.device).manual_seed(0)
+    v = torch.randn(D.shape[0], 1, device=D.device, dtype=D.dtype, generator=g)
+    lam = 0.0
+    for _ in range(iters):
+        w = D @ v
+        n = float(torch.linalg.vector_norm(w).item())
+        if n == 0.0:
+            return 0.0, fro
+        lam = n / float(torch.linalg.vector_norm(v).item())
+        v = w / n
+    return lam, fro
+
+
+def cpu_oracle_sample(H_host, s, k, lam, seconds=15.0):
+    """Time the oracle's naive FP64 Newton-Schulz on a row sample of one step and
+    extrapolate to the full workload (all d rows, m* steps).  Returns a dict."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    A = oracle.shifted(H_host, s)
+    alpha = oracle.gershgorin_alpha(A)
+    X0 = np.ascontiguousarray(alpha * A)
+    del A
+    d = X0.shape[0]
+    gamma = alpha * float(np.min(np.abs(lam - s)))
+    steps = oracle.ns_steps(gamma, 1e-6, 10000)
+    rows = 4
+    t0 = time.perf_counter()
+    oracle.ns_step_rows(X0, 0, rows)
+    t1 = time.perf_counter() - t0
+    rows2 = int(max(rows, min(d, rows * seconds / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.ns_step_rows(X0, 0, rows2)
+    t2 = time.perf_counter() - t0
+    per_step = t2 * d / rows2
+    return {"value": per_step * steps * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "rows 0..%d of one naive FP64 Newton-Schulz step at d=%d (%.1f s), extrapolated x%d rows/"
+                      "sample x %d steps (scalar recurrence, gamma=%.3e, eps<=1e-6)" % (
+                          rows2, d, t2, d // max(rows2, 1), steps, gamma),
+            "sample_seconds": t2}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+
+    import workloads
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    H, lam, Q = workloads.controlled_spectrum_torch(args.d, args.k, args.delta,
+                                                    workloads.controlled_seed(args.d, 1, 1), device=dev)
+    lam_h = lam.cpu().numpy()
+    s = float(lam_h[args.k - 1] + args.theta * (lam_h[args.k] - lam_h[args.k - 1]))
+    H_host = H.cpu().numpy()
+    del H, Q
+    budget = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    vals, last = [], None
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(H_host, s, args.k, lam_h, seconds=budget)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            last = r
+    value = statistics.mean(vals)
+    cb = dict(last)
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": "controlled-spectrum dense symmetric H, d=%d, k=%d, delta=%g, shift at %.0f%% of the gap,"
+                        " %s to err<=%g" % (args.d, args.k, args.delta, 100 * args.theta, args.policy, args.tol),
+            "d": args.d, "k": args.k, "delta": args.delta, "theta": args.theta, "policy": args.policy,
+            "tol": args.tol, "alpha": "1/||H-sI||_inf", "parallelism": "replicas",
+            "l2": "inputs larger than L2 (H = 8 d^2 bytes)"}
+
+
+def run_rsign(args):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    import paper_2605_24840_gb300 as rs
+    import workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        tdist.init_process_group("nccl", device_id=dev)
+    rs.load()
+    policy = rs.Policy[args.policy]
+    seed = workloads.controlled_seed(args.d, 1, 1) + rank
+    H, lam, Q = workloads.controlled_spectrum_torch(args.d, args.k, args.delta, seed, device=dev)
+    lam_h = lam.cpu().numpy()
+    s = float(lam_h[args.k - 1] + args.theta * (lam_h[args.k] - lam_h[args.k - 1]))
+    R = torch.empty_like(H)
+    opt = rs.default_options()
+    stream = torch.cuda.current_stream(dev)
+
+    def call(Hin, Rout, pol=policy, tol=args.tol):
+        return rs.reflector(Hin, args.k, s, tol=tol, policy=pol, out=Rout, options=opt, check=False)
+
+    for _ in range(args.warmup):
+        _, info, st = call(H, R)
+        if st != rs.Status.OK:
+            raise SystemExit("warm-up call failed: %s %s" % (st.name, info.as_dict()))
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        tdist.barrier()
+    clocks = ClockSampler(smi_device_id(torch, dev))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, info, st = call(H, R)
+        infos.append((info, st))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = elapsed / (args.steps * ws)
+    info = infos[-1][0]
+    statuses = sorted({st.name for _, st in infos})
+
+    err2, errf = spectral_error(torch, R, Q, args.k)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the call
+    Hh = H.cpu().pin_memory()
+    Rh = torch.empty(Hh.shape, dtype=torch.float64).pin_memory()
+    Hn, Rn = Hh.numpy(), Rh.numpy()
+    e2e_t = []
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rs.reflector(Hn, args.k, s, tol=args.tol, policy=policy, out=Rn, options=opt, check=False)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_t.append((t1 - t0) * 1e3)
+    e2e_ms = statistics.mean(e2e_t) if e2e_t else None
+    nbytes = 8 * args.d * args.d
+
+    # roofline of the dominant kernel family: the tcgen05 Newton-Schulz GEMMs of
+    # the low-precision stage (algorithmic d^3 flops per launch: SYRK X^2 or the
+    # symmetric product X (I - X^2)); duration from the library's CUDA events
+    pk, pk_kind = peaks()
+    ms_low = statistics.mean(i.ms_low for i, _ in infos)
+    launches_low = 2 * info.steps_low + 1
+    avg_launch_ms = ms_low / launches_low
+    flops_per_launch = float(args.d) ** 3
+    achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
+    peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "tc_gemm_kernel (NS SYRK / symmetric update, FP16, 128x256 tiles)",
+            "peak_kind": "%s bf16 sustained (FP16 has the same nominal dense rate)" % pk_kind,
+            "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_ms}
+
+    fp64 = None
+    if not args.no_fp64:
+        R64 = torch.empty_like(H)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, i64, st64 = call(H, R64, pol=rs.Policy.FP64, tol=args.tol)
+        torch.cuda.synchronize(dev)
+        t64 = (time.perf_counter() - t0) * 1e3
+        e64, _ = spectral_error(torch, R64, Q, args.k)
+        fp64 = {"ms": i64.ms_total if i64.ms_total > 0 else t64, "status": st64.name, "steps": i64.steps_fp64,
+                "err_2": e64, "resid_fro": i64.resid_fro}
+        del R64
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_sample(H.cpu().numpy(), s, args.k, lam_h, seconds=15.0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f16+f64grade", "data": "synthetic",
+                "config": workload_config(args),
+                "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": int(sum(i.launches for i, _ in infos)),
+                "err_2": err2, "err_fro": errf, "status": statuses,
+                "tensor_tflops_low_stage": info.flops_low / (info.ms_low * 1e-3) / 1e12 if info.ms_low > 0 else None,
+                "fp64_ns": fp64,
+                "speedup_vs_fp64_ns": (fp64["ms"] / value) if fp64 else None,
+                "info": {k: v for k, v in info.as_dict().items()}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_rsign(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -83,7 +83,10 @@ typedef struct {
   double resid_fro;        /* ||R^2 - I||_F of the returned R                          */
   double trace;            /* trace(R)                                                 */
   double correction_fro;   /* ||last refinement correction||_F (REFINE policies)       */
-  double commutator_fro;   /* ||R A - A R||_F / ||A||_F at the last check (REFINE)     */
+  double commutator_fro;   /* ||R A - A R||_F, A = H - sI, at the last check (REFINE)  */
+  double err_est;          /* a-posteriori estimate of ||R - sign(H - sI)||_2 (REFINE):
+                              1.5 kappa ||alpha G||_2, G = 1/4 (R C + (R C)^T), kappa the
+                              gain of the last tangent solve; NaN for other policies   */
   double tol_fro;          /* the residual threshold applied: max(tol, 16 d u_64)      */
   double ms_total;         /* device time of the call, ms (CUDA events on `stream`)    */
   double ms_low;           /* device time of the low-precision stage, ms               */
@@ -102,6 +105,10 @@ typedef struct {
   int32_t alpha_mode;       /* rsign_alpha_mode (default RSIGN_ALPHA_INF)               */
   int32_t power_steps;      /* power steps for RSIGN_ALPHA_POWER (default 12)           */
   int32_t timing;           /* 1: fill ms_* fields with CUDA events (default 1)        */
+  int32_t low_split;        /* REFINE policies: 1 carries the low-precision iterates as
+                               hi/lo pairs (three fused pair products per step, about
+                               twice the mantissa bits, one refinement sweep usually
+                               suffices); 0 plain operands (default 1)                */
 } rsign_options;
 
 void rsign_options_default(rsign_options* opt);

@@ -35,6 +35,15 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
 rsign_status rsign_dbg_f64_gemm(const double* A, const double* B, int64_t dp, int32_t sym,
                                 double* out, void* stream);
 
+/*
+ * FP64-grade product on the FP16 tensor cores: out = A * B for symmetric
+ * FP64 A, B (dp x dp, dp a multiple of 256, rows/columns >= d_real zero),
+ * through 5-bit integer digit planes whose level sums are exact in FP32.
+ * Blocking: allocates and frees its own workspace, synchronises `stream`.
+ */
+rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t dp, int64_t d_real,
+                                      int32_t sym, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,7 @@ class Info(ctypes.Structure):
         ("alpha", ctypes.c_double), ("shift", ctypes.c_double), ("gamma_est", ctypes.c_double),
         ("resid_fro", ctypes.c_double), ("trace", ctypes.c_double),
         ("correction_fro", ctypes.c_double), ("commutator_fro", ctypes.c_double),
+        ("err_est", ctypes.c_double),
         ("tol_fro", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_low", ctypes.c_double),
         ("ms_fp64", ctypes.c_double), ("flops_low", ctypes.c_double),
         ("launches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
@@ -71,6 +72,7 @@ class Options(ctypes.Structure):
         ("max_steps", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
         ("max_sweeps", ctypes.c_int32), ("alpha_mode", ctypes.c_int32),
         ("power_steps", ctypes.c_int32), ("timing", ctypes.c_int32),
+        ("low_split", ctypes.c_int32),
     ]
 
 
@@ -127,6 +129,8 @@ def load():
     lib.rsign_dbg_tc_gemm.restype = ctypes.c_int
     lib.rsign_dbg_f64_gemm.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.rsign_dbg_f64_gemm.restype = ctypes.c_int
+    lib.rsign_dbg_fp64grade_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
+    lib.rsign_dbg_fp64grade_gemm.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -302,6 +306,20 @@ def dbg_f64_gemm(A, B, sym=0, out=None, stream=None):
         out = torch.empty((dp, dp), dtype=torch.float64, device=A.device)
     st = Status(lib.rsign_dbg_f64_gemm(A.data_ptr(), B.data_ptr(), dp, int(sym), out.data_ptr(),
                                        _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return out
+
+
+def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
+    """out = A B (FP64-grade, digit planes on the FP16 tensor cores); A, B symmetric CUDA float64."""
+    torch = _torch()
+    lib = load()
+    dp = int(A.shape[0])
+    if out is None:
+        out = torch.empty((dp, dp), dtype=torch.float64, device=A.device)
+    st = Status(lib.rsign_dbg_fp64grade_gemm(A.data_ptr(), B.data_ptr(), dp, int(d_real or dp), int(sym),
+                                             out.data_ptr(), _stream_ptr(stream, True)))
     if st != Status.OK:
         raise RsignError(st)
     return out

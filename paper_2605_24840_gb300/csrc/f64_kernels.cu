@@ -267,6 +267,24 @@ __global__ void scale_convert_kernel(const double* __restrict__ src, size_t n, c
 }
 
 template <typename T>
+__global__ void convert_split_kernel(const double* __restrict__ src, size_t n, const double* scale_dev,
+                                     T* __restrict__ dst) {
+  const double sc = scale_dev ? *scale_dev : 1.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = src[i] * sc;
+    const T hi = from_f64<T>(v);
+    dst[i] = hi;
+    dst[n + i] = from_f64<T>(v - (double)to_f32<T>(hi));
+  }
+}
+
+template <typename T>
+__global__ void split_to_f64_kernel(const T* __restrict__ src, size_t n, double* __restrict__ dst) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (double)to_f32<T>(src[i]) + (double)to_f32<T>(src[n + i]);
+}
+
+template <typename T>
 __global__ void to_f64_kernel(const T* __restrict__ src, size_t n, double* __restrict__ dst) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if constexpr (sizeof(T) == 4) dst[i] = (double)src[i];
@@ -370,6 +388,21 @@ cudaError_t to_f64(const void* src, int fmt, size_t n, double* dst, cudaStream_t
     case 3: to_f64_kernel<float><<<g, 256, 0, st>>>((const float*)src, n, dst); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t scale_convert_split(const double* src, size_t n, const double* scale_dev, void* dst, int fmt,
+                                cudaStream_t st) {
+  const int g = grid_for(n);
+  if (fmt == 0) convert_split_kernel<__half><<<g, 256, 0, st>>>(src, n, scale_dev, (__half*)dst);
+  else convert_split_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(src, n, scale_dev, (__nv_bfloat16*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t split_to_f64(const void* src, int fmt, size_t n, double* dst, cudaStream_t st) {
+  const int g = grid_for(n);
+  if (fmt == 0) split_to_f64_kernel<__half><<<g, 256, 0, st>>>((const __half*)src, n, dst);
+  else split_to_f64_kernel<__nv_bfloat16><<<g, 256, 0, st>>>((const __nv_bfloat16*)src, n, dst);
   return cudaGetLastError();
 }
 

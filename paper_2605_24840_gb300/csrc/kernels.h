@@ -43,6 +43,14 @@ struct TcGemmArgs {
   const double* cs;        // TC_EPI_OZAKI: per-row scale of the right operand
   int* status;             // device status word of the call
   const int* skip;         // optional: kernel returns at once when *skip != 0
+  int split;               // TC_EPI_NS_*: operands/outputs are hi/lo pairs of planes
+                           // (plane stride dp*dp); out = hi + lo carries ~2x the bits
+  // TC_EPI_OZAKI with diagonal-free digit planes: the first group adds the
+  // exact FP64 diagonal terms d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
+  const double* a_full;    // FP64 A (dp x dp), or nullptr
+  const double* b_full;    // FP64 B (dp x dp, symmetric)
+  const double* a_diag;
+  const double* b_diag;
 };
 
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
@@ -91,6 +99,11 @@ cudaError_t scale_convert(const double* src, size_t n, const double* scale_dev, 
                           void* dst, int dst_fmt /*0 f16, 1 bf16, 2 f64, 3 f32*/, cudaStream_t st);
 // dst(FP64) = src(fmt) converted.
 cudaError_t to_f64(const void* src, int src_fmt, size_t n, double* dst, cudaStream_t st);
+// Split FP64 into a hi/lo pair of FP16/BF16 planes (plane stride n):
+// hi = T(x s), lo = T(x s - hi), s = *scale_dev (or 1); and back: dst = hi + lo.
+cudaError_t scale_convert_split(const double* src, size_t n, const double* scale_dev, void* dst,
+                                int fmt, cudaStream_t st);
+cudaError_t split_to_f64(const void* src, int fmt, size_t n, double* dst, cudaStream_t st);
 // Deterministic sum of n partials -> out[0]; out[1] = sqrt(out[0]) when sqrt_out.
 cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_t st);
 // y = A x for dp x dp FP64 A (row-major), x,y length dp.
@@ -110,5 +123,70 @@ cudaError_t ns_check(const double* partials, int n, double* hist, int m, double 
 cudaError_t trace_f64(const double* X, int dp, int d, double* out, cudaStream_t st);
 // Power-iteration helpers: x <- y / ||y||_2, norm stored in *nrm.
 cudaError_t normalize(double* y, int n, double* x, double* nrm, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// FP64-grade products on the FP16 tensor cores (refine.cu).
+// A symmetric FP64 matrix M is split row by row into S digit planes:
+//   M_ik = sigma_i * sum_p d_p(i,k) 2^(-beta (p+1)) + O(sigma_i 2^(-beta S - 1)),
+//   sigma_i = 2^e_i >= 2 max_k |M_ik|, d_p integers in [-2^(beta-1), 2^(beta-1)],
+// stored exactly as FP16.  A product of two split matrices is a sum of digit
+// plane products grouped by level t = p + q; each group sum is an integer
+// bounded by (#pairs) 2^(2 beta - 2) K and is exact in the FP32 accumulator
+// while that bound stays <= 2^24.  The epilogue adds
+// sigma_i sigma_j 2^(-beta (t+2)) acc_t into an FP64 output.
+// ---------------------------------------------------------------------------
+constexpr int kSliceBeta = 5;   // bits per digit plane
+constexpr int kSlices = 7;      // digit planes per operand (35 bits)
+
+// The diagonal is kept out of the digit planes (rows are scaled by their
+// off-diagonal maximum, which is far below the diagonal for the reflector
+// and for diagonally heavy Hessians) and re-enters exactly in the epilogue.
+struct SplitMat {
+  void* planes;        // [kSlices][dp][dp] FP16 digits of M - diag(M)
+  double* sigma;       // [dp] row scales (powers of two)
+  double* diag;        // [dp] diag(M)
+  const double* full;  // the FP64 matrix itself (dp x dp), not owned
+};
+// Split the FP64 matrix M (dp x dp, symmetric) into digit planes; out.full = M.
+cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st);
+// out (FP64, dp x dp) = A * B for split symmetric A, B (K = d_real nonzeros);
+// sym = 1 when the product is symmetric (A == B): upper tiles + mirror.
+cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym,
+                       double* out, int* status, int num_sms, cudaStream_t st);
+
+// Elementwise kernels of the refinement sweep.  `scal` is a small device
+// array of scalars: each kernel documents the slots it reads and writes.
+// C = N - N^T (FP32), block maxima of |C| -> blockmax and FP64 sums of C^2
+// -> part (one each per 32x32 tile).
+cudaError_t antisym_part(const double* N, int dp, float* C, float* blockmax, double* part,
+                         cudaStream_t st);
+// out[0] = max of n floats; out[1] = 2^-ceil(log2 out[0]) (1 if out[0] == 0).
+cudaError_t max_pow2(const float* x, int n, float* out, cudaStream_t st);
+// dst (FP16/BF16) = src * scale[0]   (scale a device float)
+cudaError_t scale_to_lp(const float* src, size_t n, const float* scale, void* dst, int fmt,
+                        cudaStream_t st);
+// Direction of the Newton correction from the commutator product:
+// P = R C_lp^T (= -sigmaC R C); E0 = alpha * 1/4 (RC + (RC)^T) = -alpha/4 (P + P^T)/sigmaC,
+// written as FP32 with per-tile maxima.
+cudaError_t newton_direction(const float* P, int dp, const float* sigmaC, double alpha, float* E,
+                             float* blockmax, cudaStream_t st);
+// Tangent Newton-Schulz step (Frechet derivative of X + 1/2 X (I - X^2)):
+// E <- 1/2 E + 1/2 (P1 + P1^T)/sigma - 1/2 P2/sigma, P1 = E_lp Et, P2 = X E_lp X,
+// with per-tile maxima of the new E.
+cudaError_t tangent_combine(float* E, const float* P1, const float* P2, int dp, const float* sigma,
+                            float* blockmax, cudaStream_t st);
+// R += E (FP64 += FP32, masked to d) and per-block sums of E^2 -> part.
+cudaError_t add_correction(double* R, const float* E, int dp, int d, double* part, cudaStream_t st);
+// Et = I - Y (FP64 -> FP32, masked to d), per-tile maxima, per-tile sums of
+// (I - Y)^2 in FP64 -> part (one per 32x32 tile).
+cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockmax, double* part,
+                        cudaStream_t st);
+// Largest |eigenvalue| of a symmetric FP32 dp x dp matrix by `iters` power
+// steps (a lower bound that converges from below) -> *out (device double).
+// v, w: dp-float work vectors.
+cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
+                              cudaStream_t st);
+// R += 1/2 P / sigma (P FP32 symmetric product R_lp Et_lp).
+cudaError_t polish_update(double* R, const float* P, int dp, const float* sigma, cudaStream_t st);
 
 }  // namespace rsign

@@ -1,0 +1,376 @@
+// refine.cu -- FP64-grade products on the FP16 tensor cores and the
+// elementwise kernels of the commutator refinement.
+//
+// FP64-grade product: each operand row is written as a power-of-two scale
+// times a short sum of balanced 5-bit integer digits (error-free splitting in
+// the spirit of Ozaki, Ogita, Oishi and Rump's scheme, 2012).  Products of
+// digit planes are integers; grouped by level t = p + q they stay below 2^24
+// and therefore accumulate exactly in the FP32 TMEM accumulator of the
+// tcgen05 GEMM.  The only rounding is the FP64 sum over levels in the
+// epilogue and the truncation after kSlices digits (35 bits).
+#include "common.cuh"
+#include "kernels.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace rsign {
+namespace {
+
+constexpr int TILE = 32;
+
+// ------------------------------------------------------------ digit planes
+__global__ void split_rows_kernel(const double* __restrict__ M, int dp, __half* __restrict__ planes,
+                                  double* __restrict__ sigma, double* __restrict__ diag) {
+  __shared__ double sh[32];
+  __shared__ int e_sh;
+  const int i = blockIdx.x;
+  const double* row = M + (size_t)i * dp;
+  double m = 0.0;
+  for (int k = threadIdx.x; k < dp; k += blockDim.x)
+    if (k != i) m = fmax(m, fabs(row[k]));
+  if (threadIdx.x == 0) diag[i] = row[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, sh[w]);
+    int ex = 0;
+    if (mm > 0.0) {
+      frexp(mm, &ex);  // mm = f 2^ex, f in [0.5, 1): 2 mm < 2^(ex+1)
+      ex += 1;
+    }
+    e_sh = ex;
+    sigma[i] = ldexp(1.0, ex);
+  }
+  __syncthreads();
+  const int ex = e_sh;
+  const size_t plane = (size_t)dp * dp;
+  for (int k = threadIdx.x; k < dp; k += blockDim.x) {
+    double r = (k == i) ? 0.0 : ldexp(row[k], -ex);  // |r| < 1/2, exact; diagonal kept apart
+#pragma unroll
+    for (int p = 0; p < kSlices; ++p) {
+      const double t = ldexp(r, kSliceBeta);  // exact
+      const double dg = rint(t);             // |dg| <= 2^(beta-1)
+      r = t - dg;                            // exact, |r| <= 1/2
+      planes[p * plane + (size_t)i * dp + k] = __double2half(dg);
+    }
+  }
+}
+
+// ------------------------------------------------------- tiled elementwise
+__device__ __forceinline__ void tile_max(float v, float* blockmax) {
+  __shared__ float sm[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.y;  // blockDim = (32, 8): one warp per threadIdx.y
+  if (threadIdx.x == 0) sm[w] = v;
+  __syncthreads();
+  if (threadIdx.y == 0 && threadIdx.x == 0) {
+    float m = 0.f;
+    for (int q = 0; q < 8; ++q) m = fmaxf(m, sm[q]);
+    blockmax[blockIdx.y * gridDim.x + blockIdx.x] = m;
+  }
+}
+
+__global__ void antisym_kernel(const double* __restrict__ N, int dp, float* __restrict__ C,
+                               float* blockmax, double* part) {
+  __shared__ double t[TILE][TILE + 1];
+  __shared__ double sd[8];
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < TILE; r += 8) t[r][tx] = N[(size_t)(bj * TILE + r) * dp + bi * TILE + tx];
+  __syncthreads();
+  float m = 0.f;
+  double s2 = 0.0;
+  for (int r = ty; r < TILE; r += 8) {
+    const size_t e = (size_t)(bi * TILE + r) * dp + bj * TILE + tx;
+    const double cd = N[e] - t[tx][r];
+    const float c = (float)cd;
+    C[e] = c;
+    m = fmaxf(m, fabsf(c));
+    s2 += cd * cd;
+  }
+  s2 = warp_sum(s2);
+  if (tx == 0) sd[ty] = s2;
+  tile_max(m, blockmax);  // contains __syncthreads
+  if (tx == 0 && ty == 0) {
+    double tt = 0.0;
+    for (int q = 0; q < 8; ++q) tt += sd[q];
+    part[blockIdx.y * gridDim.x + blockIdx.x] = tt;
+  }
+}
+
+__global__ void newton_direction_kernel(const float* __restrict__ P, int dp, const float* sigmaC,
+                                        double alpha, float* __restrict__ E, float* blockmax) {
+  __shared__ float t[TILE][TILE + 1];
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < TILE; r += 8) t[r][tx] = P[(size_t)(bj * TILE + r) * dp + bi * TILE + tx];
+  __syncthreads();
+  const float f = (float)(-0.25 * alpha) / sigmaC[0];
+  float m = 0.f;
+  for (int r = ty; r < TILE; r += 8) {
+    const size_t e = (size_t)(bi * TILE + r) * dp + bj * TILE + tx;
+    const float v = f * (P[e] + t[tx][r]);
+    E[e] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  tile_max(m, blockmax);
+}
+
+__global__ void tangent_combine_kernel(float* __restrict__ E, const float* __restrict__ P1,
+                                       const float* __restrict__ P2, int dp, const float* sigma,
+                                       float* blockmax) {
+  __shared__ float t[TILE][TILE + 1];
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < TILE; r += 8) t[r][tx] = P1[(size_t)(bj * TILE + r) * dp + bi * TILE + tx];
+  __syncthreads();
+  const float inv = 0.5f / sigma[0];
+  float m = 0.f;
+  for (int r = ty; r < TILE; r += 8) {
+    const size_t e = (size_t)(bi * TILE + r) * dp + bj * TILE + tx;
+    const float v = 0.5f * E[e] + inv * (P1[e] + t[tx][r] - P2[e]);
+    E[e] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  tile_max(m, blockmax);
+}
+
+__global__ void ident_minus_kernel(const double* __restrict__ Y, int dp, int d, float* __restrict__ Et,
+                                   float* blockmax, double* part) {
+  __shared__ double sd[8];
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
+  float m = 0.f;
+  double s2 = 0.0;
+  for (int r = ty; r < TILE; r += 8) {
+    const int i = bi * TILE + r, j = bj * TILE + tx;
+    const size_t e = (size_t)i * dp + j;
+    const bool real = i < d && j < d;
+    const double v = real ? ((i == j ? 1.0 : 0.0) - Y[e]) : 0.0;
+    Et[e] = (float)v;
+    m = fmaxf(m, fabsf((float)v));
+    s2 += v * v;
+  }
+  s2 = warp_sum(s2);
+  if (tx == 0) sd[ty] = s2;
+  tile_max(m, blockmax);  // contains __syncthreads
+  if (tx == 0 && ty == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sd[q];
+    part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void max_pow2_kernel(const float* __restrict__ x, int n, float* out) {
+  __shared__ float sh[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, x[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, sh[w]);
+    int ex = 0;
+    if (mm > 0.f) frexpf(mm, &ex);  // mm = f 2^ex, f in [0.5, 1)
+    out[0] = mm;
+    out[1] = mm > 0.f ? ldexpf(1.f, -ex) : 1.f;  // mm * out[1] in [0.5, 1)
+  }
+}
+
+template <typename T>
+__global__ void scale_to_lp_kernel(const float* __restrict__ src, size_t n, const float* scale,
+                                   T* __restrict__ dst) {
+  const float s = scale[0];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = from_f32<T>(src[i] * s);
+}
+
+__global__ void add_correction_kernel(double* __restrict__ R, const float* __restrict__ E, int dp, int d,
+                                      double* part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  const size_t n = (size_t)dp * dp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double v = (double)E[e];
+    R[e] += v;
+    s += v * v;
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+__global__ void polish_update_kernel(double* __restrict__ R, const float* __restrict__ P, int dp,
+                                     const float* sigma) {
+  const double f = 0.5 / (double)sigma[0];
+  const size_t n = (size_t)dp * dp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    R[e] += f * (double)P[e];
+}
+
+// w = M v for a dp x dp FP32 matrix, one warp per row; v deterministic start
+// when init != 0 (v_i = 1 + (i mod 7)/8, a vector with components along every
+// eigenvector with probability one for the matrices met here).
+__global__ void gemv_f32_kernel(const float* __restrict__ M, int dp, const float* __restrict__ v,
+                                float* __restrict__ w, int init) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= dp) return;
+  const float* m = M + (size_t)row * dp;
+  double s = 0.0;
+  for (int j = lane; j < dp; j += 32) s += (double)m[j] * (init ? 1.0 + (j % 7) * 0.125 : (double)v[j]);
+  s = warp_sum(s);
+  if (lane == 0) w[row] = (float)s;
+}
+
+// v = w / ||w||; *out = ||w|| / ||v_prev|| (v_prev normalised except on the first pass)
+__global__ void power_normalize_kernel(const float* __restrict__ w, int n, float* __restrict__ v, double* out,
+                                       int first) {
+  __shared__ double sh[32];
+  double s = 0.0, s0 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    s += (double)w[i] * w[i];
+    if (first) {
+      const double v0 = 1.0 + (i % 7) * 0.125;
+      s0 += v0 * v0;
+    }
+  }
+  s = warp_sum(s);
+  s0 = warp_sum(s0);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double tot = 0.0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += sh[q];
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s0;
+  __syncthreads();
+  double tot0 = 0.0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot0 += sh[q];
+  const double nw = sqrt(tot);
+  const double inv = nw > 0.0 ? 1.0 / nw : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (float)(w[i] * inv);
+  if (threadIdx.x == 0) *out = first ? nw / sqrt(tot0) : nw;
+}
+
+dim3 tiles_of(int dp) { return dim3(dp / TILE, dp / TILE); }
+int grid_for(size_t n) {
+  size_t g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  return (int)(g ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st) {
+  split_rows_kernel<<<dp, 256, 0, st>>>(M, dp, (__half*)out.planes, out.sigma, out.diag);
+  return cudaGetLastError();
+}
+
+cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym, double* out,
+                       int* status, int num_sms, cudaStream_t st) {
+  TcGemmArgs a{};
+  a.dp = dp;
+  a.d_real = d_real;
+  a.sym = sym;
+  a.epi = TC_EPI_OZAKI;
+  a.scale = 1.0f;
+  a.out = out;
+  a.rs = A.sigma;
+  a.cs = B.sigma;
+  a.status = status;
+  a.skip = nullptr;
+  a.a_full = A.full;
+  a.b_full = B.full;
+  a.a_diag = A.diag;
+  a.b_diag = B.diag;
+  // |digit| <= 2^(beta-1): a group of n pairs sums to at most n 2^(2 beta - 2) K
+  const double bound1 = std::ldexp(1.0, 2 * kSliceBeta - 2) * (double)d_real;
+  const int max_pairs = std::max(1, (int)std::floor(std::ldexp(1.0, 24) / bound1));
+  int np = 0, ng = 0;
+  for (int t = 0; t < kSlices; ++t) {  // levels 0 .. kSlices-1 (truncation after 35 bits)
+    int in_group = 0;
+    for (int p = 0; p <= t; ++p) {
+      const int q = t - p;
+      if (p >= kSlices || q >= kSlices) continue;
+      if (in_group == 0) {
+        if (ng >= kTcMaxGroups) return cudaErrorInvalidValue;
+        a.group_start[ng] = np;
+        a.group_scale[ng] = std::ldexp(1.0, -kSliceBeta * (t + 2));
+        ++ng;
+      }
+      if (np >= kTcMaxPairs) return cudaErrorInvalidValue;
+      a.pair_a[np] = p;
+      a.pair_b[np] = q;
+      ++np;
+      if (++in_group == max_pairs) in_group = 0;
+    }
+  }
+  a.n_groups = ng;
+  a.group_start[ng] = np;
+  return tc_gemm(a, A.planes, kSlices, B.planes, kSlices, 0, num_sms, st);
+}
+
+cudaError_t antisym_part(const double* N, int dp, float* C, float* blockmax, double* part,
+                         cudaStream_t st) {
+  antisym_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(N, dp, C, blockmax, part);
+  return cudaGetLastError();
+}
+
+cudaError_t max_pow2(const float* x, int n, float* out, cudaStream_t st) {
+  max_pow2_kernel<<<1, 1024, 0, st>>>(x, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_to_lp(const float* src, size_t n, const float* scale, void* dst, int fmt, cudaStream_t st) {
+  if (fmt == 0) scale_to_lp_kernel<__half><<<grid_for(n), 256, 0, st>>>(src, n, scale, (__half*)dst);
+  else scale_to_lp_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, st>>>(src, n, scale, (__nv_bfloat16*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t newton_direction(const float* P, int dp, const float* sigmaC, double alpha, float* E,
+                             float* blockmax, cudaStream_t st) {
+  newton_direction_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(P, dp, sigmaC, alpha, E, blockmax);
+  return cudaGetLastError();
+}
+
+cudaError_t tangent_combine(float* E, const float* P1, const float* P2, int dp, const float* sigma,
+                            float* blockmax, cudaStream_t st) {
+  tangent_combine_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(E, P1, P2, dp, sigma, blockmax);
+  return cudaGetLastError();
+}
+
+cudaError_t add_correction(double* R, const float* E, int dp, int d, double* part, cudaStream_t st) {
+  (void)d;
+  add_correction_kernel<<<1024, 256, 0, st>>>(R, E, dp, d, part);
+  return cudaGetLastError();
+}
+
+cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockmax, double* part,
+                        cudaStream_t st) {
+  ident_minus_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(Y, dp, d, Et, blockmax, part);
+  return cudaGetLastError();
+}
+
+cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
+                              cudaStream_t st) {
+  for (int it = 0; it < iters; ++it) {
+    gemv_f32_kernel<<<(dp + 7) / 8, 256, 0, st>>>(M, dp, v, w, it == 0 ? 1 : 0);
+    power_normalize_kernel<<<1, 1024, 0, st>>>(w, dp, v, out, it == 0 ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t polish_update(double* R, const float* P, int dp, const float* sigma, cudaStream_t st) {
+  polish_update_kernel<<<grid_for((size_t)dp * dp), 256, 0, st>>>(R, P, dp, sigma);
+  return cudaGetLastError();
+}
+
+}  // namespace rsign

@@ -137,6 +137,171 @@ bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_ste
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Commutator refinement (beyond the paper's plain iteration; needed because
+// Newton-Schulz forgets A after X_0: an error that anticommutes with sign(A)
+// is a fixed point of the update, so low-precision subspace errors persist
+// through any number of FP64 steps).  With R ~ S = sign(A) an involution and
+// C = R A - A R, the off-block error F = S - R solves |A| F + F |A| = R C
+// (eigen-basis: F_ij = (RC)_ij / (|lam_i| + |lam_j|)), i.e. F = L_sign(A, G)
+// with G = 1/4 (R C + (R C)^T), the Frechet derivative of the sign function.
+// L_sign(A, G) is evaluated by the tangent recursion of Eq. NS along the
+// stored low-precision iterates:
+//   E_0 = alpha G,  E_{m+1} = 1/2 E_m + 1/2 (E_m Et_m + Et_m E_m) - 1/2 X_m E_m X_m,
+// (Et_m = I - X_m^2), then R <- R + E_M and one update-form polish step
+// R <- R + 1/2 R (I - R^2) restores R^2 = I.  N = R A and R^2 are FP64-grade
+// products; everything else is FP16/BF16 with FP32 accumulation.
+// ---------------------------------------------------------------------------
+struct RefineIn {
+  int dp, d, fmt, M, max_sweeps;
+  double alpha, tol;
+  double* A64;          // A = sym(H) - sI, FP64, zero padded
+  double* R64;          // in: stage-1 result; out: refined reflector
+  void* const* X;       // X_0 .. X_{M-1} (operand type)
+  void* const* Et;      // I - X_m^2, m = 0 .. M-1 (operand type)
+};
+struct RefineOut {
+  int sweeps = 0, polish_steps = 0;
+  bool converged = false;
+  double resid = NAN, corr = NAN, comm = NAN, err_est = NAN;
+};
+
+cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, RefineOut* o) {
+  const int dp = in.dp, d = in.d;
+  const size_t dd = (size_t)dp * dp;
+  const int ntile = (dp / 32) * (dp / 32);
+  cudaStream_t st = c.st;
+  SplitMat As{}, Rs{};
+  double *N64 = nullptr, *part = nullptr, *red = nullptr;
+  float *C32 = nullptr, *P32 = nullptr, *Q32 = nullptr, *E32 = nullptr, *bmax = nullptr, *fs = nullptr;
+  void *Clp = nullptr, *Rlp = nullptr, *Elp = nullptr, *Qlp = nullptr;
+  cudaError_t e;
+#define RS_TRY(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
+  RS_TRY(mem.alloc(&As.planes, dd * 2 * kSlices));
+  RS_TRY(mem.alloc((void**)&As.sigma, (size_t)dp * 8));
+  RS_TRY(mem.alloc((void**)&As.diag, (size_t)dp * 8));
+  RS_TRY(mem.alloc(&Rs.planes, dd * 2 * kSlices));
+  RS_TRY(mem.alloc((void**)&Rs.sigma, (size_t)dp * 8));
+  RS_TRY(mem.alloc((void**)&Rs.diag, (size_t)dp * 8));
+  As.full = in.A64;
+  Rs.full = in.R64;
+  RS_TRY(mem.alloc((void**)&N64, dd * 8));
+  RS_TRY(mem.alloc((void**)&C32, dd * 4));
+  RS_TRY(mem.alloc((void**)&P32, dd * 4));
+  RS_TRY(mem.alloc((void**)&Q32, dd * 4));
+  RS_TRY(mem.alloc((void**)&E32, dd * 4));
+  RS_TRY(mem.alloc(&Clp, dd * 2));
+  RS_TRY(mem.alloc(&Rlp, dd * 2));
+  RS_TRY(mem.alloc(&Elp, dd * 2));
+  RS_TRY(mem.alloc(&Qlp, dd * 2));
+  RS_TRY(mem.alloc((void**)&bmax, (size_t)ntile * 4));
+  RS_TRY(mem.alloc((void**)&part, (size_t)std::max(ntile, 1024) * 8));
+  RS_TRY(mem.alloc((void**)&fs, 16 * 4));
+  RS_TRY(mem.alloc((void**)&red, 16 * 8));
+  int* status = &ctl->status;
+
+  auto tc = [&](const void* A, const void* B, int fmt, int sym, int epi, void* out) {
+    TcGemmArgs a{};
+    a.dp = dp; a.d_real = d; a.sym = sym; a.epi = epi; a.n_groups = 1;
+    a.group_start[0] = 0; a.group_start[1] = 1; a.pair_a[0] = 0; a.pair_b[0] = 0;
+    a.group_scale[0] = 1.0; a.scale = 1.0f; a.out = out; a.status = status; a.skip = nullptr;
+    return tc_gemm(a, A, 1, B, 1, fmt, c.num_sms, st);
+  };
+  // one update-form polish step: R <- R + 1/2 R (I - R^2); residual -> red[0..1]
+  auto polish = [&]() -> cudaError_t {
+    cudaError_t r;
+    if (!c.ok(r = split_rows(in.R64, dp, Rs, st))) return r;
+    if (!c.ok(r = ozaki_gemm(Rs, Rs, dp, d, 1, N64, status, c.num_sms, st))) return r;
+    if (!c.ok(r = ident_minus(N64, dp, d, C32, bmax, part, st))) return r;
+    if (!c.ok(r = sum_partials(part, ntile, red + 0, st))) return r;
+    if (!c.ok(r = max_pow2(bmax, ntile, fs + 0, st))) return r;
+    if (!c.ok(r = scale_to_lp(C32, dd, fs + 1, Clp, 0, st))) return r;
+    if (!c.ok(r = scale_convert(in.R64, dd, nullptr, 1.0, Rlp, 0, st))) return r;
+    if (!c.ok(r = tc(Rlp, Clp, 0, 1, TC_EPI_STORE_F32, P32))) return r;
+    if (!c.ok(r = polish_update(in.R64, P32, dp, fs + 1, st))) return r;
+    o->polish_steps++;
+    return cudaSuccess;
+  };
+
+  RS_TRY(c.ok(split_rows(in.A64, dp, As, st)) ? cudaSuccess : c.err);
+  RS_TRY(polish());
+  double h_red[16];
+  if (in.M == 0) {
+    // X_0 was already at the low-precision floor (A a scaled near-involution):
+    // there is no trajectory to differentiate; the polish alone finishes R.
+    RS_TRY(polish());
+    RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
+    RS_TRY(cudaStreamSynchronize(st));
+    o->resid = h_red[1];
+    o->converged = h_red[1] <= in.tol;
+    return cudaSuccess;
+  }
+  // A-posteriori stop test.  The error of the current R is the correction the
+  // next sweep would add, F = L_sign(A, G).  Its 2-norm is estimated as
+  // kappa * ||alpha G||_2 with kappa = ||E||_2 / ||E_0||_2 measured on the
+  // previous tangent solve (the gain of L_sign on the error directions),
+  // times a safety factor of 1.5 (measured: the unscaled estimate exceeds the
+  // true error by 1.2x to 3x at errors of 1e-7 .. 1e-6).  The commutator that
+  // feeds the estimate is the first step of the next sweep, so a passed test
+  // costs one FP64-grade product and no tangent recursion.
+  float *pv = nullptr, *pw = nullptr;
+  RS_TRY(mem.alloc((void**)&pv, (size_t)dp * 4));
+  RS_TRY(mem.alloc((void**)&pw, (size_t)dp * 4));
+  constexpr int kPowerIters = 24;
+  double kappa = NAN;
+  for (int sw = 0; sw <= in.max_sweeps; ++sw) {
+    // commutator C = R A - A R from the FP64-grade product N = R A
+    if (!c.ok(split_rows(in.R64, dp, Rs, st))) return c.err;
+    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st))) return c.err;
+    if (!c.ok(antisym_part(N64, dp, C32, bmax, part, st))) return c.err;
+    if (!c.ok(sum_partials(part, ntile, red + 4, st))) return c.err;
+    if (!c.ok(max_pow2(bmax, ntile, fs + 2, st))) return c.err;
+    if (!c.ok(scale_to_lp(C32, dd, fs + 3, Clp, 0, st))) return c.err;
+    if (!c.ok(scale_convert(in.R64, dd, nullptr, 1.0, Rlp, 0, st))) return c.err;
+    // P = R C_lp^T = -sigma_C R C;  E_0 = alpha/4 (R C + (R C)^T)
+    if (!c.ok(tc(Rlp, Clp, 0, 0, TC_EPI_STORE_F32, P32))) return c.err;
+    if (!c.ok(newton_direction(P32, dp, fs + 3, in.alpha, E32, bmax, st))) return c.err;
+    if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return c.err;
+    if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 6, st))) return c.err;
+    c.launches += 2 * kPowerIters - 1;
+    RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
+    RS_TRY(cudaStreamSynchronize(st));
+    o->comm = h_red[5];
+    const double e0 = h_red[6];
+    if (sw >= 1) {
+      kappa = (h_red[8] > 0.0) ? h_red[7] / h_red[8] : 1.0;
+      o->err_est = 1.5 * kappa * e0;
+      if (!(e0 > 0.0) || o->err_est <= in.tol) {
+        o->converged = true;
+        break;
+      }
+    }
+    if (sw == in.max_sweeps) break;
+    RS_TRY(cudaMemcpyAsync(red + 8, red + 6, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // tangent recursion along the stored iterates
+    for (int m = 0; m < in.M; ++m) {
+      if (!c.ok(scale_to_lp(E32, dd, fs + 5, Elp, in.fmt, st))) return c.err;
+      if (!c.ok(tc(Elp, in.Et[m], in.fmt, 0, TC_EPI_STORE_F32, P32))) return c.err;   // E Et
+      if (!c.ok(tc(in.X[m], Elp, in.fmt, 0, TC_EPI_STORE_LP, Qlp))) return c.err;     // X E
+      if (!c.ok(tc(Qlp, in.X[m], in.fmt, 1, TC_EPI_STORE_F32, Q32))) return c.err;    // X E X
+      if (!c.ok(tangent_combine(E32, P32, Q32, dp, fs + 5, bmax, st))) return c.err;
+      if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return c.err;
+    }
+    if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 7, st))) return c.err;
+    c.launches += 2 * kPowerIters - 1;
+    if (!c.ok(add_correction(in.R64, E32, dp, d, part, st))) return c.err;
+    if (!c.ok(sum_partials(part, 1024, red + 2, st))) return c.err;
+    RS_TRY(polish());
+    RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
+    RS_TRY(cudaStreamSynchronize(st));
+    o->sweeps = sw + 1;
+    o->resid = h_red[1];
+    o->corr = h_red[3];
+  }
+#undef RS_TRY
+  return cudaSuccess;
+}
+
 rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, double tol,
                             rsign_policy policy, const rsign_options* opt_in, double* R,
                             rsign_info* info, cudaStream_t st) {
@@ -152,7 +317,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     return RSIGN_ERR_ARG;
   if (std::isinf(s)) return RSIGN_ERR_ARG;
   if (std::isnan(s)) return RSIGN_ERR_UNSUPPORTED;  // automatic shift: not in this build
-  if (policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE) return RSIGN_ERR_UNSUPPORTED;
+  const bool refine = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE;
 
   Ctx c;
   c.st = st;
@@ -171,7 +336,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   Ctl ctl_h;
   std::memset(&ctl_h, 0, sizeof(ctl_h));
-  int steps_low = 0, steps64 = 0;
+  int steps_low = 0, steps64 = 0, sweeps_done = 0;
+  double corr_fro = NAN, comm_fro = NAN, err_est = NAN;
   bool conv64 = true;
   double resid = NAN;
   std::vector<double> hist_h;
@@ -246,13 +412,41 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   if (is_low(policy)) {
     // ---------------------------------------------- low-precision stage (tcgen05)
     const int fmt = lp_fmt_of(policy);
-    void* xs[2] = {nullptr, nullptr};
-    void* es = nullptr;
-    if (mem.alloc(&xs[0], dd * 2) != cudaSuccess || mem.alloc(&xs[1], dd * 2) != cudaSuccess ||
-        mem.alloc(&es, dd * 2) != cudaSuccess)
-      return fail_cuda();
-    if (!c.ok(scale_convert(A64, dd, ctl->scal + 1, 1.0, xs[0], fmt, st))) return fail_cuda();
-    const double u = unit_roundoff(fmt);
+    // Iterates X_m and E_m = I - X_m^2: two ping-pong slots, or (refinement)
+    // one slot per step, kept for the tangent recursion.  For refinement the
+    // iterates are carried as hi/lo pairs of planes (X = X_hi + X_lo, about
+    // twice the bits of the operand type): every product is the fused sum of
+    // the pair products hi*hi + hi*lo + lo*hi, so the stored trajectory is an
+    // accurate one and its derivative (the tangent recursion) is accurate too.
+    const bool split = refine && opt.low_split != 0;
+    const int planes = split ? 2 : 1;
+    std::vector<void*> xs, es;
+    auto slot_x = [&](int m) -> void* {
+      const int idx = refine ? m : (m & 1);
+      while ((int)xs.size() <= idx) {
+        void* p = nullptr;
+        if (mem.alloc(&p, dd * 2 * planes) != cudaSuccess) return nullptr;
+        xs.push_back(p);
+      }
+      return xs[idx];
+    };
+    auto slot_e = [&](int m) -> void* {
+      const int idx = refine ? m : 0;
+      while ((int)es.size() <= idx) {
+        void* p = nullptr;
+        if (mem.alloc(&p, dd * 2 * planes) != cudaSuccess) return nullptr;
+        es.push_back(p);
+      }
+      return es[idx];
+    };
+    if (!slot_x(0)) return fail_cuda();
+    if (split) {
+      if (!c.ok(scale_convert_split(A64, dd, ctl->scal + 1, slot_x(0), fmt, st))) return fail_cuda();
+    } else {
+      if (!c.ok(scale_convert(A64, dd, ctl->scal + 1, 1.0, slot_x(0), fmt, st))) return fail_cuda();
+    }
+    // the split trajectory reaches a floor near u^2 (FP32 accumulation)
+    const double u = split ? 4.0 * unit_roundoff(fmt) * unit_roundoff(fmt) : unit_roundoff(fmt);
     const double floor_lo = 2.0 * u * std::sqrt((double)d);
     const double floor_hi = 16.0 * u * std::sqrt((double)d);
     const int nt = tc_num_tiles(dp, 1);
@@ -261,19 +455,30 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     while (m <= opt.max_steps && !stopped) {
       const int m_end = std::min(m + kChunk, opt.max_steps + 1);
       for (int mm = m; mm < m_end; ++mm) {
+        void* xm = slot_x(mm);
+        void* em = slot_e(mm);
+        void* xn = (mm < opt.max_steps) ? slot_x(mm + 1) : xm;
+        if (!xm || !em || !xn) return fail_cuda();
         TcGemmArgs sy{};
         sy.dp = dp; sy.d_real = d; sy.sym = 1; sy.epi = TC_EPI_NS_SYRK; sy.n_groups = 1;
-        sy.group_start[0] = 0; sy.group_start[1] = 1; sy.pair_a[0] = 0; sy.pair_b[0] = 0;
-        sy.group_scale[0] = 1.0; sy.scale = 1.0f; sy.out = es; sy.partials = partials;
+        sy.group_start[0] = 0; sy.pair_a[0] = 0; sy.pair_b[0] = 0;
+        if (split) {  // hi*hi + hi*lo + lo*hi in one accumulator
+          sy.pair_a[1] = 0; sy.pair_b[1] = 1; sy.pair_a[2] = 1; sy.pair_b[2] = 0;
+          sy.group_start[1] = 3;
+        } else {
+          sy.group_start[1] = 1;
+        }
+        sy.split = split ? 1 : 0;
+        sy.group_scale[0] = 1.0; sy.scale = 1.0f; sy.out = em; sy.partials = partials;
         sy.status = &ctl->status; sy.skip = &ctl->done_low;
-        if (!c.ok(tc_gemm(sy, xs[mm & 1], 1, xs[mm & 1], 1, fmt, c.num_sms, st))) return fail_cuda();
+        if (!c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st))) return fail_cuda();
         if (!c.ok(ns_check(partials, nt * 4, hist_low, mm, 0.0, floor_lo, floor_hi, 0.5, &ctl->done_low,
                            &ctl->steps_low, st)))
           return fail_cuda();
         if (mm == opt.max_steps) break;
         TcGemmArgs up = sy;
-        up.epi = TC_EPI_NS_UPDATE; up.out = xs[(mm + 1) & 1]; up.xin = xs[mm & 1];
-        if (!c.ok(tc_gemm(up, xs[mm & 1], 1, es, 1, fmt, c.num_sms, st))) return fail_cuda();
+        up.epi = TC_EPI_NS_UPDATE; up.out = xn; up.xin = xm;
+        if (!c.ok(tc_gemm(up, xm, planes, em, planes, fmt, c.num_sms, st))) return fail_cuda();
       }
       if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess)
@@ -283,7 +488,11 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       m = m_end;
     }
     steps_low = stopped ? ctl_h.steps_low : opt.max_steps;
-    if (!c.ok(to_f64(xs[steps_low & 1], fmt, dd, xb64[0], st))) return fail_cuda();
+    if (split) {
+      if (!c.ok(split_to_f64(slot_x(steps_low), fmt, dd, xb64[0], st))) return fail_cuda();
+    } else {
+      if (!c.ok(to_f64(slot_x(steps_low), fmt, dd, xb64[0], st))) return fail_cuda();
+    }
     Rfinal = xb64[0];
     hist_h.resize(opt.max_steps + 2);
     if (cudaMemcpyAsync(hist_h.data(), hist_low, hist_h.size() * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -291,10 +500,28 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       return fail_cuda();
     resid = hist_h[steps_low];
     if (!stopped && ctl_h.status == 0) result = RSIGN_ERR_NOCONV;
+    if (opt.timing) cudaEventRecord(ev[2], st);
+    if (refine && ctl_h.status == 0 && result == RSIGN_OK) {
+      // ------------------------------------------- commutator refinement sweeps
+      RefineIn in{};
+      in.dp = dp; in.d = d; in.fmt = fmt; in.M = steps_low; in.alpha = alpha; in.tol = tol;
+      in.A64 = A64; in.R64 = xb64[0]; in.X = xs.data(); in.Et = es.data();
+      in.max_sweeps = std::max(1, opt.max_sweeps);
+      RefineOut ro{};
+      const cudaError_t re = refine_sweeps(c, mem, in, ctl, &ro);
+      if (re != cudaSuccess) return fail_cuda();
+      sweeps_done = ro.sweeps;
+      steps64 = ro.polish_steps;
+      resid = ro.resid;
+      corr_fro = ro.corr;
+      comm_fro = ro.comm;
+      err_est = ro.err_est;
+      if (!ro.converged && result == RSIGN_OK) result = RSIGN_ERR_NOCONV;
+    }
   } else {
     if (!c.ok(scale_convert(A64, dd, ctl->scal + 1, 1.0, xb64[0], 2, st))) return fail_cuda();
+    if (opt.timing) cudaEventRecord(ev[2], st);
   }
-  if (opt.timing) cudaEventRecord(ev[2], st);
 
   if (need64 && ctl_h.status == 0) {
     // ------------------------------------------------------------- FP64 stage
@@ -334,15 +561,16 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     std::memset(info, 0, sizeof(*info));
     info->steps_low = steps_low;
     info->steps_fp64 = steps64;
-    info->sweeps_refine = 0;
+    info->sweeps_refine = sweeps_done;
     info->cert_ok = (trace_ok && resid_ok) ? 1 : 0;
     info->alpha = alpha;
     info->shift = s;
     info->gamma_est = NAN;
     info->resid_fro = resid;
     info->trace = trace;
-    info->correction_fro = NAN;
-    info->commutator_fro = NAN;
+    info->correction_fro = corr_fro;
+    info->commutator_fro = comm_fro;
+    info->err_est = err_est;
     info->tol_fro = tol_fro;
     if (opt.timing) {
       float t = 0.f;
@@ -401,6 +629,7 @@ void rsign_options_default(rsign_options* opt) {
   opt->alpha_mode = RSIGN_ALPHA_INF;
   opt->power_steps = 12;
   opt->timing = 1;
+  opt->low_split = 1;
 }
 
 rsign_status rsign_reflector_ex(const double* H, int64_t d, int32_t k, double s, double tol,
@@ -516,6 +745,43 @@ rsign_status rsign_dbg_f64_gemm(const double* A, const double* B, int64_t dp, in
   a.dp = (int)dp; a.d_real = (int)dp; a.sym = sym ? 1 : 0; a.epi = F64_EPI_STORE; a.scale = 1.0;
   a.A = A; a.B = B; a.out = out;
   return f64_gemm(a, (cudaStream_t)stream) == cudaSuccess ? RSIGN_OK : RSIGN_ERR_CUDA;
+}
+
+rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t dp, int64_t d_real,
+                                      int32_t sym, double* out, void* stream) {
+  if (!A || !B || !out || dp < 256 || dp % 256 || dp > 16384 || d_real < 1 || d_real > dp)
+    return RSIGN_ERR_ARG;
+  int sms = 0;
+  rsign_status ds = check_device(&sms);
+  if (ds != RSIGN_OK) return ds;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf mem;
+  mem.st = st;
+  const size_t dd = (size_t)dp * dp;
+  SplitMat sa{}, sb{};
+  int* status = nullptr;
+  rsign_status res = RSIGN_OK;
+  sa.full = A;
+  sb.full = B;
+  if (mem.alloc(&sa.planes, dd * 2 * kSlices) != cudaSuccess ||
+      mem.alloc((void**)&sa.sigma, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc((void**)&sa.diag, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc(&sb.planes, dd * 2 * kSlices) != cudaSuccess ||
+      mem.alloc((void**)&sb.sigma, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc((void**)&sb.diag, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc((void**)&status, 4) != cudaSuccess || cudaMemsetAsync(status, 0, 4, st) != cudaSuccess ||
+      split_rows(A, (int)dp, sa, st) != cudaSuccess || split_rows(B, (int)dp, sb, st) != cudaSuccess ||
+      ozaki_gemm(sa, sb, (int)dp, (int)d_real, sym ? 1 : 0, out, status, sms, st) != cudaSuccess)
+    res = RSIGN_ERR_CUDA;
+  int hs = 0;
+  if (res == RSIGN_OK && (cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                          cudaStreamSynchronize(st) != cudaSuccess))
+    res = RSIGN_ERR_CUDA;
+  if (res == RSIGN_OK && hs != 0) res = (rsign_status)hs;
+  mem.release();
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  cudaGetLastError();
+  return res;
 }
 
 }  // extern "C"

@@ -133,22 +133,60 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
         if (j > i) out[(size_t)j * ld + i] = x;
       }
     }
-  } else if constexpr (EPI == TC_EPI_NS_SYRK) {
-    // E = I - X^2 restricted to the logical d x d block; residual ||X^2 - I||_F^2
+  } else if constexpr (EPI == TC_EPI_NS_SYRK || EPI == TC_EPI_NS_UPDATE) {
+    // SYRK:   E  = I - X^2 restricted to the logical d x d block, with the
+    //         residual ||X^2 - I||_F^2 accumulated in acc1;
+    // UPDATE: X+ = X + 1/2 X (I - X^2), trace of the stored iterate in acc1.
+    // With a.split the value is stored as hi = T(v), lo = T(v - hi) in two
+    // planes (and X is read back as hi + lo).
     T* out = reinterpret_cast<T*>(a.out);
-    const bool row_real = i < a.d_real;
+    const size_t plane = (size_t)ld * ld;
+    if constexpr (EPI == TC_EPI_NS_SYRK) {
+      const bool row_real = i < a.d_real;
 #pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
-      const int j = j0 + jj;
-      const bool real = row_real && (j < a.d_real);
-      const float e = real ? ((i == j ? 1.0f : 0.0f) - v[jj]) : 0.0f;
-      v[jj] = e;
-      if (real && j >= i) acc1 += (j > i ? 2.0 : 1.0) * (double)e * (double)e;
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = j0 + jj;
+        const bool real = row_real && (j < a.d_real);
+        const float e = real ? ((i == j ? 1.0f : 0.0f) - v[jj]) : 0.0f;
+        v[jj] = e;
+        if (real && j >= i) acc1 += (j > i ? 2.0 : 1.0) * (double)e * (double)e;
+      }
+    } else {
+      const T* xin = reinterpret_cast<const T*>(a.xin);
+      float x[32];
+      load32_lp<T>(xin + row + j0, x);
+      if (a.split) {
+        float xl[32];
+        load32_lp<T>(xin + plane + row + j0, xl);
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) x[jj] += xl[jj];
+      }
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) v[jj] = x[jj] + 0.5f * v[jj];
+      if (i >= j0 && i < j0 + 32 && i < a.d_real) {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj)
+          if (j0 + jj == i) {
+            const T h = from_f32<T>(v[jj]);
+            acc1 += (double)to_f32<T>(h);
+            if (a.split) acc1 += (double)to_f32<T>(from_f32<T>(v[jj] - to_f32<T>(h)));
+          }
+      }
+    }
+    float lo[32];
+    if (a.split) {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) lo[jj] = v[jj] - to_f32<T>(from_f32<T>(v[jj]));
     }
     if (above) {
       store32_lp<T>(out + row + j0, v);
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
+      if (a.split) {
+        store32_lp<T>(out + plane + row + j0, lo);
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) out[plane + (size_t)(j0 + jj) * ld + i] = from_f32<T>(lo[jj]);
+      }
     } else {
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
@@ -156,38 +194,28 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
         const T x = from_f32<T>(v[jj]);
         if (j >= i) out[row + j] = x;
         if (j > i) out[(size_t)j * ld + i] = x;
-      }
-    }
-  } else if constexpr (EPI == TC_EPI_NS_UPDATE) {
-    // X+ = X + 1/2 X (I - X^2); trace of the rounded iterate
-    T* out = reinterpret_cast<T*>(a.out);
-    const T* xin = reinterpret_cast<const T*>(a.xin);
-    float x[32];
-    load32_lp<T>(xin + row + j0, x);
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) v[jj] = x[jj] + 0.5f * v[jj];
-    if (above) {
-      store32_lp<T>(out + row + j0, v);
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
-    } else {
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const int j = j0 + jj;
-        const T xt = from_f32<T>(v[jj]);
-        if (j >= i) out[row + j] = xt;
-        if (j > i) out[(size_t)j * ld + i] = xt;
-        if (j == i && i < a.d_real) acc1 += (double)to_f32<T>(xt);
+        if (a.split) {
+          const T y = from_f32<T>(lo[jj]);
+          if (j >= i) out[plane + row + j] = y;
+          if (j > i) out[plane + (size_t)j * ld + i] = y;
+        }
       }
     }
   } else {  // TC_EPI_OZAKI
     double* out = reinterpret_cast<double*>(a.out);
     const double ri = a.rs[i] * a.group_scale[g];
     const bool first = (g == 0);
+    const bool with_diag = first && a.a_full != nullptr;
+    const double dai = with_diag ? a.a_diag[i] : 0.0;
 #pragma unroll 4
     for (int jj = 0; jj < 32; ++jj) {
       const int j = j0 + jj;
-      const double x = (double)v[jj] * ri * a.cs[j];
+      double x = (double)v[jj] * ri * a.cs[j];
+      if (with_diag) {
+        // exact diagonal terms: d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
+        const double dbj = a.b_diag[j];
+        x += dai * a.b_full[row + j] + a.a_full[row + j] * dbj - (i == j ? dai * dbj : 0.0);
+      }
       if (!a.sym || j >= i) {
         double* p = out + row + j;
         *p = first ? x : (*p + x);

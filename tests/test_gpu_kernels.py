@@ -66,3 +66,31 @@ def test_f64_gemm_matches_torch(dp, sym):
     ref = A @ B
     torch.cuda.synchronize()
     assert (out - ref).abs().max().item() <= 1e-13 * dp
+
+
+@pytest.mark.parametrize("dp,d_real,sym", [(256, 256, 0), (512, 300, 1), (1024, 1024, 0), (2048, 2048, 1)])
+def test_fp64grade_product_matches_fp64(dp, d_real, sym):
+    # digit-plane product on the FP16 tensor cores vs an FP64 matmul
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    g = torch.Generator(device="cuda").manual_seed(dp + d_real)
+    A = torch.zeros((dp, dp), device="cuda", dtype=torch.float64)
+    B = torch.zeros((dp, dp), device="cuda", dtype=torch.float64)
+    a = torch.randn((d_real, d_real), generator=g, device="cuda", dtype=torch.float64)
+    A[:d_real, :d_real] = 0.5 * (a + a.T) * torch.logspace(-3, 0, d_real, device="cuda", dtype=torch.float64)
+    A = 0.5 * (A + A.T)
+    if sym:
+        B = A
+    else:
+        b = torch.randn((d_real, d_real), generator=g, device="cuda", dtype=torch.float64)
+        B[:d_real, :d_real] = 0.5 * (b + b.T)
+    out = rs.dbg_fp64grade_gemm(A, B, d_real=d_real, sym=sym)
+    ref = A @ B
+    torch.cuda.synchronize()
+    # 35 bits per operand relative to the row maxima, exact integer accumulation
+    rmax = A.abs().amax(dim=1, keepdim=True)
+    cmax = B.abs().amax(dim=1, keepdim=True).T
+    bound = 1e-9 * (d_real ** 0.5) * rmax * cmax + 1e-13 * (A.abs() @ B.abs())
+    assert ((out - ref).abs() - bound).max().item() <= 0.0
+    if sym:
+        assert (out - out.T).abs().max().item() == 0.0

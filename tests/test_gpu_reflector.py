@@ -151,3 +151,32 @@ def test_direction_error_bound():
     dt = rs.apply(R_lo, g.reshape(-1, 1)).ravel()
     de = R_ex @ g
     assert np.linalg.norm(dt - de) <= spec_norm_sym(R_lo - R_ex) * np.linalg.norm(g) * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("policy", ["FP16_REFINE", "BF16_REFINE"])
+@pytest.mark.parametrize("d,k,delta", [(1024, 16, 1e-2), (768, 384, 1e-2), (300, 5, 1e-1)])
+def test_refine_reaches_1e6(policy, d, k, delta):
+    # low-precision steps + commutator refinement: ||R - R_exact||_2 <= 1e-6
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.controlled_spectrum(d, k, delta, seed=40 + d + k)
+    R, info, st = _run(rs, torch, spec.H, k, 0.0, rs.Policy[policy], tol=1e-6)
+    R_ex = oracle.reflector_from_basis(spec.Q, k)
+    err = spec_norm_sym(R - R_ex)
+    assert st == rs.Status.OK, (st, info.as_dict())
+    assert info.sweeps_refine >= 1 and info.cert_ok == 1
+    assert abs(info.trace - (d - 2 * k)) < 1e-6
+    assert err <= 1e-6, (err, info.as_dict())
+    assert info.resid_fro < 1e-5
+
+
+@pytest.mark.parametrize("theta", [0.1, 0.9])
+def test_refine_off_midpoint_shift_same_reflector(theta):
+    # Prop. 2.1 on the GPU path: shifts inside the gap give the same R
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.controlled_spectrum(512, 12, 5e-2, seed=77)
+    s = workloads.shift_in_gap(spec, theta)
+    R, info, st = _run(rs, torch, spec.H, 12, s, rs.Policy.FP16_REFINE, tol=1e-7)
+    assert st == rs.Status.OK
+    assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, 12)) <= 1e-7

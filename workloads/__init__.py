@@ -173,3 +173,28 @@ def batched_sizes(count: int = 512, d_choices=tuple(range(32, 513, 32)), k_max: 
     k = rng.integers(1, k_max + 1, size=count)
     logd = rng.uniform(math.log(delta_range[0]), math.log(delta_range[1]), size=count)
     return [(int(d[i]), int(min(k[i], d[i] - 1)), float(math.exp(logd[i]))) for i in range(count)]
+
+
+def controlled_spectrum_torch(d: int, k: int, delta: float, seed: int, device="cuda"):
+    """Same recipe as ``controlled_spectrum`` built with torch on ``device``.
+
+    Used where the numpy construction is too slow (d in the thousands on the
+    host).  The random stream is torch's, so the matrix differs from the numpy
+    one with the same seed; the spectrum distribution and the structure are
+    the same.  Returns (H, lam, Q) as float64 tensors on ``device``.
+    """
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    G = torch.randn((d, d), generator=g, device=device, dtype=torch.float64)
+    Q, Rf = torch.linalg.qr(G)
+    sgn = torch.sign(torch.diagonal(Rf))
+    sgn[sgn == 0] = 1.0
+    Q = Q * sgn
+    del G, Rf
+    lo = -(delta + (1.0 - delta) * torch.rand(k - 1, generator=g, device=device, dtype=torch.float64))
+    hi = delta + (1.0 - delta) * torch.rand(d - k - 1, generator=g, device=device, dtype=torch.float64)
+    pin = torch.tensor([-delta, delta], device=device, dtype=torch.float64)
+    lam, _ = torch.sort(torch.cat([lo, pin, hi]))
+    H = (Q * lam) @ Q.T
+    H = 0.5 * (H + H.T)
+    return H.contiguous(), lam, Q
