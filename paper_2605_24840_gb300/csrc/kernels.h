@@ -35,6 +35,8 @@ struct TcGemmArgs {
   int pair_a[kTcMaxPairs];
   int pair_b[kTcMaxPairs];
   double group_scale[kTcMaxGroups];
+  int group_shift[kTcMaxGroups];  // TC_EPI_OZAKI: group weight 2^shift in the int64 sum
+  double final_scale;             // TC_EPI_OZAKI: weight of one unit of that sum
   float scale;
   void* out;
   const void* xin;         // TC_EPI_NS_UPDATE: current iterate (operand type)

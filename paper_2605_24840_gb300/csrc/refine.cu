@@ -48,14 +48,19 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int dp, __half* 
   __syncthreads();
   const int ex = e_sh;
   const size_t plane = (size_t)dp * dp;
+  // r = M_ik 2^-ex in (-1/2, 1/2) as a fixed-point integer with 62 fraction
+  // bits (one exact FP64 scaling and one conversion); the balanced base-2^beta
+  // digits are then peeled off with integer shifts: the FP64 pipe of this GPU
+  // is far slower than its integer pipe.
+  const double to_fixed = ldexp(1.0, 62 - ex);
   for (int k = threadIdx.x; k < dp; k += blockDim.x) {
-    double r = (k == i) ? 0.0 : ldexp(row[k], -ex);  // |r| < 1/2, exact; diagonal kept apart
+    long long n = (k == i) ? 0ll : __double2ll_rn(row[k] * to_fixed);  // diagonal kept apart
 #pragma unroll
     for (int p = 0; p < kSlices; ++p) {
-      const double t = ldexp(r, kSliceBeta);  // exact
-      const double dg = rint(t);             // |dg| <= 2^(beta-1)
-      r = t - dg;                            // exact, |r| <= 1/2
-      planes[p * plane + (size_t)i * dp + k] = __double2half(dg);
+      const int sh = 62 - kSliceBeta * (p + 1);                // weight of digit p: 2^sh
+      const long long dg = (n + (1ll << (sh - 1))) >> sh;      // nearest, |dg| <= 2^(beta-1)
+      n -= dg * (1ll << sh);                                   // |n| <= 2^(sh-1)
+      planes[p * plane + (size_t)i * dp + k] = __int2half_rn((int)dg);
     }
   }
 }
@@ -225,10 +230,15 @@ __global__ void gemv_f32_kernel(const float* __restrict__ M, int dp, const float
   const int lane = threadIdx.x & 31;
   if (row >= dp) return;
   const float* m = M + (size_t)row * dp;
-  double s = 0.0;
-  for (int j = lane; j < dp; j += 32) s += (double)m[j] * (init ? 1.0 + (j % 7) * 0.125 : (double)v[j]);
-  s = warp_sum(s);
-  if (lane == 0) w[row] = (float)s;
+  float s = 0.f;  // FP32: a norm estimate needs no more, and the FP64 pipe is slow here
+  if (init) {
+    for (int j = lane; j < dp; j += 32) s += m[j] * (1.0f + (float)(j % 7) * 0.125f);
+  } else {
+    for (int j = lane; j < dp; j += 32) s += m[j] * v[j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) w[row] = s;
 }
 
 // v = w / ||w||; *out = ||w|| / ||v_prev|| (v_prev normalised except on the first pass)
@@ -304,6 +314,9 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
         if (ng >= kTcMaxGroups) return cudaErrorInvalidValue;
         a.group_start[ng] = np;
         a.group_scale[ng] = std::ldexp(1.0, -kSliceBeta * (t + 2));
+        // integer weight relative to the deepest level kSlices-1: the int64
+        // sum stays below 2^(24 + beta (kSlices-1) + 2) < 2^63
+        a.group_shift[ng] = kSliceBeta * (kSlices - 1 - t);
         ++ng;
       }
       if (np >= kTcMaxPairs) return cudaErrorInvalidValue;
@@ -315,6 +328,7 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
   }
   a.n_groups = ng;
   a.group_start[ng] = np;
+  a.final_scale = std::ldexp(1.0, -kSliceBeta * (kSlices - 1 + 2));
   return tc_gemm(a, A.planes, kSlices, B.planes, kSlices, 0, num_sms, st);
 }
 

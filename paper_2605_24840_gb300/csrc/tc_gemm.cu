@@ -202,28 +202,40 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
       }
     }
   } else {  // TC_EPI_OZAKI
+    // The group sums are exact integers (< 2^24).  They are combined as one
+    // int64 fixed-point value V = sum_g acc_g 2^(group_shift[g]) kept in the
+    // output buffer between groups; the last group converts V to FP64 once,
+    // applies the row/column scales and adds the exact diagonal terms.
     double* out = reinterpret_cast<double*>(a.out);
-    const double ri = a.rs[i] * a.group_scale[g];
+    long long* outi = reinterpret_cast<long long*>(a.out);
     const bool first = (g == 0);
-    const bool with_diag = first && a.a_full != nullptr;
+    const bool last = (g == a.n_groups - 1);
+    const int shift = a.group_shift[g];
+    const bool with_diag = last && a.a_full != nullptr;
+    const double ri = last ? a.rs[i] * a.final_scale : 0.0;
     const double dai = with_diag ? a.a_diag[i] : 0.0;
 #pragma unroll 4
     for (int jj = 0; jj < 32; ++jj) {
       const int j = j0 + jj;
-      double x = (double)v[jj] * ri * a.cs[j];
+      const bool direct = !a.sym || j >= i;
+      const bool mirror = a.sym && j > i;
+      if (!direct && !mirror) continue;
+      const size_t e = direct ? row + j : (size_t)j * ld + i;
+      long long vv = (long long)__float2int_rn(v[jj]) * (1ll << shift);
+      if (!first) vv += outi[e];
+      if (!last) {
+        outi[e] = vv;
+        if (direct && mirror) outi[(size_t)j * ld + i] = vv;
+        continue;
+      }
+      double x = (double)vv * ri * a.cs[j];
       if (with_diag) {
         // exact diagonal terms: d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
         const double dbj = a.b_diag[j];
         x += dai * a.b_full[row + j] + a.a_full[row + j] * dbj - (i == j ? dai * dbj : 0.0);
       }
-      if (!a.sym || j >= i) {
-        double* p = out + row + j;
-        *p = first ? x : (*p + x);
-      }
-      if (a.sym && j > i) {
-        double* p = out + (size_t)j * ld + i;
-        *p = first ? x : (*p + x);
-      }
+      out[e] = x;
+      if (direct && mirror) out[(size_t)j * ld + i] = x;
     }
   }
 }
