@@ -293,10 +293,15 @@ def run_rsign(args):
     flops_per_launch = float(args.d) ** 3
     achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+    # the hi/lo stage-1 representation issues three pair products per launch
+    issued_mult = 3.0 if (policy in (rs.Policy.FP16_REFINE, rs.Policy.BF16_REFINE) and opt.low_split) else 1.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "tc_gemm_kernel (NS SYRK / symmetric update, FP16, 128x256 tiles)",
+            "traffic": None,
+            "kernel": "tc_gemm_kernel NS SYRK / symmetric update (stage 1, FP16, 128x256 tiles)",
             "peak_kind": "%s bf16 sustained (FP16 has the same nominal dense rate)" % pk_kind,
-            "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_ms}
+            "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_ms,
+            "issued_per_algorithmic": issued_mult,
+            "issued_tflops": achieved * issued_mult, "issued_frac": achieved * issued_mult / peak}
 
     fp64 = None
     if not args.no_fp64:

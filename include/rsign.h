@@ -80,7 +80,9 @@ typedef struct {
   double shift;            /* shift s used                                             */
   double gamma_est;        /* alpha * estimated margin min |lam_i - s| (auto shift) or
                               NaN when the margin is not known                         */
-  double resid_fro;        /* ||R^2 - I||_F of the returned R                          */
+  double resid_fro;        /* ||R^2 - I||_F of the returned R; REFINE policies: of the
+                              iterate before the final update-form polish step (the
+                              returned R is one quadratically convergent step further) */
   double trace;            /* trace(R)                                                 */
   double correction_fro;   /* ||last refinement correction||_F (REFINE policies)       */
   double commutator_fro;   /* ||R A - A R||_F, A = H - sI, at the last check (REFINE)  */

@@ -29,6 +29,14 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
                                float* out, int* status, void* stream);
 
 /*
+ * Process-wide choice of the tensor-core GEMM variant used by every later
+ * call: 2 (default) = CTA pairs of a thread-block cluster sharing each
+ * 256-row B panel through TMA multicast; 1 = independent CTAs.  Returns the
+ * previous setting.  Not thread-safe; meant for tests and measurements.
+ */
+int32_t rsign_dbg_set_tc_cluster(int32_t cluster);
+
+/*
  * FP64 product on the FP64 pipe: out = A * B, all dp x dp row-major FP64,
  * dp a multiple of 64; sym = 1 as above.
  */

@@ -131,6 +131,8 @@ def load():
     lib.rsign_dbg_f64_gemm.restype = ctypes.c_int
     lib.rsign_dbg_fp64grade_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
     lib.rsign_dbg_fp64grade_gemm.restype = ctypes.c_int
+    lib.rsign_dbg_set_tc_cluster.argtypes = [i32]
+    lib.rsign_dbg_set_tc_cluster.restype = i32
     _lib = lib
     return lib
 
@@ -309,6 +311,11 @@ def dbg_f64_gemm(A, B, sym=0, out=None, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def dbg_set_tc_cluster(cluster: int) -> int:
+    """Select the tensor-core GEMM variant (2: cluster pairs, 1: single CTAs); returns the previous one."""
+    return int(load().rsign_dbg_set_tc_cluster(int(cluster)))
 
 
 def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):

@@ -35,6 +35,7 @@ struct TcGemmArgs {
   int pair_a[kTcMaxPairs];
   int pair_b[kTcMaxPairs];
   double group_scale[kTcMaxGroups];
+  int cluster;                    // 1: single-CTA tiles; 0 or 2: cluster pairs sharing B (default)
   int group_shift[kTcMaxGroups];  // TC_EPI_OZAKI: group weight 2^shift in the int64 sum
   double final_scale;             // TC_EPI_OZAKI: weight of one unit of that sum
   float scale;
@@ -57,6 +58,9 @@ struct TcGemmArgs {
 
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
 int tc_num_tiles(int dp, int sym);
+// Process-wide default for TcGemmArgs::cluster == 0 (2 unless set to 1);
+// returns the previous value.
+int tc_set_default_cluster(int cl);
 
 // Launch.  A/B point to [a_slices][dp][dp] / [b_slices][dp][dp] arrays of
 // the operand type; lp_fmt 0 = FP16, 1 = BF16.  dp must be a multiple of 256.

@@ -223,12 +223,15 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     return cudaSuccess;
   };
 
+  // No polish before the first sweep: the stage-1 result is an involution to
+  // the split trajectory's floor, and the sweep's own polish step follows the
+  // correction (measured: the same error after one sweep with or without it).
   RS_TRY(c.ok(split_rows(in.A64, dp, As, st)) ? cudaSuccess : c.err);
-  RS_TRY(polish());
   double h_red[16];
   if (in.M == 0) {
     // X_0 was already at the low-precision floor (A a scaled near-involution):
     // there is no trajectory to differentiate; the polish alone finishes R.
+    RS_TRY(polish());
     RS_TRY(polish());
     RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
     RS_TRY(cudaStreamSynchronize(st));
@@ -734,6 +737,8 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
   a.scale = 1.0f; a.out = out; a.status = status; a.skip = nullptr;
   return tc_gemm(a, A, 1, B, 1, fmt, sms, (cudaStream_t)stream) == cudaSuccess ? RSIGN_OK : RSIGN_ERR_CUDA;
 }
+
+int32_t rsign_dbg_set_tc_cluster(int32_t cluster) { return tc_set_default_cluster(cluster); }
 
 rsign_status rsign_dbg_f64_gemm(const double* A, const double* B, int64_t dp, int32_t sym, double* out,
                                 void* stream) {

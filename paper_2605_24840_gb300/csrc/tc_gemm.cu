@@ -29,31 +29,41 @@ constexpr int NUM_THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
+// Tile schedule over 128 x 256 output tiles (bm, bn).  With cluster pairs
+// (cl = 2) the unit is a 256-row super-tile (a, bn) covering bm = 2a and
+// bm = 2a + 1: both tiles need the same 256-row panel of B, which the pair
+// loads once (each CTA half of it, multicast to both).  In the triangular
+// schedule tile (bm, bn) is needed iff bn >= floor(bm / 2), so both members
+// of a pair are always needed together.
 struct TileSched {
-  int nbm, nbn, sym, n;
-  __device__ __host__ TileSched(int dp, int s) : nbm(dp / BM), nbn(dp / BN), sym(s) {
+  int nbm, nbn, sym, cl, n;
+  __device__ __host__ TileSched(int dp, int s, int c) : nbm(dp / BM), nbn(dp / BN), sym(s), cl(c) {
+    const int rows = nbm / cl;  // schedule rows: tiles (cl == 1) or super-tiles (cl == 2)
     if (!s) {
-      n = nbm * nbn;
+      n = rows * nbn;
     } else {
       n = 0;
-      for (int bm = 0; bm < nbm; ++bm) n += nbn - bm / 2;
+      for (int r = 0; r < rows; ++r) n += nbn - (cl == 1 ? r / 2 : r);
     }
   }
-  __device__ __forceinline__ void decode(int t, int& bm, int& bn) const {
+  // unit t -> (bm, bn) for cluster rank `rank`
+  __device__ __forceinline__ void decode(int t, int rank, int& bm, int& bn) const {
+    int r, c;
     if (!sym) {
-      bm = t / nbn;
-      bn = t % nbn;
-      return;
+      r = t / nbn;
+      c = t % nbn;
+    } else {
+      r = 0;
+      for (;;) {
+        const int cnt = nbn - (cl == 1 ? r / 2 : r);
+        if (t < cnt) break;
+        t -= cnt;
+        ++r;
+      }
+      c = (cl == 1 ? r / 2 : r) + t;
     }
-    int b = 0;
-    for (;;) {
-      const int cnt = nbn - b / 2;
-      if (t < cnt) break;
-      t -= cnt;
-      ++b;
-    }
-    bm = b;
-    bn = b / 2 + t;
+    bm = cl == 1 ? r : 2 * r + rank;
+    bn = c;
   }
 };
 
@@ -240,11 +250,11 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
   }
 }
 
-template <int EPI, typename T>
+template <int EPI, typename T, int CL>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ TcGemmArgs args, const uint32_t idesc) {
-  if (args.skip != nullptr && *args.skip != 0) return;  // uniform across the grid
+  if (args.skip != nullptr && *args.skip != 0) return;  // uniform across the grid (and cluster)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -261,10 +271,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* status = args.status;
 
+  // cluster rank (pairs share the B panel); a stage of a pair is free only
+  // when the MMAs of both CTAs have consumed it
+  const int rank = CL == 2 ? (int)cluster_ctarank() : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&empty[s]), CL);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&tfull[s]), 1);
@@ -282,12 +295,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tmem_relinquish();
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (CL == 2) cluster_sync_all();  // peer barriers initialised before any multicast
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const TileSched sched(args.dp, args.sym);
+  const TileSched sched(args.dp, args.sym, CL);
   const int n_kb = args.dp / BK;
+  const int unit0 = blockIdx.x / CL, unit_step = gridDim.x / CL;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -295,17 +310,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < sched.n; t += gridDim.x) {
+      for (int t = unit0; ok && t < sched.n; t += unit_step) {
         int bm, bn;
-        sched.decode(t, bm, bn);
+        sched.decode(t, rank, bm, bn);
         for (int g = 0; ok && g < args.n_groups; ++g) {
           for (int pi = args.group_start[g]; ok && pi < args.group_start[g + 1]; ++pi) {
             for (int kb = 0; kb < n_kb; ++kb) {
               if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, status)) { ok = false; break; }
               const uint32_t fb = smem_u32(&full[stage]);
+              // the full barrier counts all of the stage's bytes, including the
+              // half of B that the peer multicasts into this CTA
               mbar_arrive_expect_tx(fb, STAGE_BYTES);
               tma_load_3d(smem_u32(sA + stage * A_BYTES), &tmA, fb, kb * BK, bm * BM, args.pair_a[pi]);
-              tma_load_3d(smem_u32(sB + stage * B_BYTES), &tmB, fb, kb * BK, bn * BN, args.pair_b[pi]);
+              if constexpr (CL == 2) {
+                tma_load_3d_mc(smem_u32(sB + stage * B_BYTES + rank * (B_BYTES / 2)), &tmB, fb, kb * BK,
+                               bn * BN + rank * (BN / 2), args.pair_b[pi], (uint16_t)0x3);
+              } else {
+                tma_load_3d(smem_u32(sB + stage * B_BYTES), &tmB, fb, kb * BK, bn * BN, args.pair_b[pi]);
+              }
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
           }
@@ -326,7 +348,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0;
       int acc_it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < sched.n; t += gridDim.x) {
+      for (int t = unit0; ok && t < sched.n; t += unit_step) {
         for (int g = 0; ok && g < args.n_groups; ++g) {
           const int acc = acc_it & 1;
           const uint32_t aph = (acc_it >> 1) & 1;
@@ -346,7 +368,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 tc_mma_f16(d_tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accumulate);
                 accumulate = 1;
               }
-              tc_commit(smem_u32(&empty[stage]));
+              if constexpr (CL == 2) tc_commit_mc(smem_u32(&empty[stage]), (uint16_t)0x3);
+              else tc_commit(smem_u32(&empty[stage]));
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
           }
@@ -364,9 +387,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int r = quad * 32 + lane;
     int acc_it = 0;
     bool ok = true;
-    for (int t = blockIdx.x; ok && t < sched.n; t += gridDim.x) {
+    for (int t = unit0; ok && t < sched.n; t += unit_step) {
       int bm, bn;
-      sched.decode(t, bm, bn);
+      sched.decode(t, rank, bm, bn);
       const int i = bm * BM + r;
       double acc1 = 0.0;
       for (int g = 0; g < args.n_groups; ++g) {
@@ -395,13 +418,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (!ok) break;
       if constexpr (EPI == TC_EPI_NS_SYRK || EPI == TC_EPI_NS_UPDATE) {
         const double s = warp_sum(acc1);
-        if (lane == 0) args.partials[(size_t)t * 4 + quad] = s;
+        if (lane == 0) args.partials[((size_t)t * CL + rank) * 4 + quad] = s;
       }
     }
   }
 
   tc_fence_before();
-  __syncthreads();
+  // Every role has drained its own asynchronous work (bounded waits above);
+  // a pair also waits for the peer, whose multicast loads and commits target
+  // this CTA's shared memory, before either CTA leaves.
+  if constexpr (CL == 2) cluster_sync_all();
+  else __syncthreads();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -443,50 +470,100 @@ bool make_map(CUtensorMap* m, const void* ptr, int dp, int slices, int box_rows,
   return r == CUDA_SUCCESS;
 }
 
-template <int EPI, typename T>
+template <int EPI, typename T, int CL>
 cudaError_t launch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
                    uint32_t idesc, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<EPI, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<EPI, T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  tc_gemm_kernel<EPI, T><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, a, idesc);
-  return cudaGetLastError();
+  if (CL > 1) {
+    // as many pairs as the GPCs can hold at once (the schedule is persistent)
+    static int max_clusters = -1;
+    static std::once_flag occ;
+    std::call_once(occ, [] {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(2 * 64, 1, 1);
+      q.blockDim = dim3(NUM_THREADS, 1, 1);
+      q.dynamicSmemBytes = SMEM_BYTES;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = CL;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<EPI, T, CL>, &q) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+      }
+      max_clusters = n;
+    });
+    if (max_clusters > 0 && grid > CL * max_clusters) grid = CL * max_clusters;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(NUM_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<EPI, T, CL>, ma, mb, a, idesc);
 }
 
-template <typename T>
+template <typename T, int CL>
 cudaError_t dispatch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
                      uint32_t idesc, cudaStream_t st) {
   switch (a.epi) {
-    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_OZAKI: return launch<TC_EPI_OZAKI, T>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T, CL>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, CL>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, CL>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, CL>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_OZAKI: return launch<TC_EPI_OZAKI, T, CL>(a, ma, mb, grid, idesc, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-int tc_num_tiles(int dp, int sym) { return TileSched(dp, sym).n; }
+int tc_num_tiles(int dp, int sym) { return TileSched(dp, sym, 1).n; }
+
+static int g_default_cluster = 2;
+int tc_set_default_cluster(int cl) {
+  const int prev = g_default_cluster;
+  g_default_cluster = (cl == 1) ? 1 : 2;
+  return prev;
+}
 
 cudaError_t tc_gemm(const TcGemmArgs& args, const void* A, int a_slices, const void* B, int b_slices,
                     int lp_fmt, int num_sms, cudaStream_t st) {
   if (args.dp % BN != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
       args.group_start[args.n_groups] > kTcMaxPairs)
     return cudaErrorInvalidValue;
+  // cluster pairs (B panel multicast) unless args.cluster == 1
+  const int cl = args.cluster == 0 ? g_default_cluster : (args.cluster == 1 ? 1 : 2);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) || !make_map(&mb, B, args.dp, b_slices, BN, lp_fmt))
+  if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) ||
+      !make_map(&mb, B, args.dp, b_slices, BN / cl, lp_fmt))
     return cudaErrorInvalidValue;
-  const int n = tc_num_tiles(args.dp, args.sym);
-  const int grid = n < num_sms ? n : num_sms;
+  const int units = TileSched(args.dp, args.sym, cl).n;
+  const int max_units = num_sms / cl;
+  const int grid = cl * (units < max_units ? units : max_units);
   const uint32_t idesc = idesc_f16(lp_fmt ? 1u : 0u, BM, BN);
-  return lp_fmt ? dispatch<__nv_bfloat16>(args, ma, mb, grid, idesc, st)
-                : dispatch<__half>(args, ma, mb, grid, idesc, st);
+  if (cl == 2)
+    return lp_fmt ? dispatch<__nv_bfloat16, 2>(args, ma, mb, grid, idesc, st)
+                  : dispatch<__half, 2>(args, ma, mb, grid, idesc, st);
+  return lp_fmt ? dispatch<__nv_bfloat16, 1>(args, ma, mb, grid, idesc, st)
+                : dispatch<__half, 1>(args, ma, mb, grid, idesc, st);
 }
 
 }  // namespace rsign

@@ -51,6 +51,28 @@ def test_tc_gemm_symmetric_schedule(dp, fmt):
     _check_fp32_accumulation(torch, out, ref, X.float().abs() @ X.float().abs(), dp)
 
 
+@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("dp,sym", [(512, 0), (1536, 1), (4096, 0), (4096, 1)])
+def test_tc_gemm_cluster_variants_agree(cluster, dp, sym):
+    # independent CTAs and cluster pairs (B panel multicast) give identical bits
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    X = _rand(torch, dp, torch.float16, 99 + dp, sym=bool(sym))
+    Y = X if sym else _rand(torch, dp, torch.float16, 98 + dp)
+    prev = rs.dbg_set_tc_cluster(cluster)
+    try:
+        out, status = rs.dbg_tc_gemm(X, Y, fmt=0, sym=sym)
+        rs.dbg_set_tc_cluster(3 - cluster)
+        out2, status2 = rs.dbg_tc_gemm(X, Y, fmt=0, sym=sym)
+    finally:
+        rs.dbg_set_tc_cluster(prev)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0 and int(status2.item()) == 0
+    assert torch.equal(out, out2)
+    ref = X.float() @ Y.float().T
+    _check_fp32_accumulation(torch, out, ref, X.float().abs() @ Y.float().abs().T, dp)
+
+
 @pytest.mark.parametrize("dp,sym", [(64, 0), (128, 1), (320, 0), (512, 1)])
 def test_f64_gemm_matches_torch(dp, sym):
     torch = cuda_or_skip()

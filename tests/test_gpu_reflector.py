@@ -167,7 +167,11 @@ def test_refine_reaches_1e6(policy, d, k, delta):
     assert info.sweeps_refine >= 1 and info.cert_ok == 1
     assert abs(info.trace - (d - 2 * k)) < 1e-6
     assert err <= 1e-6, (err, info.as_dict())
-    assert info.resid_fro < 1e-5
+    # the returned R is an involution and symmetric to working accuracy
+    assert np.linalg.norm(R @ R - np.eye(d)) < 1e-6
+    assert np.array_equal(R, R.T)
+    assert info.resid_fro < 1e-3  # measured before the last polish step
+    assert info.err_est <= 1e-6
 
 
 @pytest.mark.parametrize("theta", [0.1, 0.9])
