@@ -170,6 +170,30 @@ rsign_status rsign_reflector_backward(const double* H, int64_t d, int32_t k, dou
                                       rsign_policy policy, const double* Rbar, double* Hbar,
                                       int32_t ckpt_every, void* stream);
 
+/*
+ * rsign_reflector_noalloc -- the FP64-policy reflector (same result as
+ * rsign_reflector with RSIGN_FP64) for callers that cannot allocate device
+ * memory during their work: code whose device memory is planned once at
+ * start-up, embedders with a fixed memory budget, or threads that must not
+ * wait on the allocator.  The paper has no counterpart of this entry point;
+ * it exists for deployment only.
+ *   - No device memory is allocated or freed: the workspace is one static
+ *     device array inside librsign (about 8.2 MiB), which every GPU that loads
+ *     the library holds until the process exits.
+ *   - Limit: 2 <= d <= 512; larger d returns RSIGN_ERR_UNSUPPORTED.
+ *   - H and R must be device pointers (host buffers would need staging
+ *     memory): host pointers return RSIGN_ERR_ARG.  tol and k as for
+ *     rsign_reflector; at most 100 Newton-Schulz steps.
+ *   - All calls share the static array: calls that overlap on the GPU (on
+ *     several streams or from several host threads) race and must be
+ *     serialised by the caller.  Each call clears the part it needs zeroed.
+ *   - The first call on each device looks up the array's device address; make
+ *     that first call before capturing the stream into a CUDA graph.
+ *   - Blocking like rsign_reflector; info->workspace_bytes is 0.
+ */
+rsign_status rsign_reflector_noalloc(const double* H, int64_t d, int32_t k, double s, double tol,
+                                     double* R, rsign_info* info, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* rsign_status_str(rsign_status st);
 
