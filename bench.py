@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--theta", type=float, default=0.5)
     p.add_argument("--policy", default="FP16_REFINE")
     p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--alpha", default="power", choices=["power", "inf"],
+                   help="scaling: power steps (1/(1.02 rho_est)) or the Gershgorin bound 1/||H-sI||_inf")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 Newton-Schulz comparator")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -155,14 +157,15 @@ def cpu_oracle_sample(H_host, s, k, lam, seconds=15.0):
     d = X0.shape[0]
     gamma = alpha * float(np.min(np.abs(lam - s)))
     steps = oracle.ns_steps(gamma, 1e-6, 10000)
-    rows = 4
-    t0 = time.perf_counter()
-    oracle.ns_step_rows(X0, 0, rows)
-    t1 = time.perf_counter() - t0
-    rows2 = int(max(rows, min(d, rows * seconds / max(t1, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.ns_step_rows(X0, 0, rows2)
-    t2 = time.perf_counter() - t0
+    # grow the row block until one timed sample takes most of `seconds`
+    rows2, t2 = 32, 0.0
+    for _ in range(6):
+        t0 = time.perf_counter()
+        oracle.ns_step_rows(X0, 0, rows2)
+        t2 = time.perf_counter() - t0
+        if t2 >= 0.6 * seconds or rows2 >= d:
+            break
+        rows2 = int(min(d, max(rows2 + 1, rows2 * seconds / max(t2, 1e-3))))
     per_step = t2 * d / rows2
     return {"value": per_step * steps * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "rows 0..%d of one naive FP64 Newton-Schulz step at d=%d (%.1f s), extrapolated x%d rows/"
@@ -209,7 +212,9 @@ def workload_config(args):
     return {"workload": "controlled-spectrum dense symmetric H, d=%d, k=%d, delta=%g, shift at %.0f%% of the gap,"
                         " %s to err<=%g" % (args.d, args.k, args.delta, 100 * args.theta, args.policy, args.tol),
             "d": args.d, "k": args.k, "delta": args.delta, "theta": args.theta, "policy": args.policy,
-            "tol": args.tol, "alpha": "1/||H-sI||_inf", "parallelism": "replicas",
+            "tol": args.tol,
+            "alpha": "1/(1.02 rho_est), 20 power steps" if args.alpha == "power" else "1/||H-sI||_inf",
+            "parallelism": "replicas",
             "l2": "inputs larger than L2 (H = 8 d^2 bytes)"}
 
 
@@ -233,7 +238,7 @@ def run_rsign(args):
     lam_h = lam.cpu().numpy()
     s = float(lam_h[args.k - 1] + args.theta * (lam_h[args.k] - lam_h[args.k - 1]))
     R = torch.empty_like(H)
-    opt = rs.default_options()
+    opt = rs.default_options(alpha_mode=int(rs.AlphaMode.POWER if args.alpha == "power" else rs.AlphaMode.INF))
     stream = torch.cuda.current_stream(dev)
 
     def call(Hin, Rout, pol=policy, tol=args.tol):

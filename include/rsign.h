@@ -18,8 +18,10 @@
  *     or pinned); host buffers are copied in and out on `stream` inside the
  *     call.  The caller owns every buffer; the library never frees them;
  *   - only the symmetric part 1/2 (H + H^T) of H is used; H is read-only;
- *   - workspace is allocated inside the call (stream-ordered) and released
- *     before it returns; no state survives a call;
+ *   - workspace is allocated inside the call (stream-ordered, from a
+ *     library-owned pool) and released before it returns; the pool keeps the
+ *     memory mapped for later calls until rsign_trim_workspace(); no other
+ *     state survives a call;
  *   - calls are blocking: they return once `info` (if given) is filled, since
  *     the certificate is part of the result;
  *   - errors are reported through the return value only: the library never
@@ -67,7 +69,10 @@ typedef enum {
 typedef enum {
   RSIGN_ALPHA_INF = 0,    /* alpha = 1/||H - sI||_inf (Gershgorin bound on rho)          */
   RSIGN_ALPHA_POWER = 1   /* alpha = 1/(1.02 rho_est), rho_est from power steps on H - sI
-                             followed by a Gershgorin-safe clamp                         */
+                             (closer to 1/rho than the Gershgorin bound, so a larger scaled
+                             margin and fewer steps); sign preservation needs alpha rho <
+                             sqrt(3), i.e. rho_est > 0.57 rho: if the trace certificate
+                             fails, rsign_reflector_ex repeats the call with RSIGN_ALPHA_INF */
 } rsign_alpha_mode;
 
 /* Per-call report, filled on the host when `info` is not NULL. */
@@ -105,7 +110,7 @@ typedef struct {
   int32_t polish_steps;     /* FP64 polish steps for *_POLISH policies (default 2)      */
   int32_t max_sweeps;       /* refinement sweep budget (default 4)                      */
   int32_t alpha_mode;       /* rsign_alpha_mode (default RSIGN_ALPHA_INF)               */
-  int32_t power_steps;      /* power steps for RSIGN_ALPHA_POWER (default 12)           */
+  int32_t power_steps;      /* power steps for RSIGN_ALPHA_POWER (default 20)           */
   int32_t timing;           /* 1: fill ms_* fields with CUDA events (default 1)        */
   int32_t low_split;        /* REFINE policies: 1 carries the low-precision iterates as
                                hi/lo pairs (three fused pair products per step, about
@@ -199,6 +204,16 @@ const char* rsign_status_str(rsign_status st);
 
 /* Library version string, e.g. "rsign 0.1 sm_103a". */
 const char* rsign_version(void);
+
+/*
+ * rsign_trim_workspace -- return the workspace memory cached by earlier calls
+ * to the driver.  Calls take their workspace from a library-owned
+ * stream-ordered pool per device that keeps freed memory for the next call
+ * (re-mapping tens of GB per call would cost tens of milliseconds); this
+ * releases it.  Call it when no rsign call is in flight.  The paper has no
+ * counterpart; it is resource management only.
+ */
+rsign_status rsign_trim_workspace(void);
 
 #ifdef __cplusplus
 }

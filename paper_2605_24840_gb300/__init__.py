@@ -125,6 +125,8 @@ def load():
     lib.rsign_status_str.restype = ctypes.c_char_p
     lib.rsign_version.argtypes = []
     lib.rsign_version.restype = ctypes.c_char_p
+    lib.rsign_trim_workspace.argtypes = []
+    lib.rsign_trim_workspace.restype = ctypes.c_int
     lib.rsign_dbg_tc_gemm.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp]
     lib.rsign_dbg_tc_gemm.restype = ctypes.c_int
     lib.rsign_dbg_f64_gemm.argtypes = [vp, vp, i64, i32, vp, vp]
@@ -143,6 +145,13 @@ def status_str(code) -> str:
 
 def version() -> str:
     return load().rsign_version().decode()
+
+
+def trim_workspace() -> None:
+    """Return the workspace memory cached by earlier calls to the driver (rsign_trim_workspace)."""
+    st = Status(load().rsign_trim_workspace())
+    if st != Status.OK:
+        raise RsignError(st)
 
 
 def default_options(**kw) -> Options:

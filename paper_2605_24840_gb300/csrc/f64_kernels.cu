@@ -324,6 +324,19 @@ __global__ void normalize_kernel(double* y, int n, double* x, double* nrm) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i] * inv;
 }
 
+__global__ void init_vec_kernel(double* x, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] = 1.0 + (i % 7) * 0.125;
+}
+
+__global__ void alpha_from_rho_kernel(const double* nrm, double c, double* scal) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double rho = nrm[0];
+    scal[3] = rho;
+    scal[1] = rho > 0.0 ? 1.0 / (c * rho) : 0.0;
+  }
+}
+
 __global__ void copy_unpad_kernel(const double* __restrict__ src, int dp, double* __restrict__ dst, int d) {
   const size_t n = (size_t)d * d;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -429,6 +442,18 @@ cudaError_t gemv_f64(const double* A, int dp, const double* x, double* y, cudaSt
 
 cudaError_t normalize(double* y, int n, double* x, double* nrm, cudaStream_t st) {
   normalize_kernel<<<1, 1024, 0, st>>>(y, n, x, nrm);
+  return cudaGetLastError();
+}
+
+cudaError_t power_alpha(const double* A, int dp, double* x, double* y, int iters, double c, double* scal,
+                        cudaStream_t st) {
+  init_vec_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y, dp);
+  normalize_kernel<<<1, 1024, 0, st>>>(y, dp, x, scal + 4);
+  for (int it = 0; it < iters; ++it) {
+    gemv_kernel<<<(dp + 7) / 8, 256, 0, st>>>(A, dp, x, y);
+    normalize_kernel<<<1, 1024, 0, st>>>(y, dp, x, scal + 4);  // scal[4] = ||A x_prev||
+  }
+  alpha_from_rho_kernel<<<1, 32, 0, st>>>(scal + 4, c, scal);
   return cudaGetLastError();
 }
 

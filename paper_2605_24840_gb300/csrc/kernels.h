@@ -129,6 +129,14 @@ cudaError_t ns_check(const double* partials, int n, double* hist, int m, double 
 cudaError_t trace_f64(const double* X, int dp, int d, double* out, cudaStream_t st);
 // Power-iteration helpers: x <- y / ||y||_2, norm stored in *nrm.
 cudaError_t normalize(double* y, int n, double* x, double* nrm, cudaStream_t st);
+// Scaling by power steps (Sec. 4.3: alpha close to 1/||H - sI||_2 enlarges the
+// scaled margin gamma): rho_est = ||A v_m|| after `iters` steps from a fixed
+// start vector (a lower bound of rho(A) converging from below); then
+// scal[1] = alpha = 1 / (c rho_est), scal[3] = rho_est.  alpha rho < sqrt(3)
+// keeps every sign (f(t) = t(3 - t^2)/2 > 0 on (0, sqrt(3))) as long as
+// rho_est > rho / (c sqrt(3)); the trace certificate checks it.
+cudaError_t power_alpha(const double* A, int dp, double* x, double* y, int iters, double c, double* scal,
+                        cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // FP64-grade products on the FP16 tensor cores (refine.cu).
@@ -157,8 +165,10 @@ struct SplitMat {
 cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st);
 // out (FP64, dp x dp) = A * B for split symmetric A, B (K = d_real nonzeros);
 // sym = 1 when the product is symmetric (A == B): upper tiles + mirror.
+// `levels` (<= kSlices) truncates the digit-plane product after levels
+// 0 .. levels-1 (5 bits each, relative to the off-diagonal row maxima).
 cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym,
-                       double* out, int* status, int num_sms, cudaStream_t st);
+                       double* out, int* status, int num_sms, cudaStream_t st, int levels = kSlices);
 
 // Elementwise kernels of the refinement sweep.  `scal` is a small device
 // array of scalars: each kernel documents the slots it reads and writes.

@@ -285,7 +285,8 @@ cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st) {
 }
 
 cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym, double* out,
-                       int* status, int num_sms, cudaStream_t st) {
+                       int* status, int num_sms, cudaStream_t st, int levels) {
+  const int L = levels < 1 ? 1 : (levels > kSlices ? kSlices : levels);
   TcGemmArgs a{};
   a.dp = dp;
   a.d_real = d_real;
@@ -305,7 +306,7 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
   const double bound1 = std::ldexp(1.0, 2 * kSliceBeta - 2) * (double)d_real;
   const int max_pairs = std::max(1, (int)std::floor(std::ldexp(1.0, 24) / bound1));
   int np = 0, ng = 0;
-  for (int t = 0; t < kSlices; ++t) {  // levels 0 .. kSlices-1 (truncation after 35 bits)
+  for (int t = 0; t < L; ++t) {  // levels 0 .. L-1 (truncation after 5 L bits)
     int in_group = 0;
     for (int p = 0; p <= t; ++p) {
       const int q = t - p;
@@ -316,7 +317,7 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
         a.group_scale[ng] = std::ldexp(1.0, -kSliceBeta * (t + 2));
         // integer weight relative to the deepest level kSlices-1: the int64
         // sum stays below 2^(24 + beta (kSlices-1) + 2) < 2^63
-        a.group_shift[ng] = kSliceBeta * (kSlices - 1 - t);
+        a.group_shift[ng] = kSliceBeta * (L - 1 - t);
         ++ng;
       }
       if (np >= kTcMaxPairs) return cudaErrorInvalidValue;
@@ -328,7 +329,7 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
   }
   a.n_groups = ng;
   a.group_start[ng] = np;
-  a.final_scale = std::ldexp(1.0, -kSliceBeta * (kSlices - 1 + 2));
+  a.final_scale = std::ldexp(1.0, -kSliceBeta * (L - 1 + 2));
   return tc_gemm(a, A.planes, kSlices, B.planes, kSlices, 0, num_sms, st);
 }
 

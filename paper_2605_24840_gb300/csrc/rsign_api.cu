@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 namespace rsign {
@@ -23,13 +24,46 @@ namespace {
 
 constexpr int kChunk = 8;  // NS steps enqueued between host checks of the stop flag
 
+// Library-owned stream-ordered memory pool per device.  Its release threshold
+// is unlimited, so the workspace of one call stays mapped for the next call
+// (re-mapping tens of GB per call costs tens of milliseconds);
+// rsign_trim_workspace() returns the cached memory to the driver.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaMemPool_t library_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxPoolDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (g_pools[dev] == nullptr) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
 struct DevBuf {
   std::vector<void*> ptrs;
   cudaStream_t st = nullptr;
   int64_t bytes = 0;
   cudaError_t alloc(void** p, size_t n) {
     n = (n + 255) & ~size_t(255);
-    cudaError_t e = cudaMallocAsync(p, n, st);
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, n, pool, st) : cudaMallocAsync(p, n, st);
     if (e == cudaSuccess) {
       ptrs.push_back(*p);
       bytes += (int64_t)n;
@@ -211,7 +245,9 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   auto polish = [&]() -> cudaError_t {
     cudaError_t r;
     if (!c.ok(r = split_rows(in.R64, dp, Rs, st))) return r;
-    if (!c.ok(r = ozaki_gemm(Rs, Rs, dp, d, 1, N64, status, c.num_sms, st))) return r;
+    // R^2 to ~1e-9 absolute suffices for the polish: 6 levels (30 bits of the
+    // off-diagonal part, the diagonal exact)
+    if (!c.ok(r = ozaki_gemm(Rs, Rs, dp, d, 1, N64, status, c.num_sms, st, kSlices - 1))) return r;
     if (!c.ok(r = ident_minus(N64, dp, d, C32, bmax, part, st))) return r;
     if (!c.ok(r = sum_partials(part, ntile, red + 0, st))) return r;
     if (!c.ok(r = max_pow2(bmax, ntile, fs + 0, st))) return r;
@@ -255,7 +291,10 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   for (int sw = 0; sw <= in.max_sweeps; ++sw) {
     // commutator C = R A - A R from the FP64-grade product N = R A
     if (!c.ok(split_rows(in.R64, dp, Rs, st))) return c.err;
-    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st))) return c.err;
+    // the first sweep only needs the commutator to ~1e-4 of its (large) size:
+    // 6 levels; the a-posteriori check and later sweeps use all 7
+    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st, sw == 0 ? kSlices - 1 : kSlices)))
+      return c.err;
     if (!c.ok(antisym_part(N64, dp, C32, bmax, part, st))) return c.err;
     if (!c.ok(sum_partials(part, ntile, red + 4, st))) return c.err;
     if (!c.ok(max_pow2(bmax, ntile, fs + 2, st))) return c.err;
@@ -385,6 +424,15 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   // ---- ingest and scaling (Sec. 4.3: alpha = 1/||H - sI||_inf)
   if (!c.ok(ingest(Hd, d, dp, s, A64, rowpart, &ctl->flags, st))) return fail_cuda();
   if (!c.ok(inf_norm_finish(rowpart, dp, rowsum, ctl->scal, st))) return fail_cuda();
+  if (opt.alpha_mode == RSIGN_ALPHA_POWER) {
+    // alpha = 1/(1.02 rho_est) from power steps on A (overwrites the Gershgorin value)
+    double *px = nullptr, *py = nullptr;
+    if (mem.alloc((void**)&px, (size_t)dp * 8) != cudaSuccess ||
+        mem.alloc((void**)&py, (size_t)dp * 8) != cudaSuccess)
+      return fail_cuda();
+    if (!c.ok(power_alpha(A64, dp, px, py, std::max(1, opt.power_steps), 1.02, ctl->scal, st))) return fail_cuda();
+    c.launches += 2 * std::max(1, opt.power_steps) + 2;
+  }
   if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return fail_cuda();
@@ -630,7 +678,7 @@ void rsign_options_default(rsign_options* opt) {
   opt->polish_steps = 2;
   opt->max_sweeps = 4;
   opt->alpha_mode = RSIGN_ALPHA_INF;
-  opt->power_steps = 12;
+  opt->power_steps = 20;
   opt->timing = 1;
   opt->low_split = 1;
 }
@@ -638,7 +686,15 @@ void rsign_options_default(rsign_options* opt) {
 rsign_status rsign_reflector_ex(const double* H, int64_t d, int32_t k, double s, double tol,
                                 rsign_policy policy, const rsign_options* opt, double* R,
                                 rsign_info* info, void* stream) {
-  return reflector_impl(H, d, k, s, tol, policy, opt, R, info, (cudaStream_t)stream);
+  rsign_status st = reflector_impl(H, d, k, s, tol, policy, opt, R, info, (cudaStream_t)stream);
+  if (st == RSIGN_ERR_CERT && opt && opt->alpha_mode == RSIGN_ALPHA_POWER) {
+    // the power estimate of rho came out too low (alpha rho >= sqrt(3) flips
+    // signs): redo the call with the Gershgorin scaling, which is always safe
+    rsign_options o = *opt;
+    o.alpha_mode = RSIGN_ALPHA_INF;
+    st = reflector_impl(H, d, k, s, tol, policy, &o, R, info, (cudaStream_t)stream);
+  }
+  return st;
 }
 
 rsign_status rsign_reflector(const double* H, int64_t d, int32_t k, double s, double tol,
@@ -716,6 +772,18 @@ const char* rsign_status_str(rsign_status st) {
 }
 
 const char* rsign_version(void) { return "rsign 0.1 sm_103a"; }
+
+rsign_status rsign_trim_workspace(void) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  for (int i = 0; i < kMaxPoolDevices; ++i) {
+    if (g_pools[i] == nullptr) continue;
+    if (cudaMemPoolTrimTo(g_pools[i], 0) != cudaSuccess) {
+      cudaGetLastError();
+      return RSIGN_ERR_CUDA;
+    }
+  }
+  return RSIGN_OK;
+}
 
 }  // extern "C"
 

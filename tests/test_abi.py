@@ -60,6 +60,7 @@ def test_status_strings_and_defaults(rs):
         assert isinstance(rs.status_str(st), str) and rs.status_str(st)
     o = rs.default_options()
     assert o.max_steps == 100 and o.polish_steps == 2 and o.timing == 1
+    assert o.power_steps == 20 and o.alpha_mode == rs.AlphaMode.INF and o.low_split == 1
     assert "sm_103a" in rs.version()
 
 

@@ -174,6 +174,38 @@ def test_refine_reaches_1e6(policy, d, k, delta):
     assert info.err_est <= 1e-6
 
 
+def test_power_alpha_enlarges_margin_and_saves_steps():
+    # Sec. 4.3: alpha near 1/||H - sI||_2 gives a larger scaled margin than the
+    # infinity-norm bound, hence fewer steps (Prop. 3.6), with the same reflector
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 1024, 16
+    spec = workloads.controlled_spectrum(d, k, 1e-2, seed=5)
+    R_ex = oracle.reflector_from_basis(spec.Q, k)
+    out = {}
+    for mode in (rs.AlphaMode.INF, rs.AlphaMode.POWER):
+        R, info, st = _run(rs, torch, spec.H, k, 0.0, rs.Policy.FP16_REFINE, tol=1e-6, alpha_mode=int(mode))
+        assert st == rs.Status.OK
+        assert spec_norm_sym(R - R_ex) <= 1e-6
+        out[mode] = info
+    a_inf, a_pow = out[rs.AlphaMode.INF].alpha, out[rs.AlphaMode.POWER].alpha
+    rho = np.abs(spec.lam).max()
+    assert a_inf * rho <= 1.0 and 1.0 / 1.02 * 0.9 <= a_pow * rho < np.sqrt(3.0)
+    assert a_pow > 5 * a_inf
+    assert out[rs.AlphaMode.POWER].steps_low < out[rs.AlphaMode.INF].steps_low
+
+
+def test_power_alpha_fp64_matches_oracle_definition():
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.split_spectrum_config(seed=0)
+    s = oracle.midpoint(*spec.gap)
+    R_or, _ = oracle.reflector(spec.H, spec.k)
+    R, info, st = _run(rs, torch, spec.H, spec.k, s, rs.Policy.FP64, tol=1e-12, alpha_mode=int(rs.AlphaMode.POWER))
+    assert st == rs.Status.OK
+    assert spec_norm_sym(R - R_or) <= 1e-12
+
+
 @pytest.mark.parametrize("theta", [0.1, 0.9])
 def test_refine_off_midpoint_shift_same_reflector(theta):
     # Prop. 2.1 on the GPU path: shifts inside the gap give the same R
