@@ -102,6 +102,14 @@ typedef struct {
                               NS step: SYRK X^2 plus the symmetric product)           */
   int64_t launches;        /* kernels this call launched                               */
   int64_t workspace_bytes; /* device workspace the call allocated                      */
+  /* automatic shift (s = NaN), Sec. 4.3 / Prop. 4.1-4.2; NaN / 0 otherwise:          */
+  double lam_k_est;        /* Lanczos estimate of lam_k                                */
+  double lam_k1_est;       /* Lanczos estimate of lam_{k+1}                            */
+  double shift_eps;        /* endpoint error bound eps (largest Ritz residual)         */
+  double margin_lb;        /* guaranteed margin m_hat - eps of the chosen shift        */
+  int32_t lanczos_iters;   /* Lanczos steps taken                                      */
+  int32_t steps_pred;      /* NS steps the scalar recurrence predicts for eps_m(gamma) <= tol,
+                              gamma = alpha * margin_lb (Prop. 3.6); -1 when unknown     */
 } rsign_info;
 
 /* Optional knobs; rsign_options_default() fills the defaults. */
@@ -116,6 +124,7 @@ typedef struct {
                                hi/lo pairs (three fused pair products per step, about
                                twice the mantissa bits, one refinement sweep usually
                                suffices); 0 plain operands (default 1)                */
+  int32_t lanczos_max;      /* automatic shift: Lanczos step budget (default 600)      */
 } rsign_options;
 
 void rsign_options_default(rsign_options* opt);

@@ -37,6 +37,16 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
 int32_t rsign_dbg_set_tc_cluster(int32_t cluster);
 
 /*
+ * Host routine of the automatic shift (runs on the CPU, no GPU needed): the
+ * j-th smallest eigenvalue (0-based) of the m x m symmetric tridiagonal with
+ * diagonal alpha[0..m-1] and off-diagonal beta[0..m-2] (Sturm bisection), and
+ * the last component of its unit eigenvector (inverse iteration), which gives
+ * the Lanczos residual bound |beta_m * last|.
+ */
+rsign_status rsign_dbg_tridiag_ritz(const double* alpha, const double* beta, int32_t m, int32_t j,
+                                    double* theta, double* last);
+
+/*
  * FP64 product on the FP64 pipe: out = A * B, all dp x dp row-major FP64,
  * dp a multiple of 64; sym = 1 as above.
  */

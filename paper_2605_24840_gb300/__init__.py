@@ -61,6 +61,8 @@ class Info(ctypes.Structure):
         ("tol_fro", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_low", ctypes.c_double),
         ("ms_fp64", ctypes.c_double), ("flops_low", ctypes.c_double),
         ("launches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+        ("lam_k_est", ctypes.c_double), ("lam_k1_est", ctypes.c_double), ("shift_eps", ctypes.c_double),
+        ("margin_lb", ctypes.c_double), ("lanczos_iters", ctypes.c_int32), ("steps_pred", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -72,7 +74,7 @@ class Options(ctypes.Structure):
         ("max_steps", ctypes.c_int32), ("polish_steps", ctypes.c_int32),
         ("max_sweeps", ctypes.c_int32), ("alpha_mode", ctypes.c_int32),
         ("power_steps", ctypes.c_int32), ("timing", ctypes.c_int32),
-        ("low_split", ctypes.c_int32),
+        ("low_split", ctypes.c_int32), ("lanczos_max", ctypes.c_int32),
     ]
 
 
@@ -135,6 +137,8 @@ def load():
     lib.rsign_dbg_fp64grade_gemm.restype = ctypes.c_int
     lib.rsign_dbg_set_tc_cluster.argtypes = [i32]
     lib.rsign_dbg_set_tc_cluster.restype = i32
+    lib.rsign_dbg_tridiag_ritz.argtypes = [dp, dp, i32, i32, dp, dp]
+    lib.rsign_dbg_tridiag_ritz.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -320,6 +324,19 @@ def dbg_f64_gemm(A, B, sym=0, out=None, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def dbg_tridiag_ritz(alpha, beta, j):
+    """(theta_j, last component) of the symmetric tridiagonal (alpha, beta) -- host routine, no GPU."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    th, la = ctypes.c_double(), ctypes.c_double()
+    p = ctypes.POINTER(ctypes.c_double)
+    st = Status(load().rsign_dbg_tridiag_ritz(a.ctypes.data_as(p), b.ctypes.data_as(p), len(a), int(j),
+                                               ctypes.byref(th), ctypes.byref(la)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return th.value, la.value
 
 
 def dbg_set_tc_cluster(cluster: int) -> int:

@@ -139,6 +139,25 @@ cudaError_t power_alpha(const double* A, int dp, double* x, double* y, int iters
                         cudaStream_t st);
 
 // ---------------------------------------------------------------------------
+// Automatic shift (lanczos.cu).
+// ---------------------------------------------------------------------------
+struct LanczosResult {
+  double lam_k, lam_k1;  // Ritz estimates of lam_k, lam_{k+1}
+  double eps_k, eps_k1;  // their residual bounds (an eigenvalue lies within each)
+  int iters;             // Lanczos steps taken
+  int converged;         // 1 when (lam_k1 - lam_k)/2 > 4 max(eps) was reached
+};
+// Lanczos with full reorthogonalisation on the symmetric dp x dp FP64 A (rows
+// and columns >= d zero) from the spectrum end nearer to k; `work` holds
+// lanczos_work_doubles(dp, max_iter) doubles.
+cudaError_t lanczos_endpoints(const double* A, int dp, int d, int k, int max_iter, double* work,
+                              LanczosResult* out, int64_t* launches, cudaStream_t st);
+size_t lanczos_work_doubles(int dp, int max_iter);
+// Host: j-th smallest eigenvalue (0-based) of the m x m symmetric tridiagonal
+// (diagonal alpha, off-diagonal beta) and the last component of its unit eigenvector.
+void tridiag_ritz(const double* alpha, const double* beta, int m, int j, double* theta, double* last);
+
+// ---------------------------------------------------------------------------
 // FP64-grade products on the FP16 tensor cores (refine.cu).
 // A symmetric FP64 matrix M is split row by row into S digit planes:
 //   M_ik = sigma_i * sum_p d_p(i,k) 2^(-beta (p+1)) + O(sigma_i 2^(-beta S - 1)),

@@ -358,7 +358,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   if (opt.max_steps < 1 || opt.max_steps > 1000 || opt.polish_steps < 0 || opt.max_sweeps < 0)
     return RSIGN_ERR_ARG;
   if (std::isinf(s)) return RSIGN_ERR_ARG;
-  if (std::isnan(s)) return RSIGN_ERR_UNSUPPORTED;  // automatic shift: not in this build
+  const bool auto_shift = std::isnan(s);
   const bool refine = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE;
 
   Ctx c;
@@ -420,6 +420,46 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), st) != cudaSuccess) return fail_cuda();
   double* hist_low = hist;
   double* hist64 = hist + opt.max_steps + 2;
+
+  // ---- automatic shift (Sec. 4.3): Lanczos endpoint estimates of lam_k and
+  // lam_{k+1}, the midpoint (Prop. 4.1), and the margin test m_hat > eps of
+  // Prop. 4.2 (the shift is then admissible with true margin >= m_hat - eps)
+  LanczosResult lr{};
+  double margin_lb = NAN;
+  auto fill_shift_info = [&](rsign_info* inf) {
+    if (!inf || !auto_shift) return;
+    inf->lam_k_est = lr.lam_k;
+    inf->lam_k1_est = lr.lam_k1;
+    inf->shift_eps = std::max(lr.eps_k, lr.eps_k1);
+    inf->margin_lb = margin_lb;
+    inf->lanczos_iters = lr.iters;
+  };
+  if (auto_shift) {
+    if (!c.ok(ingest(Hd, d, dp, 0.0, A64, rowpart, &ctl->flags, st))) return fail_cuda();
+    const int lmax = opt.lanczos_max > 0 ? opt.lanczos_max : 600;
+    double* lw = nullptr;
+    if (mem.alloc((void**)&lw, lanczos_work_doubles(dp, lmax) * 8) != cudaSuccess) return fail_cuda();
+    if (lanczos_endpoints(A64, dp, d, k, lmax, lw, &lr, &c.launches, st) != cudaSuccess) return fail_cuda();
+    if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail_cuda();
+    const double eps = std::max(lr.eps_k, lr.eps_k1);
+    const double m_hat = 0.5 * (lr.lam_k1 - lr.lam_k);
+    s = 0.5 * (lr.lam_k + lr.lam_k1);
+    margin_lb = m_hat - eps;
+    if ((ctl_h.flags & 1) || !std::isfinite(s) || !(m_hat > eps)) {
+      if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->shift = s;
+        info->steps_pred = -1;
+        fill_shift_info(info);
+      }
+      mem.release();
+      cudaStreamSynchronize(st);
+      for (auto& e : ev) if (e) cudaEventDestroy(e);
+      return (ctl_h.flags & 1) ? RSIGN_ERR_ARG : RSIGN_ERR_GAP;
+    }
+  }
 
   // ---- ingest and scaling (Sec. 4.3: alpha = 1/||H - sI||_inf)
   if (!c.ok(ingest(Hd, d, dp, s, A64, rowpart, &ctl->flags, st))) return fail_cuda();
@@ -616,7 +656,19 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     info->cert_ok = (trace_ok && resid_ok) ? 1 : 0;
     info->alpha = alpha;
     info->shift = s;
-    info->gamma_est = NAN;
+    info->gamma_est = auto_shift ? alpha * margin_lb : NAN;
+    info->steps_pred = -1;
+    if (auto_shift && info->gamma_est > 0.0) {
+      // smallest m with eps_m(gamma) <= tol, eps_0 = 1 - gamma, eps_{m+1} = eps_m^2 (3 - eps_m)/2
+      double e = 1.0 - std::min(1.0, info->gamma_est);
+      int m = 0;
+      while (e > tol && m < 10000) {
+        e = 0.5 * e * e * (3.0 - e);
+        ++m;
+      }
+      info->steps_pred = m;
+    }
+    fill_shift_info(info);
     info->resid_fro = resid;
     info->trace = trace;
     info->correction_fro = corr_fro;
@@ -681,6 +733,7 @@ void rsign_options_default(rsign_options* opt) {
   opt->power_steps = 20;
   opt->timing = 1;
   opt->low_split = 1;
+  opt->lanczos_max = 600;
 }
 
 rsign_status rsign_reflector_ex(const double* H, int64_t d, int32_t k, double s, double tol,
@@ -807,6 +860,13 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
 }
 
 int32_t rsign_dbg_set_tc_cluster(int32_t cluster) { return tc_set_default_cluster(cluster); }
+
+rsign_status rsign_dbg_tridiag_ritz(const double* alpha, const double* beta, int32_t m, int32_t j, double* theta,
+                                    double* last) {
+  if (!alpha || (m > 1 && !beta) || !theta || !last || m < 1 || j < 0 || j >= m) return RSIGN_ERR_ARG;
+  tridiag_ritz(alpha, beta, m, j, theta, last);
+  return RSIGN_OK;
+}
 
 rsign_status rsign_dbg_f64_gemm(const double* A, const double* B, int64_t dp, int32_t sym, double* out,
                                 void* stream) {

@@ -85,6 +85,24 @@ def test_argument_errors_need_no_gpu(rs):
     assert lib.rsign_apply(None, 4, H.ctypes.data, 1, R.ctypes.data, None) == rs.Status.ERR_ARG
 
 
+@pytest.mark.parametrize("m,seed", [(1, 0), (2, 1), (7, 2), (60, 3), (200, 4)])
+def test_tridiagonal_ritz_solver_matches_scipy(rs, m, seed):
+    # host part of the automatic shift: eigenvalues (Sturm bisection) and the last
+    # eigenvector components (inverse iteration) of a symmetric tridiagonal
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(m)
+    b = rng.uniform(0.05, 1.0, max(m - 1, 0))
+    if m > 1:
+        w, V = scipy_linalg.eigh_tridiagonal(a, b)
+    else:
+        w, V = a.copy(), np.ones((1, 1))
+    for j in sorted({0, m // 2, m - 1}):
+        th, last = rs.dbg_tridiag_ritz(a, b if m > 1 else np.zeros(1), j)
+        assert th == pytest.approx(w[j], abs=1e-12 * max(1.0, np.abs(w).max()))
+        assert abs(last) == pytest.approx(abs(V[-1, j]), abs=1e-8)
+
+
 def test_binding_rejects_wrong_dtype(rs):
     with pytest.raises(TypeError):
         rs.reflector(np.eye(4, dtype=np.float32), 1, 0.0)

@@ -174,6 +174,54 @@ def test_refine_reaches_1e6(policy, d, k, delta):
     assert info.err_est <= 1e-6
 
 
+def test_auto_shift_plain_method_d256():
+    # s = NaN: Lanczos endpoints, midpoint (Prop. 4.1), margin test (Prop. 4.2)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.split_spectrum_config(seed=0)
+    R_or, lam = oracle.reflector(spec.H, spec.k)
+    R, info, st = _run(rs, torch, spec.H, spec.k, float("nan"), rs.Policy.FP64, tol=1e-12)
+    assert st == rs.Status.OK
+    assert spec_norm_sym(R - R_or) <= 1e-12
+    lk, lk1 = lam[spec.k - 1], lam[spec.k]
+    assert lk < info.shift < lk1
+    # each estimate lies within its bound of the true endpoint, and the certified
+    # margin is a true lower bound (Prop. 4.2)
+    assert abs(info.lam_k_est - lk) <= info.shift_eps + 1e-12
+    assert abs(info.lam_k1_est - lk1) <= info.shift_eps + 1e-12
+    assert 0 < info.margin_lb <= oracle.margin(info.shift, lk, lk1) + 1e-12
+    assert info.lanczos_iters > 0 and info.steps_pred > 0
+
+
+@pytest.mark.parametrize("d,k,delta", [(300, 290, 5e-2), (512, 3, 2e-2)])
+def test_auto_shift_both_spectrum_ends(d, k, delta):
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.controlled_spectrum(d, k, delta, seed=60 + d)
+    R, info, st = _run(rs, torch, spec.H, k, float("nan"), rs.Policy.FP16_REFINE, tol=1e-7)
+    assert st == rs.Status.OK, (st, info.as_dict())
+    assert -delta < info.shift < delta
+    assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, k)) <= 1e-7
+
+
+def test_auto_shift_unresolved_gap_is_reported():
+    # lam_k == lam_{k+1}: no admissible shift exists (Prop. 2.1 needs lam_k < s < lam_{k+1})
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 128, 3
+    rng = np.random.default_rng(1)
+    Q = workloads.haar_orthogonal(d, rng)
+    lam = np.sort(np.concatenate([[-1.0, -0.8, 0.3, 0.3], rng.uniform(0.5, 1.0, d - 4)]))
+    H = (Q * lam) @ Q.T
+    H = 0.5 * (H + H.T)
+    R, info, st = _run(rs, torch, H, k, float("nan"), rs.Policy.FP64)
+    # either the margin test fails (GAP) or, when the Krylov space held only one
+    # copy of the double eigenvalue, the trace certificate rejects the shift
+    assert st in (rs.Status.ERR_GAP, rs.Status.ERR_CERT)
+    if st == rs.Status.ERR_CERT:
+        assert abs(info.trace - (d - 2 * k)) >= 0.5
+
+
 def test_power_alpha_enlarges_margin_and_saves_steps():
     # Sec. 4.3: alpha near 1/||H - sI||_2 gives a larger scaled margin than the
     # infinity-norm bound, hence fewer steps (Prop. 3.6), with the same reflector
