@@ -324,6 +324,31 @@ __global__ void normalize_kernel(double* y, int n, double* x, double* nrm) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i] * inv;
 }
 
+// G = 1/2 G + 1/2 (P1 + P1^T - P2), 32x32 tiles with a transposed read of P1
+__global__ void tangent_combine_f64_kernel(double* __restrict__ G, const double* __restrict__ P1,
+                                           const double* __restrict__ P2, int dp) {
+  __shared__ double t[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) t[r][tx] = P1[(size_t)(bj * 32 + r) * dp + bi * 32 + tx];
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const size_t e = (size_t)(bi * 32 + r) * dp + bj * 32 + tx;
+    G[e] = 0.5 * G[e] + 0.5 * (P1[e] + t[tx][r] - P2[e]);
+  }
+}
+
+__global__ void symmetrize_scale_kernel(const double* __restrict__ S, int dp, double scale,
+                                        double* __restrict__ D) {
+  __shared__ double t[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) t[r][tx] = S[(size_t)(bj * 32 + r) * dp + bi * 32 + tx];
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const size_t e = (size_t)(bi * 32 + r) * dp + bj * 32 + tx;
+    D[e] = 0.5 * scale * (S[e] + t[tx][r]);
+  }
+}
+
 __global__ void init_vec_kernel(double* x, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     x[i] = 1.0 + (i % 7) * 0.125;
@@ -345,6 +370,14 @@ __global__ void copy_unpad_kernel(const double* __restrict__ src, int dp, double
   }
 }
 
+__global__ void copy_pad_kernel(const double* __restrict__ src, int d, double* __restrict__ dst, int dp) {
+  const size_t n = (size_t)dp * dp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / dp, j = e % dp;
+    dst[e] = (i < (size_t)d && j < (size_t)d) ? src[i * d + j] : 0.0;
+  }
+}
+
 int grid_for(size_t n) {
   size_t g = (n + 255) / 256;
   if (g > 8192) g = 8192;
@@ -352,6 +385,11 @@ int grid_for(size_t n) {
 }
 
 }  // namespace
+
+cudaError_t copy_pad(const double* src, int d, double* dst, int dp, cudaStream_t st) {
+  copy_pad_kernel<<<grid_for((size_t)dp * dp), 256, 0, st>>>(src, d, dst, dp);
+  return cudaGetLastError();
+}
 
 int f64_num_tiles(int dp, int sym) { return F64Sched(dp, sym).n; }
 
@@ -442,6 +480,17 @@ cudaError_t gemv_f64(const double* A, int dp, const double* x, double* y, cudaSt
 
 cudaError_t normalize(double* y, int n, double* x, double* nrm, cudaStream_t st) {
   normalize_kernel<<<1, 1024, 0, st>>>(y, n, x, nrm);
+  return cudaGetLastError();
+}
+
+cudaError_t tangent_combine_f64(double* G, const double* P1, const double* P2, int dp, cudaStream_t st) {
+  tangent_combine_f64_kernel<<<dim3(dp / 32, dp / 32), dim3(32, 8), 0, st>>>(G, P1, P2, dp);
+  return cudaGetLastError();
+}
+
+cudaError_t symmetrize_scale(const double* src, int dp, double scale, double* dst, cudaStream_t st) {
+  if (src == dst) return cudaErrorInvalidValue;  // tiles read transposed: out of place only
+  symmetrize_scale_kernel<<<dim3(dp / 32, dp / 32), dim3(32, 8), 0, st>>>(src, dp, scale, dst);
   return cudaGetLastError();
 }
 

@@ -114,8 +114,10 @@ cudaError_t split_to_f64(const void* src, int fmt, size_t n, double* dst, cudaSt
 cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_t st);
 // y = A x for dp x dp FP64 A (row-major), x,y length dp.
 cudaError_t gemv_f64(const double* A, int dp, const double* x, double* y, cudaStream_t st);
-// Copy the leading d x d block of src (ld dp) into dst (ld d), and back.
+// Copy the leading d x d block of src (ld dp) into dst (ld d), and back
+// (copy_pad writes the whole dp x dp destination, zeros outside d x d).
 cudaError_t copy_unpad(const double* src, int dp, double* dst, int d, cudaStream_t st);
+cudaError_t copy_pad(const double* src, int d, double* dst, int dp, cudaStream_t st);
 // Newton-Schulz step check (one block, deterministic): r = sqrt(sum of
 // partials) is stored in hist[m]; if *done == 0 the stop rule is applied:
 //   r < tol_abs                                   (converged), or
@@ -125,6 +127,10 @@ cudaError_t copy_unpad(const double* src, int dp, double* dst, int d, cudaStream
 cudaError_t ns_check(const double* partials, int n, double* hist, int m, double tol_abs,
                      double floor_lo, double floor_hi, double ratio, int* done, int* steps,
                      cudaStream_t st);
+// Adjoint helpers (FP64): G <- 1/2 G + 1/2 (P1 + P1^T - P2) (the transposed
+// Frechet step of X + 1/2 X (I - X^2), P1 = G E, P2 = X G X); dst = scale/2 (src + src^T).
+cudaError_t tangent_combine_f64(double* G, const double* P1, const double* P2, int dp, cudaStream_t st);
+cudaError_t symmetrize_scale(const double* src, int dp, double scale, double* dst, cudaStream_t st);
 // out[0] = sum_{i<d} X[i*dp + i] (FP64 X).
 cudaError_t trace_f64(const double* X, int dp, int d, double* out, cudaStream_t st);
 // Power-iteration helpers: x <- y / ||y||_2, norm stored in *nrm.
@@ -195,6 +201,8 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
 // -> part (one each per 32x32 tile).
 cudaError_t antisym_part(const double* N, int dp, float* C, float* blockmax, double* part,
                          cudaStream_t st);
+// Per-32x32-tile maxima of |M| for an FP32 dp x dp matrix.
+cudaError_t absmax_tiles(const float* M, int dp, float* blockmax, cudaStream_t st);
 // out[0] = max of n floats; out[1] = 2^-ceil(log2 out[0]) (1 if out[0] == 0).
 cudaError_t max_pow2(const float* x, int n, float* out, cudaStream_t st);
 // dst (FP16/BF16) = src * scale[0]   (scale a device float)

@@ -167,6 +167,13 @@ __global__ void ident_minus_kernel(const double* __restrict__ Y, int dp, int d, 
   }
 }
 
+__global__ void absmax_tiles_kernel(const float* __restrict__ M, int dp, float* blockmax) {
+  const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
+  float m = 0.f;
+  for (int r = ty; r < TILE; r += 8) m = fmaxf(m, fabsf(M[(size_t)(bi * TILE + r) * dp + bj * TILE + tx]));
+  tile_max(m, blockmax);
+}
+
 __global__ void max_pow2_kernel(const float* __restrict__ x, int n, float* out) {
   __shared__ float sh[32];
   float m = 0.f;
@@ -336,6 +343,11 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
 cudaError_t antisym_part(const double* N, int dp, float* C, float* blockmax, double* part,
                          cudaStream_t st) {
   antisym_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(N, dp, C, blockmax, part);
+  return cudaGetLastError();
+}
+
+cudaError_t absmax_tiles(const float* M, int dp, float* blockmax, cudaStream_t st) {
+  absmax_tiles_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(M, dp, blockmax);
   return cudaGetLastError();
 }
 

@@ -692,6 +692,270 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   return result;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of R = p_M(alpha (H - sI)) (Eq. NS unrolled M times) with s and alpha
+// held fixed.  The Frechet derivative of f(X) = 3/2 X - 1/2 X^3 at a symmetric
+// X, L_f(X, E) = 3/2 E - 1/2 (E X^2 + X E X + X^2 E), is self-adjoint for the
+// Frobenius inner product, so with G_M = sym(Rbar) the backward sweep is
+//   G_m = L_f(X_m, G_{m+1}) = 1/2 G + 1/2 (G E_m + E_m G) - 1/2 X_m G X_m,
+// E_m = I - X_m^2, and Hbar = alpha sym(G_0) (A = sym(H) - sI).
+// FP64 policy: FP64 products; the forward keeps X every `ckpt_every` steps
+// and each backward segment recomputes its iterates from its checkpoint.
+// Low-precision policies: the stage-1 trajectory (hi/lo for *_REFINE) is kept
+// whole and the sweep uses the FP16/BF16 tangent products of the refinement.
+// ---------------------------------------------------------------------------
+rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rsign_policy policy,
+                           const double* Rbar, double* Hbar, int32_t ckpt_every, cudaStream_t st) {
+  if (!H || !Rbar || !Hbar) return RSIGN_ERR_ARG;
+  if (d64 < 2 || d64 > 16384) return d64 > 16384 ? RSIGN_ERR_UNSUPPORTED : RSIGN_ERR_ARG;
+  if (k < 1 || k > d64 - 1 || !std::isfinite(s)) return RSIGN_ERR_ARG;
+  if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_BF16_REFINE) return RSIGN_ERR_ARG;
+  if (policy == RSIGN_FP16_POLISH || policy == RSIGN_BF16_POLISH) return RSIGN_ERR_UNSUPPORTED;
+  const int ck = ckpt_every > 0 ? ckpt_every : 4;
+  Ctx c;
+  c.st = st;
+  rsign_status dst = check_device(&c.num_sms);
+  if (dst != RSIGN_OK) return dst;
+  const int d = (int)d64, dp = (d + 255) / 256 * 256;
+  const size_t dd = (size_t)dp * dp;
+  const int max_steps = 100;
+  DevBuf mem;
+  mem.st = st;
+  auto fail = [&]() {
+    mem.release();
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    return RSIGN_ERR_CUDA;
+  };
+  Ctl* ctl = nullptr;
+  Ctl h;
+  std::memset(&h, 0, sizeof(h));
+  double *A64 = nullptr, *rowpart = nullptr, *rowsum = nullptr, *partials = nullptr, *hist = nullptr;
+  double *G = nullptr, *Gs = nullptr;
+  const int n_part = std::max(tc_num_tiles(dp, 1), f64_num_tiles(dp, 1)) * 4;
+  if (mem.alloc((void**)&ctl, sizeof(Ctl)) != cudaSuccess || mem.alloc((void**)&A64, dd * 8) != cudaSuccess ||
+      mem.alloc((void**)&rowpart, (size_t)(dp / 32) * dp * 8) != cudaSuccess ||
+      mem.alloc((void**)&rowsum, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc((void**)&partials, (size_t)n_part * 8) != cudaSuccess ||
+      mem.alloc((void**)&hist, (size_t)(max_steps + 2) * 8) != cudaSuccess ||
+      mem.alloc((void**)&G, dd * 8) != cudaSuccess || mem.alloc((void**)&Gs, dd * 8) != cudaSuccess)
+    return fail();
+  // inputs may live on the host
+  const double *Hd = H, *Rb = Rbar;
+  double* Hb = Hbar;
+  if (!is_device_ptr(H)) {
+    double* t = nullptr;
+    if (mem.alloc((void**)&t, (size_t)d * d * 8) != cudaSuccess ||
+        cudaMemcpyAsync(t, H, (size_t)d * d * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return fail();
+    Hd = t;
+  }
+  if (!is_device_ptr(Rbar)) {
+    double* t = nullptr;
+    if (mem.alloc((void**)&t, (size_t)d * d * 8) != cudaSuccess ||
+        cudaMemcpyAsync(t, Rbar, (size_t)d * d * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return fail();
+    Rb = t;
+  }
+  const bool hb_dev = is_device_ptr(Hbar);
+  if (!hb_dev && mem.alloc((void**)&Hb, (size_t)d * d * 8) != cudaSuccess) return fail();
+  if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), st) != cudaSuccess) return fail();
+  if (!c.ok(ingest(Hd, d, dp, s, A64, rowpart, &ctl->flags, st)) ||
+      !c.ok(inf_norm_finish(rowpart, dp, rowsum, ctl->scal, st)))
+    return fail();
+  if (cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail();
+  const double alpha = h.scal[1];
+  if ((h.flags & 1) || !(alpha > 0.0)) {
+    mem.release();
+    cudaStreamSynchronize(st);
+    return RSIGN_ERR_ARG;
+  }
+  // G_M = sym(Rbar), zero padded
+  if (!c.ok(copy_pad(Rb, d, Gs, dp, st)) || !c.ok(symmetrize_scale(Gs, dp, 1.0, G, st))) return fail();
+  const int nt64 = f64_num_tiles(dp, 1);
+  const double tol_fro = 16.0 * d * 2.220446049250313e-16;
+
+  if (policy == RSIGN_FP64) {
+    // -------- forward: Newton-Schulz to convergence, checkpoints every ck steps
+    double *xb[2] = {nullptr, nullptr}, *E = nullptr;
+    if (mem.alloc((void**)&xb[0], dd * 8) != cudaSuccess || mem.alloc((void**)&xb[1], dd * 8) != cudaSuccess ||
+        mem.alloc((void**)&E, dd * 8) != cudaSuccess)
+      return fail();
+    std::vector<double*> ckpt;
+    auto checkpoint = [&](int j, const double* src) -> bool {
+      while ((int)ckpt.size() <= j) {
+        double* p = nullptr;
+        if (mem.alloc((void**)&p, dd * 8) != cudaSuccess) return false;
+        ckpt.push_back(p);
+      }
+      return cudaMemcpyAsync(ckpt[j], src, dd * 8, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    };
+    if (!c.ok(scale_convert(A64, dd, ctl->scal + 1, 1.0, xb[0], 2, st)) || !checkpoint(0, xb[0])) return fail();
+    int M = max_steps;
+    for (int m = 0; m <= max_steps; ++m) {
+      F64GemmArgs sy{};
+      sy.dp = dp; sy.d_real = d; sy.sym = 1; sy.epi = F64_EPI_NS_SYRK;
+      sy.A = xb[m & 1]; sy.B = xb[m & 1]; sy.out = E; sy.partials = partials;
+      if (!c.ok(f64_gemm(sy, st)) ||
+          !c.ok(ns_check(partials, nt64 * 4, hist, m, tol_fro, -1.0, -1.0, 0.0, &ctl->done64, &ctl->steps64, st)))
+        return fail();
+      if (cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return fail();
+      if (h.done64 || m == max_steps) {
+        M = m;
+        break;
+      }
+      F64GemmArgs up{};
+      up.dp = dp; up.d_real = d; up.sym = 1; up.epi = F64_EPI_NS_UPDATE;
+      up.A = xb[m & 1]; up.B = E; up.xin = xb[m & 1]; up.out = xb[(m + 1) & 1]; up.partials = partials;
+      if (!c.ok(f64_gemm(up, st))) return fail();
+      if ((m + 1) % ck == 0 && !checkpoint((m + 1) / ck, xb[(m + 1) & 1])) return fail();
+    }
+    // -------- backward over segments [c0, c1), iterates recomputed from checkpoints
+    std::vector<double*> segX(ck, nullptr), segE(ck, nullptr);
+    for (int q = 0; q < ck; ++q)
+      if (mem.alloc((void**)&segX[q], dd * 8) != cudaSuccess || mem.alloc((void**)&segE[q], dd * 8) != cudaSuccess)
+        return fail();
+    double *P1 = nullptr, *Q = nullptr, *P2 = nullptr;
+    if (mem.alloc((void**)&P1, dd * 8) != cudaSuccess || mem.alloc((void**)&Q, dd * 8) != cudaSuccess ||
+        mem.alloc((void**)&P2, dd * 8) != cudaSuccess)
+      return fail();
+    const int nseg = (M + ck - 1) / ck;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int c0 = seg * ck, c1 = std::min(c0 + ck, M);
+      if (cudaMemcpyAsync(segX[0], ckpt[seg], dd * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return fail();
+      for (int m = c0; m < c1; ++m) {
+        const int q = m - c0;
+        F64GemmArgs sy{};
+        sy.dp = dp; sy.d_real = d; sy.sym = 1; sy.epi = F64_EPI_NS_SYRK;
+        sy.A = segX[q]; sy.B = segX[q]; sy.out = segE[q]; sy.partials = partials;
+        if (!c.ok(f64_gemm(sy, st))) return fail();
+        if (m + 1 < c1) {
+          F64GemmArgs up{};
+          up.dp = dp; up.d_real = d; up.sym = 1; up.epi = F64_EPI_NS_UPDATE;
+          up.A = segX[q]; up.B = segE[q]; up.xin = segX[q]; up.out = segX[q + 1]; up.partials = partials;
+          if (!c.ok(f64_gemm(up, st))) return fail();
+        }
+      }
+      for (int m = c1 - 1; m >= c0; --m) {
+        const int q = m - c0;
+        F64GemmArgs g1{};
+        g1.dp = dp; g1.d_real = d; g1.sym = 0; g1.epi = F64_EPI_STORE; g1.scale = 1.0;
+        g1.A = G; g1.B = segE[q]; g1.out = P1;                      // G E_m
+        F64GemmArgs g2 = g1;
+        g2.A = segX[q]; g2.B = G; g2.out = Q;                       // X_m G
+        F64GemmArgs g3 = g1;
+        g3.sym = 1; g3.A = Q; g3.B = segX[q]; g3.out = P2;          // X_m G X_m (symmetric)
+        if (!c.ok(f64_gemm(g1, st)) || !c.ok(f64_gemm(g2, st)) || !c.ok(f64_gemm(g3, st)) ||
+            !c.ok(tangent_combine_f64(G, P1, P2, dp, st)))
+          return fail();
+      }
+    }
+  } else {
+    // -------- low precision: the stage-1 trajectory kept whole, tangent products in FP16/BF16
+    const int fmt = lp_fmt_of(policy);
+    const bool split = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE;
+    const int planes = split ? 2 : 1;
+    std::vector<void*> xs, es;
+    auto slot = [&](std::vector<void*>& v, int m) -> void* {
+      while ((int)v.size() <= m) {
+        void* p = nullptr;
+        if (mem.alloc(&p, dd * 2 * planes) != cudaSuccess) return nullptr;
+        v.push_back(p);
+      }
+      return v[m];
+    };
+    if (!slot(xs, 0)) return fail();
+    if (split) {
+      if (!c.ok(scale_convert_split(A64, dd, ctl->scal + 1, xs[0], fmt, st))) return fail();
+    } else if (!c.ok(scale_convert(A64, dd, ctl->scal + 1, 1.0, xs[0], fmt, st))) {
+      return fail();
+    }
+    const double u = split ? 4.0 * unit_roundoff(fmt) * unit_roundoff(fmt) : unit_roundoff(fmt);
+    const int nt = tc_num_tiles(dp, 1);
+    int M = max_steps;
+    for (int m = 0; m <= max_steps; ++m) {
+      void* xm = slot(xs, m);
+      void* em = slot(es, m);
+      if (!xm || !em) return fail();
+      TcGemmArgs sy{};
+      sy.dp = dp; sy.d_real = d; sy.sym = 1; sy.epi = TC_EPI_NS_SYRK; sy.n_groups = 1;
+      sy.group_start[0] = 0; sy.pair_a[0] = 0; sy.pair_b[0] = 0;
+      if (split) {
+        sy.pair_a[1] = 0; sy.pair_b[1] = 1; sy.pair_a[2] = 1; sy.pair_b[2] = 0; sy.group_start[1] = 3;
+      } else {
+        sy.group_start[1] = 1;
+      }
+      sy.split = split ? 1 : 0; sy.group_scale[0] = 1.0; sy.scale = 1.0f; sy.out = em; sy.partials = partials;
+      sy.status = &ctl->status;
+      if (!c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st)) ||
+          !c.ok(ns_check(partials, nt * 4, hist, m, 0.0, 2.0 * u * std::sqrt((double)d), 16.0 * u * std::sqrt((double)d),
+                         0.5, &ctl->done_low, &ctl->steps_low, st)))
+        return fail();
+      if (cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return fail();
+      if (h.status != 0) {
+        mem.release();
+        cudaStreamSynchronize(st);
+        return (rsign_status)h.status;
+      }
+      if (h.done_low || m == max_steps) {
+        M = m;
+        break;
+      }
+      void* xn = slot(xs, m + 1);
+      if (!xn) return fail();
+      TcGemmArgs up = sy;
+      up.epi = TC_EPI_NS_UPDATE; up.out = xn; up.xin = xm;
+      if (!c.ok(tc_gemm(up, xm, planes, em, planes, fmt, c.num_sms, st))) return fail();
+    }
+    // backward tangent sweep in the operand type (hi planes), FP32 master G
+    const int ntile = (dp / 32) * (dp / 32);
+    float *G32 = nullptr, *P32 = nullptr, *Q32 = nullptr, *bmax = nullptr, *fs = nullptr;
+    void *Glp = nullptr, *Qlp = nullptr;
+    if (mem.alloc((void**)&G32, dd * 4) != cudaSuccess || mem.alloc((void**)&P32, dd * 4) != cudaSuccess ||
+        mem.alloc((void**)&Q32, dd * 4) != cudaSuccess || mem.alloc(&Glp, dd * 2) != cudaSuccess ||
+        mem.alloc(&Qlp, dd * 2) != cudaSuccess || mem.alloc((void**)&bmax, (size_t)ntile * 4) != cudaSuccess ||
+        mem.alloc((void**)&fs, 16 * 4) != cudaSuccess)
+      return fail();
+    auto tc = [&](const void* Aop, const void* Bop, int sym, int epi, void* out) {
+      TcGemmArgs a{};
+      a.dp = dp; a.d_real = d; a.sym = sym; a.epi = epi; a.n_groups = 1;
+      a.group_start[0] = 0; a.group_start[1] = 1; a.pair_a[0] = 0; a.pair_b[0] = 0;
+      a.group_scale[0] = 1.0; a.scale = 1.0f; a.out = out; a.status = &ctl->status;
+      return tc_gemm(a, Aop, 1, Bop, 1, fmt, c.num_sms, st);
+    };
+    if (!c.ok(scale_convert(G, dd, nullptr, 1.0, G32, 3, st))) return fail();
+    if (!c.ok(absmax_tiles(G32, dp, bmax, st)) || !c.ok(max_pow2(bmax, ntile, fs + 4, st))) return fail();
+    for (int m = M - 1; m >= 0; --m) {
+      if (!c.ok(scale_to_lp(G32, dd, fs + 5, Glp, fmt, st))) return fail();
+      if (!c.ok(tc(Glp, es[m], 0, TC_EPI_STORE_F32, P32))) return fail();     // G E_m
+      if (!c.ok(tc(xs[m], Glp, 0, TC_EPI_STORE_LP, Qlp))) return fail();      // X_m G
+      if (!c.ok(tc(Qlp, xs[m], 1, TC_EPI_STORE_F32, Q32))) return fail();     // X_m G X_m
+      if (!c.ok(tangent_combine(G32, P32, Q32, dp, fs + 5, bmax, st))) return fail();
+      if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return fail();
+    }
+    if (!c.ok(to_f64(G32, 3, dd, G, st))) return fail();
+  }
+  // Hbar = alpha sym(G_0), unpadded
+  if (!c.ok(symmetrize_scale(G, dp, alpha, Gs, st)) || !c.ok(copy_unpad(Gs, dp, Hb, d, st))) return fail();
+  if (!hb_dev && cudaMemcpyAsync(Hbar, Hb, (size_t)d * d * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return fail();
+  if (cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail();
+  mem.release();
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return RSIGN_ERR_CUDA;
+  }
+  return h.status != 0 ? (rsign_status)h.status : RSIGN_OK;
+}
+
 // out = R V, FP64; one warp per row of R, 8 columns of V per pass.
 __global__ void apply_kernel(const double* __restrict__ R, int64_t d, const double* __restrict__ V,
                              int64_t nv, double* __restrict__ out) {
@@ -805,9 +1069,7 @@ rsign_status rsign_reflector_batched(int32_t n, const double* const* H, const in
 rsign_status rsign_reflector_backward(const double* H, int64_t d, int32_t k, double s,
                                       rsign_policy policy, const double* Rbar, double* Hbar,
                                       int32_t ckpt_every, void* stream) {
-  (void)H; (void)d; (void)k; (void)s; (void)policy; (void)Rbar; (void)Hbar; (void)ckpt_every;
-  (void)stream;
-  return RSIGN_ERR_UNSUPPORTED;
+  return backward_impl(H, d, k, s, policy, Rbar, Hbar, ckpt_every, (cudaStream_t)stream);
 }
 
 const char* rsign_status_str(rsign_status st) {
