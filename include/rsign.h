@@ -90,9 +90,11 @@ typedef struct {
                               returned R is one quadratically convergent step further) */
   double trace;            /* trace(R)                                                 */
   double correction_fro;   /* ||last refinement correction||_F (REFINE policies)       */
-  double commutator_fro;   /* ||R A - A R||_F, A = H - sI, at the last check (REFINE)  */
+  double commutator_norm;  /* estimate of ||R A - A R||_2, A = H - sI, at the last
+                              a-posteriori check (REFINE): 2 ||G||_2 from FP64 power
+                              steps on v -> 1/2 R (R A v - A R v); NaN otherwise       */
   double err_est;          /* a-posteriori estimate of ||R - sign(H - sI)||_2 (REFINE):
-                              1.5 kappa ||alpha G||_2, G = 1/4 (R C + (R C)^T), kappa the
+                              1.5 kappa alpha ||G||_2, G = 1/2 R (R A - A R), kappa the
                               gain of the last tangent solve; NaN for other policies   */
   double tol_fro;          /* the residual threshold applied: max(tol, 16 d u_64)      */
   double ms_total;         /* device time of the call, ms (CUDA events on `stream`)    */

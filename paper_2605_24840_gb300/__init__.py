@@ -56,7 +56,7 @@ class Info(ctypes.Structure):
         ("sweeps_refine", ctypes.c_int32), ("cert_ok", ctypes.c_int32),
         ("alpha", ctypes.c_double), ("shift", ctypes.c_double), ("gamma_est", ctypes.c_double),
         ("resid_fro", ctypes.c_double), ("trace", ctypes.c_double),
-        ("correction_fro", ctypes.c_double), ("commutator_fro", ctypes.c_double),
+        ("correction_fro", ctypes.c_double), ("commutator_norm", ctypes.c_double),
         ("err_est", ctypes.c_double),
         ("tol_fro", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_low", ctypes.c_double),
         ("ms_fp64", ctypes.c_double), ("flops_low", ctypes.c_double),

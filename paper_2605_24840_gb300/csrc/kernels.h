@@ -229,6 +229,13 @@ cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockm
 // v, w: dp-float work vectors.
 cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
                               cudaStream_t st);
+// Matrix-free estimate of ||G||_2, G = 1/2 R C, C = R A - A R (FP64 A, R):
+// power steps on v -> 1/2 R (R (A v) - A (R v)), five FP64 GEMVs per step; the
+// commutator action is formed from FP64 matrix-vector products, accurate to
+// ~1e-16 relative per term, so no FP64-grade matrix product is needed.
+// work: 6 dp doubles; result -> *out (device double).
+cudaError_t commutator_gain_norm(const double* A, const double* R, int dp, int d, int iters, double* work,
+                                 double* out, cudaStream_t st);
 // R += 1/2 P / sigma (P FP32 symmetric product R_lp Et_lp).
 cudaError_t polish_update(double* R, const float* P, int dp, const float* sigma, cudaStream_t st);
 

@@ -193,7 +193,7 @@ extern "C" rsign_status rsign_reflector_noalloc(const double* H, int64_t d64, in
     info->resid_fro = resid;
     info->trace = trace;
     info->correction_fro = NAN;
-    info->commutator_fro = NAN;
+    info->commutator_norm = NAN;
     info->err_est = NAN;
     info->tol_fro = tol_fro;
     info->launches = 6 + 3 * (int64_t)m;

@@ -277,6 +277,35 @@ __global__ void power_normalize_kernel(const float* __restrict__ w, int n, float
   if (threadIdx.x == 0) *out = first ? nw / sqrt(tot0) : nw;
 }
 
+// y = A x (FP64), one warp per row, two matrices at once: y1 = M1 x1, y2 = M2 x2
+__global__ void gemv2_f64_kernel(const double* __restrict__ M1, const double* __restrict__ x1,
+                                 double* __restrict__ y1, const double* __restrict__ M2,
+                                 const double* __restrict__ x2, double* __restrict__ y2, int dp) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= 2 * dp) return;
+  const bool second = row >= dp;
+  const int r = second ? row - dp : row;
+  const double* m = (second ? M2 : M1) + (size_t)r * dp;
+  const double* x = second ? x2 : x1;
+  double s = 0.0;
+  for (int j = lane; j < dp; j += 32) s += m[j] * x[j];
+  s = warp_sum(s);
+  if (lane == 0) (second ? y2 : y1)[r] = s;
+}
+
+__global__ void scale_scalar_kernel(double* x, double f) { x[0] *= f; }
+
+__global__ void diff_kernel(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c,
+                            int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c[i] = a[i] - b[i];
+}
+
+__global__ void start_vec_f64_kernel(double* y, int d, int dp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < dp; i += gridDim.x * blockDim.x)
+    y[i] = (i < d) ? 1.0 + (i % 7) * 0.125 : 0.0;
+}
+
 dim3 tiles_of(int dp) { return dim3(dp / TILE, dp / TILE); }
 int grid_for(size_t n) {
   size_t g = (n + 255) / 256;
@@ -392,6 +421,30 @@ cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int it
     gemv_f32_kernel<<<(dp + 7) / 8, 256, 0, st>>>(M, dp, v, w, it == 0 ? 1 : 0);
     power_normalize_kernel<<<1, 1024, 0, st>>>(w, dp, v, out, it == 0 ? 1 : 0);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t commutator_gain_norm(const double* A, const double* R, int dp, int d, int iters, double* work,
+                                 double* out, cudaStream_t st) {
+  double* v = work;           // current unit vector
+  double* t1 = work + dp;     // A v
+  double* t2 = work + 2 * dp; // R v
+  double* y1 = work + 3 * dp; // R A v
+  double* y2 = work + 4 * dp; // A R v
+  double* w = work + 5 * dp;  // C v, then R C v
+  const int blocks2 = (2 * dp + 7) / 8;
+  start_vec_f64_kernel<<<(dp + 255) / 256, 256, 0, st>>>(w, d, dp);
+  cudaError_t e = normalize(w, dp, v, out, st);
+  if (e != cudaSuccess) return e;
+  for (int it = 0; it < iters; ++it) {
+    gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(A, v, t1, R, v, t2, dp);      // A v, R v
+    gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(R, t1, y1, A, t2, y2, dp);    // R A v, A R v
+    diff_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y1, y2, t1, dp);           // C v
+    if ((e = gemv_f64(R, dp, t1, w, st)) != cudaSuccess) return e;          // R C v
+    if ((e = normalize(w, dp, v, out, st)) != cudaSuccess) return e;        // ||R C v|| (v unit)
+  }
+  // *out = ||R C v_prev|| = 2 ||G v_prev||: halve it
+  scale_scalar_kernel<<<1, 1, 0, st>>>(out, 0.5);
   return cudaGetLastError();
 }
 

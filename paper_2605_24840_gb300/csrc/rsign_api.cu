@@ -280,19 +280,39 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   // kappa * ||alpha G||_2 with kappa = ||E||_2 / ||E_0||_2 measured on the
   // previous tangent solve (the gain of L_sign on the error directions),
   // times a safety factor of 1.5 (measured: the unscaled estimate exceeds the
-  // true error by 1.2x to 3x at errors of 1e-7 .. 1e-6).  The commutator that
-  // feeds the estimate is the first step of the next sweep, so a passed test
-  // costs one FP64-grade product and no tangent recursion.
+  // true error by 1.2x to 3x at errors of 1e-7 .. 1e-6).  ||G||_2 is taken
+  // matrix free: to first order G = 1/2 R C, and C v = R (A v) - A (R v) needs
+  // only FP64 matrix-vector products, so a passed test costs a few GEMV sweeps
+  // over A and R instead of an FP64-grade matrix product.
   float *pv = nullptr, *pw = nullptr;
   RS_TRY(mem.alloc((void**)&pv, (size_t)dp * 4));
   RS_TRY(mem.alloc((void**)&pw, (size_t)dp * 4));
   constexpr int kPowerIters = 24;
+  constexpr int kCheckIters = 12;
+  double* cwork = nullptr;
+  RS_TRY(mem.alloc((void**)&cwork, (size_t)6 * dp * 8));
   double kappa = NAN;
   for (int sw = 0; sw <= in.max_sweeps; ++sw) {
+    if (sw >= 1) {
+      // a-posteriori check of the current R (matrix free, FP64 GEMVs):
+      // err ~ 1.5 kappa alpha ||G||_2 with kappa the gain of the last tangent solve
+      if (!c.ok(commutator_gain_norm(in.A64, in.R64, dp, d, kCheckIters, cwork, red + 9, st))) return c.err;
+      c.launches += 5 * kCheckIters + 2;
+      RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
+      RS_TRY(cudaStreamSynchronize(st));
+      const double g2 = h_red[9];
+      o->comm = 2.0 * g2;  // ||R A - A R||_2 = 2 ||G||_2 for an orthogonal R
+      o->err_est = 1.5 * kappa * in.alpha * g2;
+      if (!(g2 > 0.0) || o->err_est <= in.tol) {
+        o->converged = true;
+        break;
+      }
+      if (sw == in.max_sweeps) break;
+    }
     // commutator C = R A - A R from the FP64-grade product N = R A
     if (!c.ok(split_rows(in.R64, dp, Rs, st))) return c.err;
     // the first sweep only needs the commutator to ~1e-4 of its (large) size:
-    // 6 levels; the a-posteriori check and later sweeps use all 7
+    // 6 levels; later sweeps use all 7
     if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st, sw == 0 ? kSlices - 1 : kSlices)))
       return c.err;
     if (!c.ok(antisym_part(N64, dp, C32, bmax, part, st))) return c.err;
@@ -304,22 +324,8 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     if (!c.ok(tc(Rlp, Clp, 0, 0, TC_EPI_STORE_F32, P32))) return c.err;
     if (!c.ok(newton_direction(P32, dp, fs + 3, in.alpha, E32, bmax, st))) return c.err;
     if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return c.err;
-    if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 6, st))) return c.err;
+    if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 6, st))) return c.err;  // ||E_0||_2
     c.launches += 2 * kPowerIters - 1;
-    RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
-    RS_TRY(cudaStreamSynchronize(st));
-    o->comm = h_red[5];
-    const double e0 = h_red[6];
-    if (sw >= 1) {
-      kappa = (h_red[8] > 0.0) ? h_red[7] / h_red[8] : 1.0;
-      o->err_est = 1.5 * kappa * e0;
-      if (!(e0 > 0.0) || o->err_est <= in.tol) {
-        o->converged = true;
-        break;
-      }
-    }
-    if (sw == in.max_sweeps) break;
-    RS_TRY(cudaMemcpyAsync(red + 8, red + 6, sizeof(double), cudaMemcpyDeviceToDevice, st));
     // tangent recursion along the stored iterates
     for (int m = 0; m < in.M; ++m) {
       if (!c.ok(scale_to_lp(E32, dd, fs + 5, Elp, in.fmt, st))) return c.err;
@@ -339,6 +345,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     o->sweeps = sw + 1;
     o->resid = h_red[1];
     o->corr = h_red[3];
+    kappa = (h_red[6] > 0.0) ? h_red[7] / h_red[6] : 1.0;  // gain ||E||_2 / ||E_0||_2 of this solve
   }
 #undef RS_TRY
   return cudaSuccess;
@@ -379,7 +386,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   Ctl ctl_h;
   std::memset(&ctl_h, 0, sizeof(ctl_h));
   int steps_low = 0, steps64 = 0, sweeps_done = 0;
-  double corr_fro = NAN, comm_fro = NAN, err_est = NAN;
+  double corr_fro = NAN, comm_norm = NAN, err_est = NAN;
   bool conv64 = true;
   double resid = NAN;
   std::vector<double> hist_h;
@@ -605,7 +612,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       steps64 = ro.polish_steps;
       resid = ro.resid;
       corr_fro = ro.corr;
-      comm_fro = ro.comm;
+      comm_norm = ro.comm;
       err_est = ro.err_est;
       if (!ro.converged && result == RSIGN_OK) result = RSIGN_ERR_NOCONV;
     }
@@ -672,7 +679,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     info->resid_fro = resid;
     info->trace = trace;
     info->correction_fro = corr_fro;
-    info->commutator_fro = comm_fro;
+    info->commutator_norm = comm_norm;
     info->err_est = err_est;
     info->tol_fro = tol_fro;
     if (opt.timing) {
