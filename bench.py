@@ -62,6 +62,15 @@ def dist_env():
     return ws, rank, local
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per stage-1
+# tcgen05 launch, mean over the SYRK and symmetric-update launches of one call,
+# from the ncu launch list summarised in
+# profiles/refine_fp16_d8192_launch_list.md (same kernel source and workload).
+# Algorithmic bytes of one launch: read X (hi + lo, 4 d^2) and write the result
+# (hi + lo, 4 d^2) = 8 d^2 = 0.54 GB at d = 8192.
+MEASURED_TRAFFIC = {(8192, "FP16_REFINE", 1): 2.645e9}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -300,8 +309,9 @@ def run_rsign(args):
     peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
     # the hi/lo stage-1 representation issues three pair products per launch
     issued_mult = 3.0 if (policy in (rs.Policy.FP16_REFINE, rs.Policy.BF16_REFINE) and opt.low_split) else 1.0
+    traffic = MEASURED_TRAFFIC.get((args.d, args.policy, int(opt.low_split)))
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": traffic, "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
             "kernel": "tc_gemm_kernel NS SYRK / symmetric update (stage 1, FP16, 128x256 tiles)",
             "peak_kind": "%s bf16 sustained (FP16 has the same nominal dense rate)" % pk_kind,
             "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_ms,
