@@ -112,6 +112,11 @@ typedef struct {
   int32_t lanczos_iters;   /* Lanczos steps taken                                      */
   int32_t steps_pred;      /* NS steps the scalar recurrence predicts for eps_m(gamma) <= tol,
                               gamma = alpha * margin_lb (Prop. 3.6); -1 when unknown     */
+  /* batched calls (rsign_reflector_batched[_ex]); 0 for single calls:                */
+  int32_t batch_grouped;   /* 1: the matrix went through the grouped launches          */
+  int32_t batch_tile;      /* tile width of the grouped tensor-core launches (128 or
+                              256; 64 = FP64 tiles only); the ms_* fields of a grouped
+                              matrix are those of the whole batch                      */
 } rsign_info;
 
 /* Optional knobs; rsign_options_default() fills the defaults. */
@@ -127,6 +132,12 @@ typedef struct {
                                twice the mantissa bits, one refinement sweep usually
                                suffices); 0 plain operands (default 1)                */
   int32_t lanczos_max;      /* automatic shift: Lanczos step budget (default 600)      */
+  int32_t batch_graphs;     /* batched calls: 1 replays each chunk of grouped NS steps
+                               as one CUDA graph (default 1); 0 launches eagerly       */
+  int32_t batch_tile;       /* batched calls: tile width of the grouped tensor-core
+                               launches, 128 or 256; 0 lets the autotuner time both
+                               widths (and two tile orders) on the batch's first step
+                               and cache the choice per batch shape (default 0)        */
 } rsign_options;
 
 void rsign_options_default(rsign_options* opt);
@@ -167,13 +178,34 @@ rsign_status rsign_apply(const double* R, int64_t d, const double* V, int64_t nv
 /*
  * rsign_reflector_batched -- n independent reflectors R_i = sign(H_i - s_i I)
  * (the batched regime of Sec. 4.5).  Arrays H, d, k, s, R, infos have n
- * entries; H[i] and R[i] are d[i] x d[i].  s[i] = NaN requests the automatic
- * shift for that matrix.  Returns the first non-OK status (all are attempted).
+ * entries; H[i] and R[i] are d[i] x d[i] (device or host memory, each on its
+ * own).  Returns the first non-OK status in index order (all are attempted);
+ * infos[i] holds each matrix's own status-relevant report.
+ *   Grouped path: every matrix with d[i] <= 1024, a finite s[i] and a
+ *   policy among FP64, FP16, BF16, FP16_POLISH, BF16_POLISH is placed in a
+ *   Dmax x Dmax slot of one slab and the whole group advances together: each
+ *   Newton-Schulz step is one grouped tensor-core (or FP64) launch for the
+ *   squares of all unconverged matrices, one stop-test launch and one
+ *   grouped launch for the updates; a matrix whose residual stops
+ *   decreasing (its own stop test, the same as rsign_reflector's) retires
+ *   and its tiles are skipped from then on.  Chunks of eight steps are
+ *   replayed as one CUDA graph.  alpha_i is the Gershgorin bound of each
+ *   matrix (Sec. 4.3).  Each matrix gets the same result as its own
+ *   rsign_reflector call with the same policy and RSIGN_ALPHA_INF.
+ *   Other matrices (s[i] = NaN for the automatic shift, REFINE policies,
+ *   d[i] > 1024) are computed one by one with rsign_reflector_ex.
  */
 rsign_status rsign_reflector_batched(int32_t n, const double* const* H, const int64_t* d,
                                      const int32_t* k, const double* s, double tol,
                                      rsign_policy policy, double* const* R, rsign_info* infos,
                                      void* stream);
+
+/* Same as rsign_reflector_batched with explicit options (NULL = defaults);
+ * alpha_mode is ignored by the grouped path (Gershgorin alpha). */
+rsign_status rsign_reflector_batched_ex(int32_t n, const double* const* H, const int64_t* d,
+                                        const int32_t* k, const double* s, double tol,
+                                        rsign_policy policy, const rsign_options* opt,
+                                        double* const* R, rsign_info* infos, void* stream);
 
 /*
  * rsign_reflector_backward -- adjoint of R = p_m(alpha (H - sI)) (Eq. NS

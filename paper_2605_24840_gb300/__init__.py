@@ -63,6 +63,7 @@ class Info(ctypes.Structure):
         ("launches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
         ("lam_k_est", ctypes.c_double), ("lam_k1_est", ctypes.c_double), ("shift_eps", ctypes.c_double),
         ("margin_lb", ctypes.c_double), ("lanczos_iters", ctypes.c_int32), ("steps_pred", ctypes.c_int32),
+        ("batch_grouped", ctypes.c_int32), ("batch_tile", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -75,6 +76,7 @@ class Options(ctypes.Structure):
         ("max_sweeps", ctypes.c_int32), ("alpha_mode", ctypes.c_int32),
         ("power_steps", ctypes.c_int32), ("timing", ctypes.c_int32),
         ("low_split", ctypes.c_int32), ("lanczos_max", ctypes.c_int32),
+        ("batch_graphs", ctypes.c_int32), ("batch_tile", ctypes.c_int32),
     ]
 
 
@@ -121,6 +123,10 @@ def load():
                                             ctypes.POINTER(dbl), dbl, ctypes.c_int, ctypes.POINTER(vp),
                                             ctypes.POINTER(Info), vp]
     lib.rsign_reflector_batched.restype = ctypes.c_int
+    lib.rsign_reflector_batched_ex.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                               ctypes.POINTER(dbl), dbl, ctypes.c_int, ctypes.POINTER(Options),
+                                               ctypes.POINTER(vp), ctypes.POINTER(Info), vp]
+    lib.rsign_reflector_batched_ex.restype = ctypes.c_int
     lib.rsign_reflector_backward.argtypes = [vp, i64, i32, dbl, ctypes.c_int, vp, vp, i32, vp]
     lib.rsign_reflector_backward.restype = ctypes.c_int
     lib.rsign_status_str.argtypes = [ctypes.c_int]
@@ -255,8 +261,12 @@ def apply(R, V, out=None, stream=None):
     return out
 
 
-def reflector_batched(Hs, ks, ss, tol=1e-12, policy=Policy.FP64, outs=None, stream=None):
-    """Independent reflectors for a list of matrices (rsign_reflector_batched)."""
+def reflector_batched(Hs, ks, ss, tol=1e-12, policy=Policy.FP64, outs=None, options=None, stream=None):
+    """Independent reflectors for a list of matrices (rsign_reflector_batched_ex).
+
+    Returns (outs, infos, status); status is the first non-OK status in index
+    order, infos[i].batch_grouped tells whether matrix i went through the
+    grouped launches."""
     lib = load()
     n = len(Hs)
     outs = outs if outs is not None else [_like(H, H.shape) for H in Hs]
@@ -276,8 +286,9 @@ def reflector_batched(Hs, ks, ss, tol=1e-12, policy=Policy.FP64, outs=None, stre
         hp[i], rp[i], dd[i], kk[i] = p, q, d, int(ks[i])
         sv[i] = float("nan") if ss[i] is None else float(ss[i])
     infos = (Info * n)()
-    st = Status(lib.rsign_reflector_batched(n, hp, dd, kk, sv, float(tol), int(policy), rp, infos,
-                                            _stream_ptr(stream, any_cuda)))
+    optp = ctypes.byref(options) if options is not None else None
+    st = Status(lib.rsign_reflector_batched_ex(n, hp, dd, kk, sv, float(tol), int(policy), optp, rp, infos,
+                                               _stream_ptr(stream, any_cuda)))
     return outs, list(infos), st
 
 

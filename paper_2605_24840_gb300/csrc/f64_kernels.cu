@@ -41,9 +41,25 @@ __global__ void __launch_bounds__(128) f64_gemm_kernel(const F64GemmArgs a) {
   if (a.skip != nullptr && *a.skip != 0) return;
   __shared__ double As[2][FK][FPAD];  // As[k][m]
   __shared__ double Bs[2][FK][FPAD];  // Bs[k][n]
-  const F64Sched sched(a.dp, a.sym);
-  int bi, bj;
-  sched.decode(blockIdx.x, bi, bj);
+  int bi, bj, slot = blockIdx.x, kext = a.dp, d_real = a.d_real;
+  size_t moff = 0;
+  if (a.units != nullptr) {
+    const int4 q = a.units[blockIdx.x];
+    if (a.mat_skip != nullptr && a.mat_skip[q.x] != 0) return;  // uniform per block
+    bi = q.y;
+    bj = q.z;
+    slot = q.w;
+    kext = a.mat_dp[q.x];
+    d_real = a.mat_d[q.x];
+    moff = (size_t)q.x * (size_t)a.mat_stride;
+  } else {
+    const F64Sched sched(a.dp, a.sym);
+    sched.decode(blockIdx.x, bi, bj);
+  }
+  const double* Ap = a.A + moff;
+  const double* Bp = a.B + moff;
+  double* outp = a.out + moff;
+  const double* xinp = a.xin != nullptr ? a.xin + moff : nullptr;
   const int m0 = bi * FT, n0 = bj * FT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 1, wn = warp & 1;
@@ -62,9 +78,9 @@ __global__ void __launch_bounds__(128) f64_gemm_kernel(const F64GemmArgs a) {
     for (int q = 0; q < 8; ++q) {
       const int e = tid + q * 128;          // 0..1023
       const int am = e >> 4, ak = e & 15;   // A: row am, col k0+ak
-      ra[q] = a.A[(size_t)(m0 + am) * ld + k0 + ak];
+      ra[q] = Ap[(size_t)(m0 + am) * ld + k0 + ak];
       const int bk = e >> 6, bn = e & 63;   // B: row k0+bk, col n0+bn
-      rb[q] = a.B[(size_t)(k0 + bk) * ld + n0 + bn];
+      rb[q] = Bp[(size_t)(k0 + bk) * ld + n0 + bn];
     }
   };
   auto sstore = [&](int buf) {
@@ -76,7 +92,7 @@ __global__ void __launch_bounds__(128) f64_gemm_kernel(const F64GemmArgs a) {
     }
   };
 
-  const int nk = a.dp / FK;
+  const int nk = kext / FK;
   gload(0);
   sstore(0);
   __syncthreads();
@@ -113,21 +129,21 @@ __global__ void __launch_bounds__(128) f64_gemm_kernel(const F64GemmArgs a) {
         if constexpr (EPI == F64_EPI_STORE) {
           v *= a.scale;
         } else if constexpr (EPI == F64_EPI_NS_SYRK) {
-          const bool real = i < a.d_real && j < a.d_real;
+          const bool real = i < d_real && j < d_real;
           v = real ? ((i == j ? 1.0 : 0.0) - v) : 0.0;
           if (real && (!a.sym || j >= i)) part += ((a.sym && j > i) ? 2.0 : 1.0) * v * v;
         } else {  // F64_EPI_NS_UPDATE
-          v = a.xin[(size_t)i * ld + j] + 0.5 * v;
-          if (i == j && i < a.d_real) part += v;
+          v = xinp[(size_t)i * ld + j] + 0.5 * v;
+          if (i == j && i < d_real) part += v;
         }
-        if (!a.sym || j >= i) a.out[(size_t)i * ld + j] = v;
-        if (a.sym && j > i) a.out[(size_t)j * ld + i] = v;
+        if (!a.sym || j >= i) outp[(size_t)i * ld + j] = v;
+        if (a.sym && j > i) outp[(size_t)j * ld + i] = v;
       }
     }
   }
   if constexpr (EPI != F64_EPI_STORE) {
     part = warp_sum(part);
-    if (lane == 0) a.partials[(size_t)blockIdx.x * 4 + warp] = part;
+    if (lane == 0) a.partials[(size_t)slot * 4 + warp] = part;
   }
 }
 
@@ -393,8 +409,20 @@ cudaError_t copy_pad(const double* src, int d, double* dst, int dp, cudaStream_t
 
 int f64_num_tiles(int dp, int sym) { return F64Sched(dp, sym).n; }
 
+cudaError_t f64_gemm_grouped(const F64GemmArgs& a, cudaStream_t st) {
+  if (a.dp % FT || a.units == nullptr || a.n_units < 1 || !a.mat_dp || !a.mat_d) return cudaErrorInvalidValue;
+  const int n = a.n_units;
+  switch (a.epi) {
+    case F64_EPI_STORE: f64_gemm_kernel<F64_EPI_STORE><<<n, 128, 0, st>>>(a); break;
+    case F64_EPI_NS_SYRK: f64_gemm_kernel<F64_EPI_NS_SYRK><<<n, 128, 0, st>>>(a); break;
+    case F64_EPI_NS_UPDATE: f64_gemm_kernel<F64_EPI_NS_UPDATE><<<n, 128, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t st) {
-  if (a.dp % FT) return cudaErrorInvalidValue;
+  if (a.dp % FT || a.units != nullptr) return cudaErrorInvalidValue;
   const int n = f64_num_tiles(a.dp, a.sym);
   switch (a.epi) {
     case F64_EPI_STORE: f64_gemm_kernel<F64_EPI_STORE><<<n, 128, 0, st>>>(a); break;

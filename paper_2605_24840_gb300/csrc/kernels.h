@@ -4,7 +4,29 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace rsign {
+
+// ---------------------------------------------------------------------------
+// Runtime helpers shared by the entry points (defined in rsign_api.cu).
+// ---------------------------------------------------------------------------
+// Library-owned stream-ordered pool of the current device (unlimited release
+// threshold: the memory stays mapped between calls), or nullptr.
+cudaMemPool_t library_pool();
+// Workspace of one call: stream-ordered allocations from library_pool(),
+// all released (stream-ordered) by release().
+struct DevBuf {
+  std::vector<void*> ptrs;
+  cudaStream_t st = nullptr;
+  int64_t bytes = 0;
+  cudaError_t alloc(void** p, size_t n);
+  void release();
+};
+bool is_device_ptr(const void* p);
+// RSIGN_OK when the current device is sm_103 (fills the SM count), else an
+// rsign_status error value.
+int check_device(int* num_sms);
 
 // ---------------------------------------------------------------------------
 // Tensor-core GEMM (tcgen05, FP16/BF16 operands, FP32 accumulation in TMEM).
@@ -54,6 +76,16 @@ struct TcGemmArgs {
   const double* b_full;    // FP64 B (dp x dp, symmetric)
   const double* a_diag;
   const double* b_diag;
+  // Grouped mode (tc_gemm_grouped): a batch of matrices, matrix m in slot m of
+  // a slab (A/B slices m * a_planes + pair_a[.], outputs at out + m * mat_stride
+  // elements, each slot dp x dp with leading dimension dp = Dmax).
+  const int4* units;       // device table of (matrix, bm, bn, slot), n_units entries
+  int n_units;
+  const int* mat_dp;       // per matrix: padded order (K extent), a multiple of the tile width
+  const int* mat_d;        // per matrix: logical order
+  const int* mat_skip;     // per matrix: nonzero = converged, its tiles are skipped
+  long long mat_stride;    // elements of the output type between consecutive matrices
+  int a_planes, b_planes;  // slices per matrix in A / B
 };
 
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
@@ -66,6 +98,16 @@ int tc_set_default_cluster(int cl);
 // the operand type; lp_fmt 0 = FP16, 1 = BF16.  dp must be a multiple of 256.
 cudaError_t tc_gemm(const TcGemmArgs& args, const void* A, int a_slices, const void* B,
                     int b_slices, int lp_fmt, int num_sms, cudaStream_t st);
+// Grouped launch over args.units (tile width bn = 128 or 256, no clusters);
+// a_slices / b_slices count all slices of the slab (matrices x planes).
+// The digit-plane epilogue has no grouped form.
+cudaError_t tc_gemm_grouped(const TcGemmArgs& args, int bn, const void* A, int a_slices, const void* B,
+                            int b_slices, int lp_fmt, int num_sms, cudaStream_t st);
+// Tile table of a batch with padded orders dp[0..n) (multiples of bn):
+// order 0 = largest matrices first, 1 = matrix order; slot_begin has n + 1
+// entries (the tiles of matrix m own partial slots slot_begin[m] ..).
+void tc_build_units(int n, const int* dp, int bn, int sym, int order, std::vector<int4>* units,
+                    std::vector<int>* slot_begin);
 
 // ---------------------------------------------------------------------------
 // FP64 kernels (native FP64 pipe, DMMA m8n8k4).
@@ -85,8 +127,19 @@ struct F64GemmArgs {
   const double* xin;
   double* partials;  // one double per (tile, warp): 4 per tile
   const int* skip;   // optional: kernel returns at once when *skip != 0
+  // grouped mode (f64_gemm_grouped): one block per entry of a device table of
+  // (matrix, bi, bj, slot) 64 x 64 tiles; matrix m at A/B/out/xin + m * mat_stride
+  const int4* units;
+  int n_units;
+  const int* mat_dp;
+  const int* mat_d;
+  const int* mat_skip;
+  long long mat_stride;
 };
 int f64_num_tiles(int dp, int sym);
+// Grouped FP64 products over a.units (64 x 64 tiles, dp = slot leading dimension).
+cudaError_t f64_gemm_grouped(const F64GemmArgs& a, cudaStream_t st);
+constexpr int kF64Tile = 64;
 cudaError_t f64_gemm(const F64GemmArgs& a, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

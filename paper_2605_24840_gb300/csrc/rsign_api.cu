@@ -20,17 +20,16 @@
 #include <vector>
 
 namespace rsign {
-namespace {
-
-constexpr int kChunk = 8;  // NS steps enqueued between host checks of the stop flag
 
 // Library-owned stream-ordered memory pool per device.  Its release threshold
 // is unlimited, so the workspace of one call stays mapped for the next call
 // (re-mapping tens of GB per call costs tens of milliseconds);
 // rsign_trim_workspace() returns the cached memory to the driver.
+namespace {
 constexpr int kMaxPoolDevices = 64;
 std::mutex g_pool_mu;
 cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+}  // namespace
 
 cudaMemPool_t library_pool() {
   int dev = 0;
@@ -56,25 +55,21 @@ cudaMemPool_t library_pool() {
   return g_pools[dev];
 }
 
-struct DevBuf {
-  std::vector<void*> ptrs;
-  cudaStream_t st = nullptr;
-  int64_t bytes = 0;
-  cudaError_t alloc(void** p, size_t n) {
-    n = (n + 255) & ~size_t(255);
-    cudaMemPool_t pool = library_pool();
-    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, n, pool, st) : cudaMallocAsync(p, n, st);
-    if (e == cudaSuccess) {
-      ptrs.push_back(*p);
-      bytes += (int64_t)n;
-    }
-    return e;
+cudaError_t DevBuf::alloc(void** p, size_t n) {
+  n = (n + 255) & ~size_t(255);
+  cudaMemPool_t pool = library_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(p, n, pool, st) : cudaMallocAsync(p, n, st);
+  if (e == cudaSuccess) {
+    ptrs.push_back(*p);
+    bytes += (int64_t)n;
   }
-  void release() {
-    for (void* p : ptrs) cudaFreeAsync(p, st);
-    ptrs.clear();
-  }
-};
+  return e;
+}
+
+void DevBuf::release() {
+  for (void* p : ptrs) cudaFreeAsync(p, st);
+  ptrs.clear();
+}
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
@@ -84,6 +79,21 @@ bool is_device_ptr(const void* p) {
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
+
+int check_device(int* num_sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return RSIGN_ERR_CUDA; }
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (major != 10 || minor != 3) return RSIGN_ERR_UNSUPPORTED;
+  return RSIGN_OK;
+}
+
+namespace {
+
+constexpr int kChunk = 8;  // NS steps enqueued between host checks of the stop flag
 
 // Control block kept in device memory (one allocation, read back with one copy).
 struct Ctl {
@@ -106,17 +116,6 @@ struct Ctx {
     return err == cudaSuccess;
   }
 };
-
-rsign_status check_device(int* num_sms) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return RSIGN_ERR_CUDA; }
-  int major = 0, minor = 0;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (major != 10 || minor != 3) return RSIGN_ERR_UNSUPPORTED;
-  return RSIGN_OK;
-}
 
 bool is_low(rsign_policy p) { return p != RSIGN_FP64; }
 int lp_fmt_of(rsign_policy p) {
@@ -370,7 +369,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
 
   Ctx c;
   c.st = st;
-  rsign_status dst = check_device(&c.num_sms);
+  rsign_status dst = (rsign_status)check_device(&c.num_sms);
   if (dst != RSIGN_OK) return dst;
 
   const int d = (int)d64;
@@ -721,7 +720,7 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
   const int ck = ckpt_every > 0 ? ckpt_every : 4;
   Ctx c;
   c.st = st;
-  rsign_status dst = check_device(&c.num_sms);
+  rsign_status dst = (rsign_status)check_device(&c.num_sms);
   if (dst != RSIGN_OK) return dst;
   const int d = (int)d64, dp = (d + 255) / 256 * 256;
   const size_t dd = (size_t)dp * dp;
@@ -1005,6 +1004,8 @@ void rsign_options_default(rsign_options* opt) {
   opt->timing = 1;
   opt->low_split = 1;
   opt->lanczos_max = 600;
+  opt->batch_graphs = 1;
+  opt->batch_tile = 0;
 }
 
 rsign_status rsign_reflector_ex(const double* H, int64_t d, int32_t k, double s, double tol,
@@ -1030,7 +1031,7 @@ rsign_status rsign_apply(const double* R, int64_t d, const double* V, int64_t nv
                          void* stream) {
   if (!R || !V || !out || d < 1 || nv < 1) return RSIGN_ERR_ARG;
   int sms = 0;
-  rsign_status ds = check_device(&sms);
+  rsign_status ds = (rsign_status)check_device(&sms);
   if (ds != RSIGN_OK) return ds;
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf mem;
@@ -1057,20 +1058,6 @@ rsign_status rsign_apply(const double* R, int64_t d, const double* V, int64_t nv
   mem.release();
   if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return RSIGN_ERR_CUDA; }
   return RSIGN_OK;
-}
-
-rsign_status rsign_reflector_batched(int32_t n, const double* const* H, const int64_t* d,
-                                     const int32_t* k, const double* s, double tol,
-                                     rsign_policy policy, double* const* R, rsign_info* infos,
-                                     void* stream) {
-  if (n < 0 || (n > 0 && (!H || !d || !k || !s || !R))) return RSIGN_ERR_ARG;
-  rsign_status first = RSIGN_OK;
-  for (int32_t i = 0; i < n; ++i) {
-    const rsign_status st = rsign_reflector(H[i], d[i], k[i], s[i], tol, policy, R[i],
-                                            infos ? &infos[i] : nullptr, stream);
-    if (st != RSIGN_OK && first == RSIGN_OK) first = st;
-  }
-  return first;
 }
 
 rsign_status rsign_reflector_backward(const double* H, int64_t d, int32_t k, double s,
@@ -1119,7 +1106,7 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
   if (!A || !B || !out || !status || dp < 256 || dp % 256 || dp > 16384 || (fmt != 0 && fmt != 1))
     return RSIGN_ERR_ARG;
   int sms = 0;
-  rsign_status ds = check_device(&sms);
+  rsign_status ds = (rsign_status)check_device(&sms);
   if (ds != RSIGN_OK) return ds;
   TcGemmArgs a{};
   a.dp = (int)dp; a.d_real = (int)dp; a.sym = sym ? 1 : 0; a.epi = TC_EPI_STORE_F32; a.n_groups = 1;
@@ -1141,7 +1128,7 @@ rsign_status rsign_dbg_f64_gemm(const double* A, const double* B, int64_t dp, in
                                 void* stream) {
   if (!A || !B || !out || dp < 64 || dp % 64 || dp > 16384) return RSIGN_ERR_ARG;
   int sms = 0;
-  rsign_status ds = check_device(&sms);
+  rsign_status ds = (rsign_status)check_device(&sms);
   if (ds != RSIGN_OK) return ds;
   F64GemmArgs a{};
   a.dp = (int)dp; a.d_real = (int)dp; a.sym = sym ? 1 : 0; a.epi = F64_EPI_STORE; a.scale = 1.0;
@@ -1154,7 +1141,7 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
   if (!A || !B || !out || dp < 256 || dp % 256 || dp > 16384 || d_real < 1 || d_real > dp)
     return RSIGN_ERR_ARG;
   int sms = 0;
-  rsign_status ds = check_device(&sms);
+  rsign_status ds = (rsign_status)check_device(&sms);
   if (ds != RSIGN_OK) return ds;
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf mem;

@@ -1,11 +1,11 @@
 // tc_gemm.cu -- persistent tcgen05 GEMM for the Newton-Schulz products.
 //
 // One CTA per SM (persistent, static round-robin over tiles), 6 warps:
-//   warp 0      TMA producer: 128x64 A and 256x64 B tiles (128B swizzle) into
-//               a 4-stage shared-memory ring, completion on mbarriers;
+//   warp 0      TMA producer: 128x64 A and BNx64 B tiles (128B swizzle) into
+//               a multi-stage shared-memory ring, completion on mbarriers;
 //   warp 1      TMEM allocator and MMA issuer: tcgen05.mma kind::f16,
-//               M=128 N=256 K=16, FP32 accumulators in TMEM, two
-//               accumulators (512 columns) so the epilogue of one tile
+//               M=128 N=BN K=16, FP32 accumulators in TMEM, two
+//               accumulators (2 BN columns) so the epilogue of one tile
 //               overlaps the main loop of the next;
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator (one TMEM lane
 //               quadrant per warp), fused elementwise work, global stores.
@@ -13,28 +13,46 @@
 // triangle and mirrors each strictly-upper element, which halves the work
 // of X^2 (SYRK) and of the symmetric product X (I - X^2) of a Newton-Schulz
 // step (Eq. NS).
+//
+// Tile widths: BN = 256 (one matrix, optionally cluster pairs sharing the B
+// panel) and BN = 128 (grouped batches of small matrices, where a 256-wide
+// tile would be mostly padding).  Grouped mode (args.units != nullptr) takes
+// its tiles from a device table of (matrix, bm, bn, slot) entries built on
+// the host: every matrix of a batch lives in its own Dmax x Dmax slot of one
+// slab, each tile runs its K loop over its own matrix's padded size only, and
+// tiles of matrices flagged in args.mat_skip (converged) are passed over by
+// all three roles alike.
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 namespace rsign {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BK = 64;
 constexpr int NUM_THREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
-// Tile schedule over 128 x 256 output tiles (bm, bn).  With cluster pairs
-// (cl = 2) the unit is a 256-row super-tile (a, bn) covering bm = 2a and
-// bm = 2a + 1: both tiles need the same 256-row panel of B, which the pair
-// loads once (each CTA half of it, multicast to both).  In the triangular
-// schedule tile (bm, bn) is needed iff bn >= floor(bm / 2), so both members
-// of a pair are always needed together.
+template <int BN>
+struct Cfg {
+  static constexpr int STAGES = BN == 256 ? 4 : 6;
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr uint32_t TMEM_COLS = 2 * BN;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+// Tile schedule of one matrix over 128 x BN output tiles (bm, bn).  With
+// cluster pairs (cl = 2) the unit is a 256-row super-tile (a, bn) covering
+// bm = 2a and bm = 2a + 1: both tiles need the same BN-row panel of B, which
+// the pair loads once (each CTA half of it, multicast to both).  In the
+// triangular schedule schedule-row r (rows r cl BM .. ) needs the columns
+// bn >= floor(r cl BM / BN); for BN = 256 both members of a pair are always
+// needed together.
+template <int BN>
 struct TileSched {
   int nbm, nbn, sym, cl, n;
   __device__ __host__ TileSched(int dp, int s, int c) : nbm(dp / BM), nbn(dp / BN), sym(s), cl(c) {
@@ -43,9 +61,10 @@ struct TileSched {
       n = rows * nbn;
     } else {
       n = 0;
-      for (int r = 0; r < rows; ++r) n += nbn - (cl == 1 ? r / 2 : r);
+      for (int r = 0; r < rows; ++r) n += nbn - first(r);
     }
   }
+  __device__ __host__ int first(int r) const { return (r * cl * BM) / BN; }
   // unit t -> (bm, bn) for cluster rank `rank`
   __device__ __forceinline__ void decode(int t, int rank, int& bm, int& bn) const {
     int r, c;
@@ -55,17 +74,44 @@ struct TileSched {
     } else {
       r = 0;
       for (;;) {
-        const int cnt = nbn - (cl == 1 ? r / 2 : r);
+        const int cnt = nbn - first(r);
         if (t < cnt) break;
         t -= cnt;
         ++r;
       }
-      c = (cl == 1 ? r / 2 : r) + t;
+      c = first(r) + t;
     }
     bm = cl == 1 ? r : 2 * r + rank;
     bn = c;
   }
 };
+
+// One schedule unit as every role sees it.
+struct Unit {
+  int mat, bm, bn, slot, n_kb;
+  bool skip;
+};
+
+template <int BN, int CL>
+__device__ __forceinline__ Unit unit_at(const TcGemmArgs& a, const TileSched<BN>& s, int t, int rank) {
+  Unit u;
+  if (a.units != nullptr) {
+    const int4 q = a.units[t];
+    u.mat = q.x;
+    u.bm = q.y;
+    u.bn = q.z;
+    u.slot = q.w;
+    u.n_kb = a.mat_dp[q.x] / BK;
+    u.skip = a.mat_skip != nullptr && a.mat_skip[q.x] != 0;
+  } else {
+    s.decode(t, rank, u.bm, u.bn);
+    u.mat = 0;
+    u.slot = t * CL + rank;
+    u.n_kb = a.dp / BK;
+    u.skip = false;
+  }
+  return u;
+}
 
 template <typename T>
 __device__ __forceinline__ void store32_lp(T* dst, const float* v) {
@@ -102,13 +148,16 @@ __device__ __forceinline__ void load32_lp(const T* src, float* v) {
 }
 
 // Epilogue for one 32-column chunk held by one thread (row i, columns j0..j0+31).
+// moff: element offset of the tile's matrix in out / xin (grouped mode);
+// d_real: that matrix's logical size.
 template <int EPI, typename T>
 __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j0, int g,
-                                               float* v, bool above, double& acc1) {
+                                               float* v, bool above, double& acc1, size_t moff,
+                                               int d_real) {
   const int ld = a.dp;
   const size_t row = (size_t)i * ld;
   if constexpr (EPI == TC_EPI_STORE_F32) {
-    float* out = reinterpret_cast<float*>(a.out);
+    float* out = reinterpret_cast<float*>(a.out) + moff;
     if (!a.sym) {
       float4* d4 = reinterpret_cast<float4*>(out + row + j0);
 #pragma unroll
@@ -125,7 +174,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
       }
     }
   } else if constexpr (EPI == TC_EPI_STORE_LP) {
-    T* out = reinterpret_cast<T*>(a.out);
+    T* out = reinterpret_cast<T*>(a.out) + moff;
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj) v[jj] *= a.scale;
     if (!a.sym || above) {
@@ -149,20 +198,20 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
     // UPDATE: X+ = X + 1/2 X (I - X^2), trace of the stored iterate in acc1.
     // With a.split the value is stored as hi = T(v), lo = T(v - hi) in two
     // planes (and X is read back as hi + lo).
-    T* out = reinterpret_cast<T*>(a.out);
+    T* out = reinterpret_cast<T*>(a.out) + moff;
     const size_t plane = (size_t)ld * ld;
     if constexpr (EPI == TC_EPI_NS_SYRK) {
-      const bool row_real = i < a.d_real;
+      const bool row_real = i < d_real;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int j = j0 + jj;
-        const bool real = row_real && (j < a.d_real);
+        const bool real = row_real && (j < d_real);
         const float e = real ? ((i == j ? 1.0f : 0.0f) - v[jj]) : 0.0f;
         v[jj] = e;
         if (real && j >= i) acc1 += (j > i ? 2.0 : 1.0) * (double)e * (double)e;
       }
     } else {
-      const T* xin = reinterpret_cast<const T*>(a.xin);
+      const T* xin = reinterpret_cast<const T*>(a.xin) + moff;
       float x[32];
       load32_lp<T>(xin + row + j0, x);
       if (a.split) {
@@ -173,7 +222,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
       }
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) v[jj] = x[jj] + 0.5f * v[jj];
-      if (i >= j0 && i < j0 + 32 && i < a.d_real) {
+      if (i >= j0 && i < j0 + 32 && i < d_real) {
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj)
           if (j0 + jj == i) {
@@ -250,17 +299,19 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
   }
 }
 
-template <int EPI, typename T, int CL>
+template <int EPI, typename T, int CL, int BN>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ TcGemmArgs args, const uint32_t idesc) {
+  using C = Cfg<BN>;
+  constexpr int STAGES = C::STAGES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
   if (args.skip != nullptr && *args.skip != 0) return;  // uniform across the grid (and cluster)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
   uint64_t* full = bars;                 // [STAGES]
   uint64_t* empty = bars + STAGES;       // [STAGES]
   uint64_t* tfull = bars + 2 * STAGES;   // [2]
@@ -291,7 +342,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     prefetch_tensormap(&tmB);
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -300,8 +351,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const TileSched sched(args.dp, args.sym, CL);
-  const int n_kb = args.dp / BK;
+  const TileSched<BN> sched(args.dp, args.sym, CL);
+  const int n_units = args.units != nullptr ? args.n_units : sched.n;
   const int unit0 = blockIdx.x / CL, unit_step = gridDim.x / CL;
 
   if (warp == 0) {
@@ -310,23 +361,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int t = unit0; ok && t < sched.n; t += unit_step) {
-        int bm, bn;
-        sched.decode(t, rank, bm, bn);
+      for (int t = unit0; ok && t < n_units; t += unit_step) {
+        const Unit u = unit_at<BN, CL>(args, sched, t, rank);
+        if (u.skip) continue;
+        const int sa = u.mat * args.a_planes, sb = u.mat * args.b_planes;
         for (int g = 0; ok && g < args.n_groups; ++g) {
           for (int pi = args.group_start[g]; ok && pi < args.group_start[g + 1]; ++pi) {
-            for (int kb = 0; kb < n_kb; ++kb) {
+            for (int kb = 0; kb < u.n_kb; ++kb) {
               if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, status)) { ok = false; break; }
               const uint32_t fb = smem_u32(&full[stage]);
               // the full barrier counts all of the stage's bytes, including the
               // half of B that the peer multicasts into this CTA
-              mbar_arrive_expect_tx(fb, STAGE_BYTES);
-              tma_load_3d(smem_u32(sA + stage * A_BYTES), &tmA, fb, kb * BK, bm * BM, args.pair_a[pi]);
+              mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
+              tma_load_3d(smem_u32(sA + stage * A_BYTES), &tmA, fb, kb * BK, u.bm * BM, sa + args.pair_a[pi]);
               if constexpr (CL == 2) {
                 tma_load_3d_mc(smem_u32(sB + stage * B_BYTES + rank * (B_BYTES / 2)), &tmB, fb, kb * BK,
-                               bn * BN + rank * (BN / 2), args.pair_b[pi], (uint16_t)0x3);
+                               u.bn * BN + rank * (BN / 2), sb + args.pair_b[pi], (uint16_t)0x3);
               } else {
-                tma_load_3d(smem_u32(sB + stage * B_BYTES), &tmB, fb, kb * BK, bn * BN, args.pair_b[pi]);
+                tma_load_3d(smem_u32(sB + stage * B_BYTES), &tmB, fb, kb * BK, u.bn * BN, sb + args.pair_b[pi]);
               }
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
@@ -348,7 +400,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0;
       int acc_it = 0;
       bool ok = true;
-      for (int t = unit0; ok && t < sched.n; t += unit_step) {
+      for (int t = unit0; ok && t < n_units; t += unit_step) {
+        const Unit u = unit_at<BN, CL>(args, sched, t, rank);
+        if (u.skip) continue;
         for (int g = 0; ok && g < args.n_groups; ++g) {
           const int acc = acc_it & 1;
           const uint32_t aph = (acc_it >> 1) & 1;
@@ -357,7 +411,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
           uint32_t accumulate = 0;
           for (int pi = args.group_start[g]; ok && pi < args.group_start[g + 1]; ++pi) {
-            for (int kb = 0; kb < n_kb; ++kb) {
+            for (int kb = 0; kb < u.n_kb; ++kb) {
               if (!mbar_wait(smem_u32(&full[stage]), phase, status)) { ok = false; break; }
               tc_fence_after();
               const uint64_t ad = smem_desc_k128(smem_u32(sA + stage * A_BYTES));
@@ -387,10 +441,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int r = quad * 32 + lane;
     int acc_it = 0;
     bool ok = true;
-    for (int t = unit0; ok && t < sched.n; t += unit_step) {
-      int bm, bn;
-      sched.decode(t, rank, bm, bn);
-      const int i = bm * BM + r;
+    for (int t = unit0; ok && t < n_units; t += unit_step) {
+      const Unit u = unit_at<BN, CL>(args, sched, t, rank);
+      if (u.skip) continue;
+      const int i = u.bm * BM + r;
+      const size_t moff = (size_t)u.mat * (size_t)args.mat_stride;
+      const int d_real = args.units != nullptr ? args.mat_d[u.mat] : args.d_real;
       double acc1 = 0.0;
       for (int g = 0; g < args.n_groups; ++g) {
         const int acc = acc_it & 1;
@@ -406,10 +462,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         for (int c = 0; c < BN / 32; ++c) {
           float v[32];
           tmem_ld32(taddr + (uint32_t)(c * 32), v);
-          const int j0 = bn * BN + c * 32;
+          const int j0 = u.bn * BN + c * 32;
           // chunk lies strictly above the diagonal for every row of this warp
-          const bool above = (j0 > bm * BM + BM - 1);
-          epilogue_chunk<EPI, T>(args, i, j0, g, v, above, acc1);
+          const bool above = (j0 > u.bm * BM + BM - 1);
+          epilogue_chunk<EPI, T>(args, i, j0, g, v, above, acc1, moff, d_real);
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&tempty[acc]));
@@ -418,7 +474,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (!ok) break;
       if constexpr (EPI == TC_EPI_NS_SYRK || EPI == TC_EPI_NS_UPDATE) {
         const double s = warp_sum(acc1);
-        if (lane == 0) args.partials[((size_t)t * CL + rank) * 4 + quad] = s;
+        if (lane == 0) args.partials[(size_t)u.slot * 4 + quad] = s;
       }
     }
   }
@@ -432,7 +488,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem_base, TMEM_COLS);
+    tmem_dealloc(tmem_base, C::TMEM_COLS);
   }
 }
 
@@ -470,13 +526,14 @@ bool make_map(CUtensorMap* m, const void* ptr, int dp, int slices, int box_rows,
   return r == CUDA_SUCCESS;
 }
 
-template <int EPI, typename T, int CL>
+template <int EPI, typename T, int CL, int BN>
 cudaError_t launch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
                    uint32_t idesc, cudaStream_t st) {
+  constexpr int SMEM_BYTES = Cfg<BN>::SMEM_BYTES;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<EPI, T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<EPI, T, CL, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return attr_err;
@@ -497,7 +554,7 @@ cudaError_t launch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap
       q.attrs = qa;
       q.numAttrs = 1;
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<EPI, T, CL>, &q) != cudaSuccess) {
+      if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<EPI, T, CL, BN>, &q) != cudaSuccess) {
         cudaGetLastError();
         n = 0;
       }
@@ -517,25 +574,38 @@ cudaError_t launch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<EPI, T, CL>, ma, mb, a, idesc);
+  return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<EPI, T, CL, BN>, ma, mb, a, idesc);
 }
 
 template <typename T, int CL>
 cudaError_t dispatch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
                      uint32_t idesc, cudaStream_t st) {
   switch (a.epi) {
-    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T, CL>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, CL>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, CL>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, CL>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_OZAKI: return launch<TC_EPI_OZAKI, T, CL>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T, CL, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, CL, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, CL, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, CL, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_OZAKI: return launch<TC_EPI_OZAKI, T, CL, 256>(a, ma, mb, grid, idesc, st);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+// grouped launches: one CTA per SM at most, no clusters, BN = 128 or 256
+template <typename T, int BN>
+cudaError_t dispatch_grouped(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
+                             uint32_t idesc, cudaStream_t st) {
+  switch (a.epi) {
+    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T, 1, BN>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, 1, BN>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, 1, BN>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, 1, BN>(a, ma, mb, grid, idesc, st);
+    default: return cudaErrorInvalidValue;  // the digit-plane epilogue has no grouped form
   }
 }
 
 }  // namespace
 
-int tc_num_tiles(int dp, int sym) { return TileSched(dp, sym, 1).n; }
+int tc_num_tiles(int dp, int sym) { return TileSched<256>(dp, sym, 1).n; }
 
 static int g_default_cluster = 2;
 int tc_set_default_cluster(int cl) {
@@ -546,24 +616,65 @@ int tc_set_default_cluster(int cl) {
 
 cudaError_t tc_gemm(const TcGemmArgs& args, const void* A, int a_slices, const void* B, int b_slices,
                     int lp_fmt, int num_sms, cudaStream_t st) {
-  if (args.dp % BN != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
+  if (args.units != nullptr || args.dp % 256 != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
       args.group_start[args.n_groups] > kTcMaxPairs)
     return cudaErrorInvalidValue;
   // cluster pairs (B panel multicast) unless args.cluster == 1
   const int cl = args.cluster == 0 ? g_default_cluster : (args.cluster == 1 ? 1 : 2);
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) ||
-      !make_map(&mb, B, args.dp, b_slices, BN / cl, lp_fmt))
+      !make_map(&mb, B, args.dp, b_slices, 256 / cl, lp_fmt))
     return cudaErrorInvalidValue;
-  const int units = TileSched(args.dp, args.sym, cl).n;
+  const int units = TileSched<256>(args.dp, args.sym, cl).n;
   const int max_units = num_sms / cl;
   const int grid = cl * (units < max_units ? units : max_units);
-  const uint32_t idesc = idesc_f16(lp_fmt ? 1u : 0u, BM, BN);
+  const uint32_t idesc = idesc_f16(lp_fmt ? 1u : 0u, BM, 256);
   if (cl == 2)
     return lp_fmt ? dispatch<__nv_bfloat16, 2>(args, ma, mb, grid, idesc, st)
                   : dispatch<__half, 2>(args, ma, mb, grid, idesc, st);
   return lp_fmt ? dispatch<__nv_bfloat16, 1>(args, ma, mb, grid, idesc, st)
                 : dispatch<__half, 1>(args, ma, mb, grid, idesc, st);
+}
+
+cudaError_t tc_gemm_grouped(const TcGemmArgs& args, int bn, const void* A, int a_slices, const void* B,
+                            int b_slices, int lp_fmt, int num_sms, cudaStream_t st) {
+  if (args.units == nullptr || args.n_units < 1 || args.mat_dp == nullptr || args.mat_d == nullptr ||
+      (bn != 128 && bn != 256) || args.dp % 256 != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
+      args.group_start[args.n_groups] > kTcMaxPairs || args.epi == TC_EPI_OZAKI)
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) || !make_map(&mb, B, args.dp, b_slices, bn, lp_fmt))
+    return cudaErrorInvalidValue;
+  const int grid = args.n_units < num_sms ? args.n_units : num_sms;
+  const uint32_t idesc = idesc_f16(lp_fmt ? 1u : 0u, BM, bn);
+  if (bn == 128)
+    return lp_fmt ? dispatch_grouped<__nv_bfloat16, 128>(args, ma, mb, grid, idesc, st)
+                  : dispatch_grouped<__half, 128>(args, ma, mb, grid, idesc, st);
+  return lp_fmt ? dispatch_grouped<__nv_bfloat16, 256>(args, ma, mb, grid, idesc, st)
+                : dispatch_grouped<__half, 256>(args, ma, mb, grid, idesc, st);
+}
+
+// Host-side tile table of a batch (grouped mode): every tile of matrix m
+// with padded size dp[m] on a 128 x bn grid (upper-triangle tiles only when
+// sym), ordered by decreasing K extent so that the large tiles start first
+// and the small ones fill the tail of the persistent schedule; slot numbers
+// are contiguous per matrix (slot_begin[m] .. slot_begin[m + 1]).
+void tc_build_units(int n, const int* dp, int bn, int sym, int order, std::vector<int4>* units,
+                    std::vector<int>* slot_begin) {
+  units->clear();
+  slot_begin->assign(n + 1, 0);
+  std::vector<int4> all;
+  for (int m = 0; m < n; ++m) {
+    (*slot_begin)[m] = (int)all.size();
+    const int nbm = dp[m] / BM, nbn = dp[m] / bn;
+    for (int r = 0; r < nbm; ++r)
+      for (int c = sym ? (r * BM) / bn : 0; c < nbn; ++c) all.push_back(make_int4(m, r, c, (int)all.size()));
+  }
+  (*slot_begin)[n] = (int)all.size();
+  if (order == 0) {
+    std::stable_sort(all.begin(), all.end(), [&](const int4& x, const int4& y) { return dp[x.x] > dp[y.x]; });
+  }
+  *units = all;
 }
 
 }  // namespace rsign

@@ -175,6 +175,28 @@ def batched_sizes(count: int = 512, d_choices=tuple(range(32, 513, 32)), k_max: 
     return [(int(d[i]), int(min(k[i], d[i] - 1)), float(math.exp(logd[i]))) for i in range(count)]
 
 
+def batched_workload(count: int = 512, d_choices=tuple(range(32, 513, 32)), k_max: int = 8,
+                     delta_range=(1e-3, 1e-1), offset: float = 0.5, seed: int = 7):
+    """The batched workload: ``count`` controlled spectra of uneven order.
+
+    (d_i, k_i, delta_i) come from ``batched_sizes``; matrix i is the controlled
+    spectrum of that size with seed ``seed * 100003 + i``, moved by a seeded
+    offset c_i uniform in [-offset, offset] (H_i + c_i I, eigenvalues lam + c_i),
+    so every matrix has its own gap midpoint s_i = c_i while its reflector
+    I - 2 Q_k Q_k^T is unchanged.  Returns a list of (Spectrum, s_i).
+    """
+    sizes = batched_sizes(count, d_choices, k_max, delta_range, seed)
+    rng = np.random.default_rng(seed + 1)
+    c = rng.uniform(-offset, offset, size=count)
+    out = []
+    for i, (d, k, delta) in enumerate(sizes):
+        sp = controlled_spectrum(d, k, delta, seed * 100003 + i)
+        H = sp.H + c[i] * np.eye(d)
+        meta = dict(sp.meta, offset=float(c[i]))
+        out.append((Spectrum(H, sp.lam + c[i], sp.Q, k, meta), float(c[i])))
+    return out
+
+
 def controlled_spectrum_torch(d: int, k: int, delta: float, seed: int, device="cuda"):
     """Same recipe as ``controlled_spectrum`` built with torch on ``device``.
 
