@@ -57,6 +57,7 @@ def parse():
                         "grouped launches, against a per-matrix call loop")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-policy", default="FP16_POLISH")
+    p.add_argument("--no-loop", action="store_true", help="batched: skip the per-matrix call loop")
     return p.parse_args()
 
 
@@ -73,7 +74,7 @@ def dist_env():
 # profiles/refine_fp16_d8192_launch_list.md (same kernel source and workload).
 # Algorithmic bytes of one launch: read X (hi + lo, 4 d^2) and write the result
 # (hi + lo, 4 d^2) = 8 d^2 = 0.54 GB at d = 8192.
-MEASURED_TRAFFIC = {(8192, "FP16_REFINE", 1): 2.645e9}
+MEASURED_TRAFFIC = {(8192, "FP16_REFINE", 1): 2.647e9}
 
 
 def peaks():
@@ -405,7 +406,7 @@ def run_batched(args):
     certified = sum(int(i.cert_ok) for i in infos)
     # per-matrix loop on the same inputs
     loop_t = []
-    for _ in range(2):
+    for _ in range(0 if args.no_loop else 2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for H, R, k, s in zip(Hs, Rs, ks, ss):
@@ -413,7 +414,7 @@ def run_batched(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         loop_t.append(e0.elapsed_time(e1))
-    loop_ms = min(loop_t)
+    loop_ms = min(loop_t) if loop_t else None
     # errors of a sample against the construction-known reflectors
     _, infos, st = batched()
     torch.cuda.synchronize(dev)
@@ -436,7 +437,7 @@ def run_batched(args):
                                    "delta log-uniform in [1e-3, 1e-1], own midpoint shifts, Gershgorin alpha, %s"
                                    % (len(items), args.batch_policy),
                        "policy": args.batch_policy, "l2": "inputs 0.3 GB FP64, larger than L2"},
-            "per_matrix_loop_ms": loop_ms, "speedup_vs_loop": loop_ms / value,
+            "per_matrix_loop_ms": loop_ms, "speedup_vs_loop": loop_ms / value if loop_ms else None,
             "certified": certified, "status": st.name, "err_2_sample_max": max(errs),
             "tile": infos[0].batch_tile, "ms_low": ms_low, "ms_fp64": infos[0].ms_fp64,
             "steps_low_max": max(i.steps_low for i in infos),

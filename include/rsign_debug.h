@@ -62,6 +62,17 @@ rsign_status rsign_dbg_f64_gemm(const double* A, const double* B, int64_t dp, in
 rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t dp, int64_t d_real,
                                       int32_t sym, double* out, void* stream);
 
+/*
+ * FP64-emulating product on the FP16 tensor cores (the products of the FP64
+ * polish steps): as rsign_dbg_fp64grade_gemm with digit planes of beta bits
+ * (the widest for which a pair product over d_real terms is exact in FP32:
+ * 7 for d_real <= 4096, 6 up to 16384) and ceil(54 / beta) planes, so each
+ * operand carries at least 54 bits relative to its off-diagonal row maxima
+ * (diagonal exact); level sums in two int64 fixed-point accumulators.
+ */
+rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, int64_t d_real, int32_t sym,
+                                  double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -141,6 +141,8 @@ def load():
     lib.rsign_dbg_f64_gemm.restype = ctypes.c_int
     lib.rsign_dbg_fp64grade_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
     lib.rsign_dbg_fp64grade_gemm.restype = ctypes.c_int
+    lib.rsign_dbg_fp64e_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
+    lib.rsign_dbg_fp64e_gemm.restype = ctypes.c_int
     lib.rsign_dbg_set_tc_cluster.argtypes = [i32]
     lib.rsign_dbg_set_tc_cluster.restype = i32
     lib.rsign_dbg_tridiag_ritz.argtypes = [dp, dp, i32, i32, dp, dp]
@@ -364,6 +366,20 @@ def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
         out = torch.empty((dp, dp), dtype=torch.float64, device=A.device)
     st = Status(lib.rsign_dbg_fp64grade_gemm(A.data_ptr(), B.data_ptr(), dp, int(d_real or dp), int(sym),
                                              out.data_ptr(), _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return out
+
+
+def dbg_fp64e_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
+    """out = A B with FP64-emulating digit planes (>= 54 bits) on the FP16 tensor cores."""
+    torch = _torch()
+    lib = load()
+    dp = int(A.shape[0])
+    if out is None:
+        out = torch.empty((dp, dp), dtype=torch.float64, device=A.device)
+    st = Status(lib.rsign_dbg_fp64e_gemm(A.data_ptr(), B.data_ptr(), dp, int(d_real or dp), int(sym),
+                                         out.data_ptr(), _stream_ptr(stream, True)))
     if st != Status.OK:
         raise RsignError(st)
     return out

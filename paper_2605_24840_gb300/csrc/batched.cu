@@ -141,19 +141,23 @@ __global__ void batch_to_f64_kernel(const T* __restrict__ X0, const T* __restric
 // stage (stop when ||X^2 - I||_F < max(tol, 16 d u_64)); mode 2: fixed-depth
 // FP64 polish (stop only at the budget).  u > 0 enables the floor rule with
 // floor_lo = 2 u sqrt(d), floor_hi = 16 u sqrt(d).  done[m]: 0 active,
-// 1 stopped, 2 budget exhausted; steps[m]: index of the current iterate;
-// all_done: 1 once no matrix is active.  One block, one warp per matrix.
+// 1 stopped, 2 budget exhausted; steps[m]: index of the current iterate.
+// One warp per matrix over many blocks (the FP64 arithmetic of the test is
+// slow on this GPU, so it is spread over the SMs); ctr[0] counts the
+// matrices that stay active and ctr[1] the finished blocks: the last block
+// sets all_done (1 once no matrix is active) and clears both counters.
+constexpr int kCheckWarps = 4;
 __global__ void batch_check_kernel(const double* __restrict__ partials, const int* __restrict__ slot_begin,
                                    int n, const int* __restrict__ dv, int mode, double tol, double u,
                                    int max_steps, int* __restrict__ done, int* __restrict__ steps,
                                    double* __restrict__ prev, double* __restrict__ resid,
-                                   int* __restrict__ all_done) {
+                                   int* __restrict__ all_done, int* __restrict__ ctr) {
   __shared__ int active;
   if (threadIdx.x == 0) active = 0;
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int m = warp; m < n; m += nw) {
-    if (done[m] != 0) continue;  // uniform across the warp
+  const int lane = threadIdx.x & 31;
+  const int m = blockIdx.x * kCheckWarps + (threadIdx.x >> 5);
+  if (m < n && done[m] == 0) {  // uniform across the warp
     const int q0 = slot_begin[m] * 4, q1 = slot_begin[m + 1] * 4;
     double s = 0.0;
     for (int q = q0 + lane; q < q1; q += 32) s += partials[q];
@@ -177,12 +181,23 @@ __global__ void batch_check_kernel(const double* __restrict__ partials, const in
         done[m] = 2;
       } else {
         steps[m] = mm + 1;
-        active = 1;
+        atomicAdd(&active, 1);
       }
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) *all_done = active ? 0 : 1;
+  if (threadIdx.x == 0) {
+    if (active) atomicAdd(&ctr[0], active);
+    __threadfence();
+    const int ticket = atomicAdd(&ctr[1], 1);
+    if (ticket == (int)gridDim.x - 1) {  // every block has published its count
+      __threadfence();
+      const int total = atomicAdd(&ctr[0], 0);
+      *all_done = total == 0 ? 1 : 0;
+      ctr[0] = 0;
+      ctr[1] = 0;
+    }
+  }
 }
 
 // trace of each matrix's result (FP64 slab pair, parity steps[m] & 1, or one
@@ -340,7 +355,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     // ints: d, dp_lp(128), dp_lp(256), dp64, done, steps, flags, done64, steps64,
     //       slot_begin (lp: n+1, f64: n+1), status, all_done, all_done64
     enum { I_D = 0, I_DP128, I_DP256, I_DP64, I_DONE, I_STEPS, I_FLAGS, I_DONE64, I_STEPS64, I_N };
-    const size_t n_int = (size_t)I_N * ng + 3 * (size_t)(ng + 1) + 4;
+    const size_t n_int = (size_t)I_N * ng + 3 * (size_t)(ng + 1) + 6;
     int* ib = nullptr;
     double* db = nullptr;
     enum { D_S = 0, D_ALPHA, D_PREV, D_RESID, D_TRACE, D_N };
@@ -358,6 +373,8 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     int* status = slot_64 + (ng + 1);
     int* all_done = status + 1;
     int* all_done64 = status + 2;
+    int* ctr = status + 3;  // two counters of the stop test (zero between launches)
+    const int check_blocks = (ng + kCheckWarps - 1) / kCheckWarps;
     auto da = [&](int which) { return db + (size_t)which * ng; };
 
     std::vector<int> h_int(n_int, 0);
@@ -438,6 +455,11 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     }
 
     int tile_bn = 64;
+    // tile table chosen for the low-precision stage (reused by the polish)
+    int4* units_sel = nullptr;
+    int n_units_sel = 0;
+    int* slot_sel = nullptr;
+    const int* mat_dp_sel = nullptr;
     void* xlp[2] = {nullptr, nullptr};
     void* elp = nullptr;
     double* x64[2] = {nullptr, nullptr};
@@ -582,6 +604,10 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
       tile_bn = cand_bn[choice];
       int* slot_use = choice == 0 ? slot_lp : slot_lp2;
       const TcGemmArgs sy = syrk_args(choice);
+      units_sel = units_c[choice];
+      n_units_sel = (int)ulp[choice].size();
+      slot_sel = slot_use;
+      mat_dp_sel = choice == 0 ? ia(I_DP128) : ia(I_DP256);
       TcGemmArgs up = sy;
       up.epi = TC_EPI_NS_UPDATE;
       const double u = fmt ? 0.00390625 : 0.00048828125;  // unit roundoff of the operand type
@@ -590,8 +616,9 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         void* xm = xlp[gs & 1];
         void* xn = xlp[(gs + 1) & 1];
         if (tc_gemm_grouped(sy, tile_bn, xm, ng, xm, ng, fmt, num_sms, s2) != cudaSuccess) return false;
-        batch_check_kernel<<<1, 1024, 0, s2>>>(partials, slot_use, ng, ia(I_D), 0, tol, u, max_steps,
-                                               ia(I_DONE), ia(I_STEPS), da(D_PREV), da(D_RESID), all_done);
+        batch_check_kernel<<<check_blocks, 32 * kCheckWarps, 0, s2>>>(
+            partials, slot_use, ng, ia(I_D), 0, tol, u, max_steps, ia(I_DONE), ia(I_STEPS), da(D_PREV),
+            da(D_RESID), all_done, ctr);
         if (cudaGetLastError() != cudaSuccess) return false;
         if (last) return true;
         TcGemmArgs a = up;
@@ -619,7 +646,66 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     if (opt.timing) cudaEventRecord(ev[2], st);
 
     const bool run64 = !low || polish;
-    if (run64) {
+    if (polish) {
+      // ---------------------------------------------------------- FP64 polish
+      // X+ = X + 1/2 X (I - X^2) with FP64-emulating digit-plane products on
+      // the tensor cores (>= 54-bit digits; see fp64e_gemm), grouped over the
+      // slab with the tile table of the low-precision stage: per step one
+      // digit split of X, one fused I - X^2 product with residual partials,
+      // the stop test, one split of E and one fused update product.
+      int dmax = 0;
+      for (int x : g.d) dmax = std::max(dmax, x);
+      const int beta = fp64e_beta(dmax);
+      const int P = fp64e_planes(beta);
+      SplitMat Xs{}, Es{};
+      Xs.n_planes = Es.n_planes = P;
+      Xs.beta = Es.beta = beta;
+      long long* acc64 = nullptr;
+      if (beta == 0 || mem.alloc(&Xs.planes, nel * 2 * P) != cudaSuccess ||
+          mem.alloc(&Es.planes, nel * 2 * P) != cudaSuccess ||
+          mem.alloc((void**)&Xs.sigma, (size_t)ng * D * 8) != cudaSuccess ||
+          mem.alloc((void**)&Xs.diag, (size_t)ng * D * 8) != cudaSuccess ||
+          mem.alloc((void**)&Es.sigma, (size_t)ng * D * 8) != cudaSuccess ||
+          mem.alloc((void**)&Es.diag, (size_t)ng * D * 8) != cudaSuccess ||
+          mem.alloc((void**)&acc64, nel * 8) != cudaSuccess)
+        return fail_cuda();
+      Fp64eExtra base{};
+      base.acc64 = acc64;
+      base.skip = all_done64;
+      base.k_extent = dmax;
+      base.units = units_sel;
+      base.n_units = n_units_sel;
+      base.n_mat = ng;
+      base.bn = tile_bn;
+      base.mat_dp = mat_dp_sel;
+      base.mat_d = ia(I_D);
+      base.mat_skip = ia(I_DONE64);
+      const int max_steps = opt.polish_steps;
+      auto step = [&](int gs, cudaStream_t s2, bool last) -> bool {
+        double* X = x64[gs & 1];
+        Xs.full = X;
+        if (split_rows_grouped(X, D, ng, mat_dp_sel, Xs, s2) != cudaSuccess) return false;
+        Fp64eExtra sq = base;
+        sq.ident = 1;
+        sq.partials = partials;
+        if (fp64e_gemm(Xs, Xs, D, dmax, 1, e64, sq, status, num_sms, s2, P) != cudaSuccess) return false;
+        batch_check_kernel<<<check_blocks, 32 * kCheckWarps, 0, s2>>>(
+            partials, slot_sel, ng, ia(I_D), 2, tol, 0.0, max_steps, ia(I_DONE64), ia(I_STEPS64),
+            da(D_PREV), da(D_RESID), all_done64, ctr);
+        if (cudaGetLastError() != cudaSuccess) return false;
+        if (last) return true;
+        Es.full = e64;
+        if (split_rows_grouped(e64, D, ng, mat_dp_sel, Es, s2) != cudaSuccess) return false;
+        Fp64eExtra up = base;
+        up.xin64 = X;
+        up.xin_mult = 0.5;
+        if (fp64e_gemm(Xs, Es, D, dmax, 1, x64[(gs + 1) & 1], up, status, num_sms, s2, P) != cudaSuccess)
+          return false;
+        if (s2 == st) launches += 5;
+        return true;
+      };
+      if (!run_stage(max_steps, all_done64, step)) return fail_cuda();
+    } else if (run64) {
       // --------------------------------------------- FP64 stage / FP64 polish
       F64GemmArgs sy{};
       sy.dp = D; sy.d_real = 0; sy.sym = 1; sy.epi = F64_EPI_NS_SYRK; sy.out = e64; sy.partials = partials;
@@ -632,9 +718,9 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         a.A = x64[gs & 1];
         a.B = x64[gs & 1];
         if (f64_gemm_grouped(a, s2) != cudaSuccess) return false;
-        batch_check_kernel<<<1, 1024, 0, s2>>>(partials, slot_64, ng, ia(I_D), mode, tol, 0.0, max_steps,
-                                               ia(I_DONE64), ia(I_STEPS64), da(D_PREV), da(D_RESID),
-                                               all_done64);
+        batch_check_kernel<<<check_blocks, 32 * kCheckWarps, 0, s2>>>(
+            partials, slot_64, ng, ia(I_D), mode, tol, 0.0, max_steps, ia(I_DONE64), ia(I_STEPS64),
+            da(D_PREV), da(D_RESID), all_done64, ctr);
         if (cudaGetLastError() != cudaSuccess) return false;
         if (last) return true;
         F64GemmArgs b = sy;

@@ -44,8 +44,8 @@ enum TcEpi : int {
   TC_EPI_OZAKI = 4,      // out_f64 (+)= rs_i cs_j group_scale_g acc (exact integer groups)
 };
 
-constexpr int kTcMaxPairs = 64;
-constexpr int kTcMaxGroups = 16;
+constexpr int kTcMaxPairs = 72;
+constexpr int kTcMaxGroups = 32;
 
 struct TcGemmArgs {
   int dp;          // padded order: rows of A/B, K extent, leading dimension of outputs
@@ -58,8 +58,21 @@ struct TcGemmArgs {
   int pair_b[kTcMaxPairs];
   double group_scale[kTcMaxGroups];
   int cluster;                    // 1: single-CTA tiles; 0 or 2: cluster pairs sharing B (default)
-  int group_shift[kTcMaxGroups];  // TC_EPI_OZAKI: group weight 2^shift in the int64 sum
-  double final_scale;             // TC_EPI_OZAKI: weight of one unit of that sum
+  int group_shift[kTcMaxGroups];  // TC_EPI_OZAKI: group weight 2^shift in its int64 sum
+  double final_scale;             // TC_EPI_OZAKI (n_sg == 0): weight of one unit of that sum
+  // TC_EPI_OZAKI with two super-groups of levels (n_sg == 2, for products of
+  // more than ~37 bits, whose fixed-point sum would overflow one int64):
+  // super-group 0 accumulates in acc64, super-group 1 in out (as int64); the
+  // last group combines V0 sg_weight[0] + V1 sg_weight[1] in FP64.
+  int n_sg;                        // 0: one sum in out (first group = group 0); 2: as above
+  int group_sg[kTcMaxGroups];      // super-group of each group
+  int group_first[kTcMaxGroups];   // 1: first group of its super-group (writes, no read)
+  double sg_weight[2];
+  long long* acc64;                // dp x dp (per matrix) int64 scratch of super-group 0
+  const double* xin64;             // optional: out = xin64 + xin_mult * (product)
+  double xin_mult;
+  int oz_ident;                    // 1: out = I - (product) on the logical d x d block (0
+                                   // outside) with ||out||_F^2 partials in `partials`
   float scale;
   void* out;
   const void* xin;         // TC_EPI_NS_UPDATE: current iterate (operand type)
@@ -86,6 +99,7 @@ struct TcGemmArgs {
   const int* mat_skip;     // per matrix: nonzero = converged, its tiles are skipped
   long long mat_stride;    // elements of the output type between consecutive matrices
   int a_planes, b_planes;  // slices per matrix in A / B
+  int mat_vec_stride;      // TC_EPI_OZAKI: elements between matrices in rs / cs / a_diag / b_diag
 };
 
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
@@ -234,13 +248,45 @@ constexpr int kSlices = 7;      // digit planes per operand (35 bits)
 // off-diagonal maximum, which is far below the diagonal for the reflector
 // and for diagonally heavy Hessians) and re-enters exactly in the epilogue.
 struct SplitMat {
-  void* planes;        // [kSlices][dp][dp] FP16 digits of M - diag(M)
+  void* planes;        // [n_planes][dp][dp] FP16 digits of M - diag(M)
+                       // (grouped: [n_mat][n_planes][dp][dp], dp = slot order)
   double* sigma;       // [dp] row scales (powers of two)
   double* diag;        // [dp] diag(M)
   const double* full;  // the FP64 matrix itself (dp x dp), not owned
+  int n_planes = kSlices;   // digit planes (n_planes * beta <= 56)
+  int beta = kSliceBeta;    // bits per digit
 };
 // Split the FP64 matrix M (dp x dp, symmetric) into digit planes; out.full = M.
 cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st);
+// The same for every matrix of a slab (matrix m in slot m, D x D, rows and
+// columns below mat_dp[m]).
+cudaError_t split_rows_grouped(const double* M, int D, int n_mat, const int* mat_dp, SplitMat out,
+                               cudaStream_t st);
+
+// FP64-emulating products (Ozaki scheme with 53+ bits): digits of beta bits,
+// beta the widest for which one pair product over K terms is exact in the
+// FP32 accumulator (fp64e_beta), and fp64e_planes(beta) planes (>= 54 bits).
+// Products of more than ~37 bits use two int64 fixed-point sums (scratch acc64).
+int fp64e_beta(int k_extent);
+int fp64e_planes(int beta);
+struct Fp64eExtra {
+  long long* acc64 = nullptr;       // int64 scratch (dp x dp per matrix) when two sums are needed
+  const double* xin64 = nullptr;    // out = xin64 + xin_mult * product
+  double xin_mult = 1.0;
+  int ident = 0;                    // out = I - product (logical block) with residual partials
+  double* partials = nullptr;       // 4 per tile (ident)
+  const int* skip = nullptr;
+  int k_extent = 0;                 // nonzero K terms (default d_real)
+  // grouped launch (slab of n_mat matrices, dp = slot order)
+  const int4* units = nullptr;
+  int n_units = 0, n_mat = 0, bn = 128;
+  const int* mat_dp = nullptr;
+  const int* mat_d = nullptr;
+  const int* mat_skip = nullptr;
+};
+cudaError_t fp64e_plan(TcGemmArgs* a, int n_planes, int beta, int levels, int k_extent);
+cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym, double* out,
+                       const Fp64eExtra& x, int* status, int num_sms, cudaStream_t st, int levels);
 // out (FP64, dp x dp) = A * B for split symmetric A, B (K = d_real nonzeros);
 // sym = 1 when the product is symmetric (A == B): upper tiles + mirror.
 // `levels` (<= kSlices) truncates the digit-plane product after levels

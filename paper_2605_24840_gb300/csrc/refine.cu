@@ -20,19 +20,25 @@ namespace {
 constexpr int TILE = 32;
 
 // ------------------------------------------------------------ digit planes
-__global__ void split_rows_kernel(const double* __restrict__ M, int dp, __half* __restrict__ planes,
-                                  double* __restrict__ sigma, double* __restrict__ diag) {
+__global__ void split_rows_kernel(const double* __restrict__ M, int ld, __half* __restrict__ planes,
+                                  double* __restrict__ sigma, double* __restrict__ diag, int n_planes,
+                                  int beta, const int* __restrict__ mat_dp) {
   __shared__ double sh[32];
   __shared__ int e_sh;
-  const int i = blockIdx.x;
-  const double* row = M + (size_t)i * dp;
-  double m = 0.0;
-  for (int k = threadIdx.x; k < dp; k += blockDim.x)
-    if (k != i) m = fmax(m, fabs(row[k]));
-  if (threadIdx.x == 0) diag[i] = row[i];
+  // block (i, m): row i of matrix m (grouped: matrix m in slot m of a slab,
+  // planes [m][n_planes][ld][ld]); single matrix: m = 0, every row
+  const int i = blockIdx.x, m = blockIdx.y;
+  const int ncols = mat_dp != nullptr ? mat_dp[m] : ld;
+  if (i >= ncols) return;  // outside the matrix's padded order: never read
+  const size_t slot = (size_t)ld * ld;
+  const double* row = M + (size_t)m * slot + (size_t)i * ld;
+  double m_abs = 0.0;
+  for (int k = threadIdx.x; k < ncols; k += blockDim.x)
+    if (k != i) m_abs = fmax(m_abs, fabs(row[k]));
+  if (threadIdx.x == 0) diag[(size_t)m * ld + i] = row[i];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  for (int o = 16; o > 0; o >>= 1) m_abs = fmax(m_abs, __shfl_xor_sync(0xffffffffu, m_abs, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m_abs;
   __syncthreads();
   if (threadIdx.x == 0) {
     double mm = 0.0;
@@ -43,24 +49,23 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int dp, __half* 
       ex += 1;
     }
     e_sh = ex;
-    sigma[i] = ldexp(1.0, ex);
+    sigma[(size_t)m * ld + i] = ldexp(1.0, ex);
   }
   __syncthreads();
   const int ex = e_sh;
-  const size_t plane = (size_t)dp * dp;
+  __half* pl = planes + (size_t)m * n_planes * slot + (size_t)i * ld;
   // r = M_ik 2^-ex in (-1/2, 1/2) as a fixed-point integer with 62 fraction
   // bits (one exact FP64 scaling and one conversion); the balanced base-2^beta
   // digits are then peeled off with integer shifts: the FP64 pipe of this GPU
-  // is far slower than its integer pipe.
+  // is far slower than its integer pipe.  n_planes * beta <= 56.
   const double to_fixed = ldexp(1.0, 62 - ex);
-  for (int k = threadIdx.x; k < dp; k += blockDim.x) {
+  for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
     long long n = (k == i) ? 0ll : __double2ll_rn(row[k] * to_fixed);  // diagonal kept apart
-#pragma unroll
-    for (int p = 0; p < kSlices; ++p) {
-      const int sh = 62 - kSliceBeta * (p + 1);                // weight of digit p: 2^sh
+    for (int p = 0; p < n_planes; ++p) {
+      const int sh = 62 - beta * (p + 1);                      // weight of digit p: 2^sh
       const long long dg = (n + (1ll << (sh - 1))) >> sh;      // nearest, |dg| <= 2^(beta-1)
       n -= dg * (1ll << sh);                                   // |n| <= 2^(sh-1)
-      planes[p * plane + (size_t)i * dp + k] = __int2half_rn((int)dg);
+      pl[p * slot + k] = __int2half_rn((int)dg);
     }
   }
 }
@@ -316,13 +321,100 @@ int grid_for(size_t n) {
 }  // namespace
 
 cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st) {
-  split_rows_kernel<<<dp, 256, 0, st>>>(M, dp, (__half*)out.planes, out.sigma, out.diag);
+  if (out.n_planes < 1 || out.n_planes * out.beta > 56 || out.beta < 2 || out.beta > 11) return cudaErrorInvalidValue;
+  split_rows_kernel<<<dim3(dp, 1), 256, 0, st>>>(M, dp, (__half*)out.planes, out.sigma, out.diag, out.n_planes,
+                                                 out.beta, nullptr);
   return cudaGetLastError();
+}
+
+cudaError_t split_rows_grouped(const double* M, int D, int n_mat, const int* mat_dp, SplitMat out,
+                               cudaStream_t st) {
+  if (out.n_planes < 1 || out.n_planes * out.beta > 56 || out.beta < 2 || out.beta > 11) return cudaErrorInvalidValue;
+  split_rows_kernel<<<dim3(D, n_mat), 256, 0, st>>>(M, D, (__half*)out.planes, out.sigma, out.diag, out.n_planes,
+                                                    out.beta, mat_dp);
+  return cudaGetLastError();
+}
+
+int fp64e_beta(int k_extent) {
+  // largest digit width whose single-pair group sum stays exact in FP32:
+  // 2^(2 beta - 2) K <= 2^24
+  for (int b = 7; b >= 4; --b)
+    if (std::ldexp(1.0, 2 * b - 2) * (double)k_extent <= std::ldexp(1.0, 24)) return b;
+  return 0;
+}
+
+int fp64e_planes(int beta) { return beta > 0 ? (54 + beta - 1) / beta : 0; }
+
+cudaError_t fp64e_plan(TcGemmArgs* a, int n_planes, int beta, int levels, int k_extent) {
+  const int L = levels < 1 ? 1 : (levels > n_planes ? n_planes : levels);
+  // |digit| <= 2^(beta-1): a group of n pairs sums to at most n 2^(2 beta - 2) K
+  const double bound1 = std::ldexp(1.0, 2 * beta - 2) * (double)k_extent;
+  const int max_pairs = (int)std::floor(std::ldexp(1.0, 24) / bound1);
+  if (max_pairs < 1) return cudaErrorInvalidValue;
+  int np = 0, ng = 0;
+  std::vector<int> level_groups(L, 0), group_level;
+  for (int t = 0; t < L; ++t) {  // levels 0 .. L-1 (truncation after beta L bits)
+    int in_group = 0;
+    for (int p = 0; p <= t; ++p) {
+      const int q = t - p;
+      if (p >= n_planes || q >= n_planes) continue;
+      if (in_group == 0) {
+        if (ng >= kTcMaxGroups) return cudaErrorInvalidValue;
+        a->group_start[ng] = np;
+        a->group_scale[ng] = std::ldexp(1.0, -beta * (t + 2));
+        group_level.push_back(t);
+        ++level_groups[t];
+        ++ng;
+      }
+      if (np >= kTcMaxPairs) return cudaErrorInvalidValue;
+      a->pair_a[np] = p;
+      a->pair_b[np] = q;
+      ++np;
+      if (++in_group == max_pairs) in_group = 0;
+    }
+  }
+  a->n_groups = ng;
+  a->group_start[ng] = np;
+  // Super-groups: levels t0..t1 share one int64 sum V = sum acc_t 2^(beta (t1 - t))
+  // while its bound sum_t groups_t 2^(24 + beta (t1 - t)) stays below 2^62.
+  auto bound = [&](int t0, int t1) {
+    double b = 0.0;
+    for (int t = t0; t <= t1; ++t) b += level_groups[t] * std::ldexp(1.0, 24 + beta * (t1 - t));
+    return b;
+  };
+  const double lim = std::ldexp(1.0, 62);
+  if (bound(0, L - 1) < lim) {
+    a->n_sg = 0;
+    for (int g = 0; g < ng; ++g) a->group_shift[g] = beta * (L - 1 - group_level[g]);
+    a->final_scale = std::ldexp(1.0, -beta * (L - 1 + 2));
+    return cudaSuccess;
+  }
+  int split = L - 1;  // super-group 1 = levels split .. L-1, as long as it fits
+  while (split > 0 && bound(split - 1, L - 1) < lim) --split;
+  if (!(bound(0, split - 1) < lim)) return cudaErrorInvalidValue;  // would need three sums
+  a->n_sg = 2;
+  for (int g = 0; g < ng; ++g) {
+    const int t = group_level[g];
+    const int s = t >= split ? 1 : 0;
+    const int t1 = s ? L - 1 : split - 1;
+    a->group_sg[g] = s;
+    a->group_shift[g] = beta * (t1 - t);
+    a->group_first[g] = (g == 0 || a->group_sg[g - 1] != s) ? 1 : 0;
+  }
+  a->sg_weight[0] = std::ldexp(1.0, -beta * (split - 1 + 2));
+  a->sg_weight[1] = std::ldexp(1.0, -beta * (L - 1 + 2));
+  return cudaSuccess;
 }
 
 cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym, double* out,
                        int* status, int num_sms, cudaStream_t st, int levels) {
-  const int L = levels < 1 ? 1 : (levels > kSlices ? kSlices : levels);
+  Fp64eExtra x{};
+  return fp64e_gemm(A, B, dp, d_real, sym, out, x, status, num_sms, st, levels);
+}
+
+cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym, double* out,
+                       const Fp64eExtra& x, int* status, int num_sms, cudaStream_t st, int levels) {
+  if (A.beta != B.beta || A.n_planes != B.n_planes) return cudaErrorInvalidValue;
   TcGemmArgs a{};
   a.dp = dp;
   a.d_real = d_real;
@@ -333,40 +425,32 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
   a.rs = A.sigma;
   a.cs = B.sigma;
   a.status = status;
-  a.skip = nullptr;
+  a.skip = x.skip;
   a.a_full = A.full;
   a.b_full = B.full;
   a.a_diag = A.diag;
   a.b_diag = B.diag;
-  // |digit| <= 2^(beta-1): a group of n pairs sums to at most n 2^(2 beta - 2) K
-  const double bound1 = std::ldexp(1.0, 2 * kSliceBeta - 2) * (double)d_real;
-  const int max_pairs = std::max(1, (int)std::floor(std::ldexp(1.0, 24) / bound1));
-  int np = 0, ng = 0;
-  for (int t = 0; t < L; ++t) {  // levels 0 .. L-1 (truncation after 5 L bits)
-    int in_group = 0;
-    for (int p = 0; p <= t; ++p) {
-      const int q = t - p;
-      if (p >= kSlices || q >= kSlices) continue;
-      if (in_group == 0) {
-        if (ng >= kTcMaxGroups) return cudaErrorInvalidValue;
-        a.group_start[ng] = np;
-        a.group_scale[ng] = std::ldexp(1.0, -kSliceBeta * (t + 2));
-        // integer weight relative to the deepest level kSlices-1: the int64
-        // sum stays below 2^(24 + beta (kSlices-1) + 2) < 2^63
-        a.group_shift[ng] = kSliceBeta * (L - 1 - t);
-        ++ng;
-      }
-      if (np >= kTcMaxPairs) return cudaErrorInvalidValue;
-      a.pair_a[np] = p;
-      a.pair_b[np] = q;
-      ++np;
-      if (++in_group == max_pairs) in_group = 0;
-    }
-  }
-  a.n_groups = ng;
-  a.group_start[ng] = np;
-  a.final_scale = std::ldexp(1.0, -kSliceBeta * (L - 1 + 2));
-  return tc_gemm(a, A.planes, kSlices, B.planes, kSlices, 0, num_sms, st);
+  a.acc64 = x.acc64;
+  a.xin64 = x.xin64;
+  a.xin_mult = x.xin_mult;
+  a.oz_ident = x.ident;
+  a.partials = x.partials;
+  const int kext = x.k_extent > 0 ? x.k_extent : d_real;
+  cudaError_t e = fp64e_plan(&a, A.n_planes, A.beta, levels, kext);
+  if (e != cudaSuccess) return e;
+  if (a.n_sg == 2 && a.acc64 == nullptr) return cudaErrorInvalidValue;
+  if (x.units == nullptr) return tc_gemm(a, A.planes, A.n_planes, B.planes, B.n_planes, 0, num_sms, st);
+  a.units = x.units;
+  a.n_units = x.n_units;
+  a.mat_dp = x.mat_dp;
+  a.mat_d = x.mat_d;
+  a.mat_skip = x.mat_skip;
+  a.mat_stride = (long long)dp * dp;
+  a.mat_vec_stride = dp;
+  a.a_planes = A.n_planes;
+  a.b_planes = B.n_planes;
+  a.cluster = 1;
+  return tc_gemm_grouped(a, x.bn, A.planes, x.n_mat * A.n_planes, B.planes, x.n_mat * B.n_planes, 0, num_sms, st);
 }
 
 cudaError_t antisym_part(const double* N, int dp, float* C, float* blockmax, double* part,

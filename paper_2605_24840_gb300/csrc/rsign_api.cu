@@ -170,6 +170,56 @@ bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_ste
   return true;
 }
 
+// FP64 polish steps X+ = X + 1/2 X (I - X^2) (Eq. NS, update form) on the
+// tensor cores: both products are FP64-emulating digit-plane products
+// (fp64e: >= 54-bit digits, FP32-exact group sums, int64 fixed point), the
+// first one fused with I - X^2 and its residual, the second with the update.
+// Runs exactly `steps` updates and a final residual product, as the FP64
+// polish of the one-matrix FP64 loop does; X_0 in xb[0], the result in
+// xb[steps & 1], residuals in hist[0..steps].
+cudaError_t fp64e_polish(Ctx& c, DevBuf& mem, double* xb[2], double* E, int dp, int d, int steps,
+                         double* partials, double* hist, Ctl* ctl) {
+  const size_t dd = (size_t)dp * dp;
+  const int beta = fp64e_beta(d);
+  if (beta == 0) return cudaErrorInvalidValue;
+  const int P = fp64e_planes(beta);
+  SplitMat Xs{}, Es{};
+  Xs.n_planes = Es.n_planes = P;
+  Xs.beta = Es.beta = beta;
+  long long* acc64 = nullptr;
+  cudaError_t e;
+  if ((e = mem.alloc(&Xs.planes, dd * 2 * P)) != cudaSuccess) return e;
+  if ((e = mem.alloc(&Es.planes, dd * 2 * P)) != cudaSuccess) return e;
+  if ((e = mem.alloc((void**)&Xs.sigma, (size_t)dp * 8)) != cudaSuccess) return e;
+  if ((e = mem.alloc((void**)&Xs.diag, (size_t)dp * 8)) != cudaSuccess) return e;
+  if ((e = mem.alloc((void**)&Es.sigma, (size_t)dp * 8)) != cudaSuccess) return e;
+  if ((e = mem.alloc((void**)&Es.diag, (size_t)dp * 8)) != cudaSuccess) return e;
+  if ((e = mem.alloc((void**)&acc64, dd * 8)) != cudaSuccess) return e;
+  const int nt = tc_num_tiles(dp, 1);
+  for (int m = 0; m <= steps; ++m) {
+    double* X = xb[m & 1];
+    Xs.full = X;
+    if (!c.ok(split_rows(X, dp, Xs, c.st))) return c.err;
+    Fp64eExtra sq{};
+    sq.acc64 = acc64;
+    sq.ident = 1;
+    sq.partials = partials;
+    if (!c.ok(fp64e_gemm(Xs, Xs, dp, d, 1, E, sq, &ctl->status, c.num_sms, c.st, P))) return c.err;
+    if (!c.ok(ns_check(partials, nt * 4, hist, m, -1.0, -1.0, -1.0, 0.0, &ctl->done64, &ctl->steps64, c.st)))
+      return c.err;
+    if (m == steps) break;
+    Es.full = E;
+    if (!c.ok(split_rows(E, dp, Es, c.st))) return c.err;
+    Fp64eExtra up{};
+    up.acc64 = acc64;
+    up.xin64 = X;
+    up.xin_mult = 0.5;
+    if (!c.ok(fp64e_gemm(Xs, Es, dp, d, 1, xb[(m + 1) & 1], up, &ctl->status, c.num_sms, c.st, P)))
+      return c.err;
+  }
+  return cudaSuccess;
+}
+
 // ---------------------------------------------------------------------------
 // Commutator refinement (beyond the paper's plain iteration; needed because
 // Newton-Schulz forgets A after X_0: an error that anticommutes with sign(A)
@@ -625,9 +675,14 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     F64Loop L{{xb64[0], xb64[1]}, E64, partials, hist64, &ctl->done64, &ctl->steps64};
     int m_ret = 0;
     const bool polish = policy != RSIGN_FP64;
-    const double tol_abs = polish ? -1.0 : tol_fro;
-    const int budget = polish ? opt.polish_steps : opt.max_steps;
-    if (!f64_ns(c, L, dp, d, tol_abs, budget, ctl, ctl_h, &m_ret, &conv64)) return fail_cuda();
+    if (polish) {
+      // FP64 polish on the tensor cores (FP64-emulating digit-plane products)
+      if (fp64e_polish(c, mem, xb64, E64, dp, d, opt.polish_steps, partials, hist64, ctl) != cudaSuccess)
+        return fail_cuda();
+      m_ret = opt.polish_steps;
+    } else if (!f64_ns(c, L, dp, d, tol_fro, opt.max_steps, ctl, ctl_h, &m_ret, &conv64)) {
+      return fail_cuda();
+    }
     steps64 = m_ret;
     Rfinal = xb64[m_ret & 1];
     hist_h.resize(opt.max_steps + 2);
@@ -1161,6 +1216,49 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
       mem.alloc((void**)&status, 4) != cudaSuccess || cudaMemsetAsync(status, 0, 4, st) != cudaSuccess ||
       split_rows(A, (int)dp, sa, st) != cudaSuccess || split_rows(B, (int)dp, sb, st) != cudaSuccess ||
       ozaki_gemm(sa, sb, (int)dp, (int)d_real, sym ? 1 : 0, out, status, sms, st) != cudaSuccess)
+    res = RSIGN_ERR_CUDA;
+  int hs = 0;
+  if (res == RSIGN_OK && (cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                          cudaStreamSynchronize(st) != cudaSuccess))
+    res = RSIGN_ERR_CUDA;
+  if (res == RSIGN_OK && hs != 0) res = (rsign_status)hs;
+  mem.release();
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  cudaGetLastError();
+  return res;
+}
+
+rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, int64_t d_real, int32_t sym,
+                                  double* out, void* stream) {
+  if (!A || !B || !out || dp < 256 || dp % 256 || dp > 16384 || d_real < 1 || d_real > dp)
+    return RSIGN_ERR_ARG;
+  int sms = 0;
+  rsign_status ds = (rsign_status)check_device(&sms);
+  if (ds != RSIGN_OK) return ds;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf mem;
+  mem.st = st;
+  const size_t dd = (size_t)dp * dp;
+  const int beta = fp64e_beta((int)d_real);
+  const int P = fp64e_planes(beta);
+  SplitMat sa{}, sb{};
+  sa.n_planes = sb.n_planes = P;
+  sa.beta = sb.beta = beta;
+  int* status = nullptr;
+  Fp64eExtra x{};
+  rsign_status res = RSIGN_OK;
+  sa.full = A;
+  sb.full = B;
+  if (beta == 0 || mem.alloc(&sa.planes, dd * 2 * P) != cudaSuccess ||
+      mem.alloc((void**)&sa.sigma, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc((void**)&sa.diag, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc(&sb.planes, dd * 2 * P) != cudaSuccess ||
+      mem.alloc((void**)&sb.sigma, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc((void**)&sb.diag, (size_t)dp * 8) != cudaSuccess ||
+      mem.alloc((void**)&x.acc64, dd * 8) != cudaSuccess ||
+      mem.alloc((void**)&status, 4) != cudaSuccess || cudaMemsetAsync(status, 0, 4, st) != cudaSuccess ||
+      split_rows(A, (int)dp, sa, st) != cudaSuccess || split_rows(B, (int)dp, sb, st) != cudaSuccess ||
+      fp64e_gemm(sa, sb, (int)dp, (int)d_real, sym ? 1 : 0, out, x, status, sms, st, P) != cudaSuccess)
     res = RSIGN_ERR_CUDA;
   int hs = 0;
   if (res == RSIGN_OK && (cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 namespace rsign {
@@ -148,49 +149,44 @@ __device__ __forceinline__ void load32_lp(const T* src, float* v) {
 }
 
 // Epilogue for one 32-column chunk held by one thread (row i, columns j0..j0+31).
-// moff: element offset of the tile's matrix in out / xin (grouped mode);
-// d_real: that matrix's logical size.
+// moff: element offset of the tile's matrix in out / xin (grouped mode),
+// voff: its offset in the per-row vectors of TC_EPI_OZAKI;
+// d_real: that matrix's logical size.  With the symmetric schedule the warp's
+// 32 rows and the chunk's 32 columns are either disjoint with every column
+// above every row (`above`: row-vector stores plus the mirrored column
+// stores, which are coalesced across the warp) or the same index range (the
+// diagonal block: row-vector stores of the whole block, then, ordered after
+// them by __syncwarp, the mirrors of the strictly-upper part overwrite its
+// lower part).  Chunks wholly below the warp's rows are never passed here.
 template <int EPI, typename T>
 __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j0, int g,
                                                float* v, bool above, double& acc1, size_t moff,
-                                               int d_real) {
+                                               size_t voff, int d_real) {
   const int ld = a.dp;
   const size_t row = (size_t)i * ld;
   if constexpr (EPI == TC_EPI_STORE_F32) {
     float* out = reinterpret_cast<float*>(a.out) + moff;
-    if (!a.sym) {
-      float4* d4 = reinterpret_cast<float4*>(out + row + j0);
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        d4[q] = make_float4(v[4 * q] * a.scale, v[4 * q + 1] * a.scale, v[4 * q + 2] * a.scale,
-                            v[4 * q + 3] * a.scale);
-    } else {
+    for (int jj = 0; jj < 32; ++jj) v[jj] *= a.scale;
+    float4* d4 = reinterpret_cast<float4*>(out + row + j0);
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const int j = j0 + jj;
-        const float x = v[jj] * a.scale;
-        if (j >= i) out[row + j] = x;
-        if (j > i) out[(size_t)j * ld + i] = x;
-      }
+    for (int q = 0; q < 8; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    if (a.sym) {
+      if (!above) __syncwarp();
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj)
+        if (above || j0 + jj > i) out[(size_t)(j0 + jj) * ld + i] = v[jj];
     }
   } else if constexpr (EPI == TC_EPI_STORE_LP) {
     T* out = reinterpret_cast<T*>(a.out) + moff;
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj) v[jj] *= a.scale;
-    if (!a.sym || above) {
-      store32_lp<T>(out + row + j0, v);
-      if (a.sym) {
+    store32_lp<T>(out + row + j0, v);
+    if (a.sym) {
+      if (!above) __syncwarp();
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
-      }
-    } else {
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) {
-        const int j = j0 + jj;
-        const T x = from_f32<T>(v[jj]);
-        if (j >= i) out[row + j] = x;
-        if (j > i) out[(size_t)j * ld + i] = x;
-      }
+      for (int jj = 0; jj < 32; ++jj)
+        if (above || j0 + jj > i) out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
     }
   } else if constexpr (EPI == TC_EPI_NS_SYRK || EPI == TC_EPI_NS_UPDATE) {
     // SYRK:   E  = I - X^2 restricted to the logical d x d block, with the
@@ -202,14 +198,20 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
     const size_t plane = (size_t)ld * ld;
     if constexpr (EPI == TC_EPI_NS_SYRK) {
       const bool row_real = i < d_real;
+      // the chunk's squares are summed in FP32 (32 terms, relative error
+      // below 2e-6, ample for the stop rule) and added to the FP64 tile sum
+      // once: FP64 arithmetic per element would cost far more than the MMAs
+      // of a small-K tile on this GPU
+      float accf = 0.0f;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int j = j0 + jj;
         const bool real = row_real && (j < d_real);
         const float e = real ? ((i == j ? 1.0f : 0.0f) - v[jj]) : 0.0f;
         v[jj] = e;
-        if (real && j >= i) acc1 += (j > i ? 2.0 : 1.0) * (double)e * (double)e;
+        if (real && j >= i) accf = fmaf((j > i ? 2.0f : 1.0f) * e, e, accf);
       }
+      acc1 += (double)accf;
     } else {
       const T* xin = reinterpret_cast<const T*>(a.xin) + moff;
       float x[32];
@@ -237,65 +239,70 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) lo[jj] = v[jj] - to_f32<T>(from_f32<T>(v[jj]));
     }
-    if (above) {
-      store32_lp<T>(out + row + j0, v);
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
-      if (a.split) {
-        store32_lp<T>(out + plane + row + j0, lo);
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) out[plane + (size_t)(j0 + jj) * ld + i] = from_f32<T>(lo[jj]);
-      }
-    } else {
+    store32_lp<T>(out + row + j0, v);
+    if (a.split) store32_lp<T>(out + plane + row + j0, lo);
+    if (!above) __syncwarp();
+    {
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
-        const int j = j0 + jj;
-        const T x = from_f32<T>(v[jj]);
-        if (j >= i) out[row + j] = x;
-        if (j > i) out[(size_t)j * ld + i] = x;
-        if (a.split) {
-          const T y = from_f32<T>(lo[jj]);
-          if (j >= i) out[plane + row + j] = y;
-          if (j > i) out[plane + (size_t)j * ld + i] = y;
-        }
+        if (!above && j0 + jj <= i) continue;
+        out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
+        if (a.split) out[plane + (size_t)(j0 + jj) * ld + i] = from_f32<T>(lo[jj]);
       }
     }
   } else {  // TC_EPI_OZAKI
-    // The group sums are exact integers (< 2^24).  They are combined as one
-    // int64 fixed-point value V = sum_g acc_g 2^(group_shift[g]) kept in the
-    // output buffer between groups; the last group converts V to FP64 once,
-    // applies the row/column scales and adds the exact diagonal terms.
-    double* out = reinterpret_cast<double*>(a.out);
-    long long* outi = reinterpret_cast<long long*>(a.out);
-    const bool first = (g == 0);
+    // The group sums are exact integers (< 2^24).  They are combined as
+    // int64 fixed-point values V = sum_g acc_g 2^(group_shift[g]) (one per
+    // super-group of levels) kept in memory between groups; the last group
+    // converts to FP64 once, applies the row/column scales, adds the exact
+    // diagonal terms and, optionally, the FP64 input xin64.  Only the direct
+    // (upper) element is carried between groups; the mirror is written once.
+    double* out = reinterpret_cast<double*>(a.out) + moff;
+    long long* outi = reinterpret_cast<long long*>(out);
+    const bool two = a.n_sg == 2;
+    const int sg = two ? a.group_sg[g] : 0;
+    long long* accp = (two && sg == 0) ? a.acc64 + moff : outi;
+    const bool first = two ? (a.group_first[g] != 0) : (g == 0);
     const bool last = (g == a.n_groups - 1);
     const int shift = a.group_shift[g];
     const bool with_diag = last && a.a_full != nullptr;
-    const double ri = last ? a.rs[i] * a.final_scale : 0.0;
-    const double dai = with_diag ? a.a_diag[i] : 0.0;
+    const double* rs = a.rs + voff;
+    const double* cs = a.cs + voff;
+    const double ri = last ? rs[i] * (two ? 1.0 : a.final_scale) : 0.0;
+    const double dai = with_diag ? a.a_diag[voff + i] : 0.0;
+    const double* a_full = with_diag ? a.a_full + moff : nullptr;
+    const double* b_full = with_diag ? a.b_full + moff : nullptr;
+    float accf = 0.0f;
 #pragma unroll 4
     for (int jj = 0; jj < 32; ++jj) {
       const int j = j0 + jj;
-      const bool direct = !a.sym || j >= i;
       const bool mirror = a.sym && j > i;
-      if (!direct && !mirror) continue;
-      const size_t e = direct ? row + j : (size_t)j * ld + i;
+      if (a.sym && j < i) continue;
+      const size_t e = row + j;
       long long vv = (long long)__float2int_rn(v[jj]) * (1ll << shift);
-      if (!first) vv += outi[e];
+      if (!first) vv += accp[e];
       if (!last) {
-        outi[e] = vv;
-        if (direct && mirror) outi[(size_t)j * ld + i] = vv;
+        accp[e] = vv;
         continue;
       }
-      double x = (double)vv * ri * a.cs[j];
+      double x = two ? ((double)vv * a.sg_weight[1] + (double)a.acc64[moff + e] * a.sg_weight[0]) : (double)vv;
+      x *= ri * cs[j];
       if (with_diag) {
         // exact diagonal terms: d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
-        const double dbj = a.b_diag[j];
-        x += dai * a.b_full[row + j] + a.a_full[row + j] * dbj - (i == j ? dai * dbj : 0.0);
+        const double dbj = a.b_diag[voff + j];
+        x += dai * b_full[e] + a_full[e] * dbj - (i == j ? dai * dbj : 0.0);
+      }
+      if (a.xin64 != nullptr) x = a.xin64[moff + e] + a.xin_mult * x;
+      if (a.oz_ident) {
+        const bool real = i < d_real && j < d_real;
+        x = real ? ((i == j ? 1.0 : 0.0) - x) : 0.0;
+        const float xf = (float)x;
+        if (real) accf = fmaf(mirror ? 2.0f * xf : xf, xf, accf);
       }
       out[e] = x;
-      if (direct && mirror) out[(size_t)j * ld + i] = x;
+      if (mirror) out[(size_t)j * ld + i] = x;
     }
+    acc1 += (double)accf;
   }
 }
 
@@ -446,6 +453,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (u.skip) continue;
       const int i = u.bm * BM + r;
       const size_t moff = (size_t)u.mat * (size_t)args.mat_stride;
+      const size_t voff = (size_t)u.mat * (size_t)args.mat_vec_stride;
       const int d_real = args.units != nullptr ? args.mat_d[u.mat] : args.d_real;
       double acc1 = 0.0;
       for (int g = 0; g < args.n_groups; ++g) {
@@ -459,20 +467,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (!got) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN);
+        const int wrow0 = u.bm * BM + quad * 32;  // first row of this warp
         for (int c = 0; c < BN / 32; ++c) {
+          const int j0 = u.bn * BN + c * 32;
+          // symmetric schedule: a chunk wholly below this warp's rows is the
+          // mirror image of elements that their row owners write
+          if (args.sym && j0 + 31 < wrow0) continue;
           float v[32];
           tmem_ld32(taddr + (uint32_t)(c * 32), v);
-          const int j0 = u.bn * BN + c * 32;
           // chunk lies strictly above the diagonal for every row of this warp
-          const bool above = (j0 > u.bm * BM + BM - 1);
-          epilogue_chunk<EPI, T>(args, i, j0, g, v, above, acc1, moff, d_real);
+          const bool above = j0 > wrow0 + 31;
+          epilogue_chunk<EPI, T>(args, i, j0, g, v, above, acc1, moff, voff, d_real);
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&tempty[acc]));
         ++acc_it;
       }
       if (!ok) break;
-      if constexpr (EPI == TC_EPI_NS_SYRK || EPI == TC_EPI_NS_UPDATE) {
+      if (EPI == TC_EPI_NS_SYRK || EPI == TC_EPI_NS_UPDATE || (EPI == TC_EPI_OZAKI && args.oz_ident)) {
         const double s = warp_sum(acc1);
         if (lane == 0) args.partials[(size_t)u.slot * 4 + quad] = s;
       }
@@ -599,7 +611,12 @@ cudaError_t dispatch_grouped(const TcGemmArgs& a, const CUtensorMap& ma, const C
     case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, 1, BN>(a, ma, mb, grid, idesc, st);
     case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, 1, BN>(a, ma, mb, grid, idesc, st);
     case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, 1, BN>(a, ma, mb, grid, idesc, st);
-    default: return cudaErrorInvalidValue;  // the digit-plane epilogue has no grouped form
+    case TC_EPI_OZAKI:
+      if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value)
+        return launch<TC_EPI_OZAKI, T, 1, BN>(a, ma, mb, grid, idesc, st);
+      else
+        return cudaErrorInvalidValue;  // digit planes are FP16
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -640,7 +657,7 @@ cudaError_t tc_gemm_grouped(const TcGemmArgs& args, int bn, const void* A, int a
                             int b_slices, int lp_fmt, int num_sms, cudaStream_t st) {
   if (args.units == nullptr || args.n_units < 1 || args.mat_dp == nullptr || args.mat_d == nullptr ||
       (bn != 128 && bn != 256) || args.dp % 256 != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
-      args.group_start[args.n_groups] > kTcMaxPairs || args.epi == TC_EPI_OZAKI)
+      args.group_start[args.n_groups] > kTcMaxPairs || (args.epi == TC_EPI_OZAKI && lp_fmt != 0))
     return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) || !make_map(&mb, B, args.dp, b_slices, bn, lp_fmt))

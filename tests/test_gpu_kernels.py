@@ -116,3 +116,33 @@ def test_fp64grade_product_matches_fp64(dp, d_real, sym):
     assert ((out - ref).abs() - bound).max().item() <= 0.0
     if sym:
         assert (out - out.T).abs().max().item() == 0.0
+
+
+@pytest.mark.parametrize("dp,d_real,sym", [(256, 200, 1), (512, 512, 0), (1024, 1000, 1), (8192, 8192, 1)])
+def test_fp64e_product_is_fp64_accurate(dp, d_real, sym):
+    # FP64-emulating digit-plane product (>= 54 bits per operand): within a
+    # few FP64 roundings of the exact product, like a native FP64 GEMM
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    g = torch.Generator(device="cuda").manual_seed(7 * dp + d_real)
+    A = torch.zeros((dp, dp), device="cuda", dtype=torch.float64)
+    a = torch.randn((d_real, d_real), generator=g, device="cuda", dtype=torch.float64)
+    A[:d_real, :d_real] = 0.5 * (a + a.T) * torch.logspace(-4, 0, d_real, device="cuda", dtype=torch.float64)
+    A = 0.5 * (A + A.T)
+    A.diagonal()[:d_real] += 3.0  # a heavy exact diagonal, as in a near-involution
+    if sym:
+        B = A
+    else:
+        B = torch.zeros_like(A)
+        b = torch.randn((d_real, d_real), generator=g, device="cuda", dtype=torch.float64)
+        B[:d_real, :d_real] = 0.5 * (b + b.T)
+    out = rs.dbg_fp64e_gemm(A, B, d_real=d_real, sym=sym)
+    # reference: A = hi + lo (hi the FP32 rounding), each part multiplied in
+    # FP64, so the reference itself is within ~u K |A||B| of the exact product
+    hi = A.float().double()
+    ref = hi @ B + (A - hi) @ B
+    torch.cuda.synchronize()
+    bound = 8 * 2.0 ** -53 * (A.abs() @ B.abs()) * (d_real ** 0.5)
+    assert ((out - ref).abs() - bound).max().item() <= 0.0
+    if sym:
+        assert (out - out.T).abs().max().item() == 0.0

@@ -86,6 +86,25 @@ def test_low_stage_then_fp64_polish():
     assert spec_norm_sym(R - R_ex) < 2e-2
 
 
+@pytest.mark.parametrize("policy", ["FP16_POLISH", "BF16_POLISH"])
+def test_polish_steps_equal_fp64_newton_schulz_steps(policy):
+    # The polish runs FP64-emulating tensor-core products; two of its steps
+    # from the low-precision result must agree with two naive FP64 steps of
+    # the oracle from the same iterate (polish_steps = 0 returns that iterate).
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 700, 6
+    spec = workloads.controlled_spectrum(d, k, 0.05, seed=21)
+    X0, i0, st0 = _run(rs, torch, spec.H, k, 0.0, rs.Policy[policy], polish_steps=0)
+    X2, i2, st2 = _run(rs, torch, spec.H, k, 0.0, rs.Policy[policy], polish_steps=2)
+    assert i0.steps_low == i2.steps_low and i2.steps_fp64 == 2
+    ref = oracle.ns_iterates(X0, 2)
+    assert np.max(np.abs(X2 - ref[2])) < 1e-13
+    # the reported residual is ||X_2^2 - I||_F of the returned iterate
+    res = np.linalg.norm(ref[2] @ ref[2] - np.eye(d))
+    assert abs(i2.resid_fro - res) <= 1e-13 + 0.1 * res
+
+
 def test_host_pointers_roundtrip():
     torch = cuda_or_skip()
     rs = lib_or_fail()
