@@ -61,6 +61,11 @@ __global__ void batch_ingest_kernel(const double* const* __restrict__ H, const i
   double* Am = A + (size_t)m * D * D;
   const int nbj = D / 32;
   const bool inside = bi * 32 < d && bj * 32 < d;
+  if (!inside) {  // padding block: zeros, no arithmetic (block-uniform)
+    for (int r = ty; r < 32; r += 8) Am[(size_t)(bi * 32 + r) * D + bj * 32 + tx] = 0.0;
+    if (ty == 0) rowpart[((size_t)m * nbj + bj) * D + bi * 32 + tx] = 0.0;
+    return;
+  }
   bool bad = false;
   for (int r = ty; r < 32; r += 8) {
     const int i = bi * 32 + r, j = bj * 32 + tx;
@@ -455,7 +460,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     }
 
     int tile_bn = 64;
-    // tile table chosen for the low-precision stage (reused by the polish)
+    // 128-column tile table of the low-precision stage (reused by the polish)
     int4* units_sel = nullptr;
     int n_units_sel = 0;
     int* slot_sel = nullptr;
@@ -604,10 +609,12 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
       tile_bn = cand_bn[choice];
       int* slot_use = choice == 0 ? slot_lp : slot_lp2;
       const TcGemmArgs sy = syrk_args(choice);
-      units_sel = units_c[choice];
-      n_units_sel = (int)ulp[choice].size();
-      slot_sel = slot_use;
-      mat_dp_sel = choice == 0 ? ia(I_DP128) : ia(I_DP256);
+      // the FP64 polish uses the 128-column tiles (its int64 sums live in
+      // TMEM next to two 128-column accumulators)
+      units_sel = units_c[0];
+      n_units_sel = (int)ulp[0].size();
+      slot_sel = slot_lp;
+      mat_dp_sel = ia(I_DP128);
       TcGemmArgs up = sy;
       up.epi = TC_EPI_NS_UPDATE;
       const double u = fmt ? 0.00390625 : 0.00048828125;  // unit roundoff of the operand type
@@ -660,6 +667,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
       SplitMat Xs{}, Es{};
       Xs.n_planes = Es.n_planes = P;
       Xs.beta = Es.beta = beta;
+      Xs.keep_diag = Es.keep_diag = 1;  // 54-bit digits of the whole rows: no exact diagonal terms needed
       long long* acc64 = nullptr;
       if (beta == 0 || mem.alloc(&Xs.planes, nel * 2 * P) != cudaSuccess ||
           mem.alloc(&Es.planes, nel * 2 * P) != cudaSuccess ||
@@ -676,7 +684,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
       base.units = units_sel;
       base.n_units = n_units_sel;
       base.n_mat = ng;
-      base.bn = tile_bn;
+      base.bn = 128;
       base.mat_dp = mat_dp_sel;
       base.mat_d = ia(I_D);
       base.mat_skip = ia(I_DONE64);

@@ -70,7 +70,10 @@ struct TcGemmArgs {
   double sg_weight[2];
   long long* acc64;                // dp x dp (per matrix) int64 scratch of super-group 0
   const double* xin64;             // optional: out = xin64 + xin_mult * (product)
-  double xin_mult;
+  double xin_mult;                 // a power of two
+  int xin_mult_exp;                // log2(xin_mult)
+  int oz_unit_exp;                 // log2 of the weight of one unit of the (last) int64 sum
+  int oz_sh01;                     // n_sg == 2: super-group 0's unit over super-group 1's, log2
   int oz_ident;                    // 1: out = I - (product) on the logical d x d block (0
                                    // outside) with ||out||_F^2 partials in `partials`
   float scale;
@@ -255,6 +258,7 @@ struct SplitMat {
   const double* full;  // the FP64 matrix itself (dp x dp), not owned
   int n_planes = kSlices;   // digit planes (n_planes * beta <= 56)
   int beta = kSliceBeta;    // bits per digit
+  int keep_diag = 0;        // 1: the diagonal is in the digits (no exact diagonal terms)
 };
 // Split the FP64 matrix M (dp x dp, symmetric) into digit planes; out.full = M.
 cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st);
@@ -272,7 +276,7 @@ int fp64e_planes(int beta);
 struct Fp64eExtra {
   long long* acc64 = nullptr;       // int64 scratch (dp x dp per matrix) when two sums are needed
   const double* xin64 = nullptr;    // out = xin64 + xin_mult * product
-  double xin_mult = 1.0;
+  double xin_mult = 1.0;            // a power of two
   int ident = 0;                    // out = I - product (logical block) with residual partials
   double* partials = nullptr;       // 4 per tile (ident)
   const int* skip = nullptr;

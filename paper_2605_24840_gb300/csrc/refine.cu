@@ -20,52 +20,85 @@ namespace {
 constexpr int TILE = 32;
 
 // ------------------------------------------------------------ digit planes
-__global__ void split_rows_kernel(const double* __restrict__ M, int ld, __half* __restrict__ planes,
+// value = mant 2^e2 exactly (mant < 2^53), for finite x
+__device__ __forceinline__ void f64_parts(long long bits, unsigned long long& mant, int& e2) {
+  const int E = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long frac = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
+  mant = E ? (frac | (1ull << 52)) : frac;
+  e2 = E ? E - 1075 : -1074;
+}
+
+// Digit planes of one row per warp (8 rows per block; grid.y = matrix).
+// Everything is integer arithmetic on the FP64 bit patterns: the row scale
+// sigma_i = 2^ex comes from the largest off-diagonal magnitude (compared as
+// bit patterns, which order like the values), each entry becomes the
+// fixed-point integer n = round(M_ik 2^(62 - ex)), |n| < 2^61, by a shift of
+// its significand, and the balanced base-2^beta digits are peeled off with
+// shifts; the FP64 pipe of this GPU is far slower than its integer pipe.
+// Lane l handles the column pairs 2 l + 64 t, 2 l + 64 t + 1 (half2 stores).
+__global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrows, __half* __restrict__ planes,
                                   double* __restrict__ sigma, double* __restrict__ diag, int n_planes,
-                                  int beta, const int* __restrict__ mat_dp) {
-  __shared__ double sh[32];
-  __shared__ int e_sh;
-  // block (i, m): row i of matrix m (grouped: matrix m in slot m of a slab,
-  // planes [m][n_planes][ld][ld]); single matrix: m = 0, every row
-  const int i = blockIdx.x, m = blockIdx.y;
-  const int ncols = mat_dp != nullptr ? mat_dp[m] : ld;
-  if (i >= ncols) return;  // outside the matrix's padded order: never read
+                                  int beta, const int* __restrict__ mat_dp, int keep_diag) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int m = blockIdx.y;
+  const int ncols = mat_dp != nullptr ? mat_dp[m] : nrows;
+  if (i >= ncols) return;  // outside the matrix's padded order: never read (warp-uniform)
   const size_t slot = (size_t)ld * ld;
-  const double* row = M + (size_t)m * slot + (size_t)i * ld;
-  double m_abs = 0.0;
-  for (int k = threadIdx.x; k < ncols; k += blockDim.x)
-    if (k != i) m_abs = fmax(m_abs, fabs(row[k]));
-  if (threadIdx.x == 0) diag[(size_t)m * ld + i] = row[i];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m_abs = fmax(m_abs, __shfl_xor_sync(0xffffffffu, m_abs, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m_abs;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double mm = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, sh[w]);
-    int ex = 0;
-    if (mm > 0.0) {
-      frexp(mm, &ex);  // mm = f 2^ex, f in [0.5, 1): 2 mm < 2^(ex+1)
-      ex += 1;
-    }
-    e_sh = ex;
-    sigma[(size_t)m * ld + i] = ldexp(1.0, ex);
+  const long long* row = reinterpret_cast<const long long*>(M + (size_t)m * slot + (size_t)i * ld);
+  long long mx = 0;
+  for (int k = 2 * lane; k < ncols; k += 64) {
+    const long long b0 = row[k] & 0x7FFFFFFFFFFFFFFFll, b1 = row[k + 1] & 0x7FFFFFFFFFFFFFFFll;
+    if (k != i || keep_diag) mx = b0 > mx ? b0 : mx;
+    if (k + 1 != i || keep_diag) mx = b1 > mx ? b1 : mx;
   }
-  __syncthreads();
-  const int ex = e_sh;
-  __half* pl = planes + (size_t)m * n_planes * slot + (size_t)i * ld;
-  // r = M_ik 2^-ex in (-1/2, 1/2) as a fixed-point integer with 62 fraction
-  // bits (one exact FP64 scaling and one conversion); the balanced base-2^beta
-  // digits are then peeled off with integer shifts: the FP64 pipe of this GPU
-  // is far slower than its integer pipe.  n_planes * beta <= 56.
-  const double to_fixed = ldexp(1.0, 62 - ex);
-  for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
-    long long n = (k == i) ? 0ll : __double2ll_rn(row[k] * to_fixed);  // diagonal kept apart
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = t > mx ? t : mx;
+  }
+  int ex = 0;
+  if (mx != 0) {
+    unsigned long long mant;
+    int e2;
+    f64_parts(mx, mant, e2);
+    const int lb = 63 - __clzll((long long)mant) + e2;  // 2^lb <= max < 2^(lb+1)
+    ex = lb + 2;                                        // 2 max < 2^ex
+  }
+  if (lane == 0) {
+    sigma[(size_t)m * ld + i] = __longlong_as_double((long long)(ex + 1023) << 52);
+    diag[(size_t)m * ld + i] = __longlong_as_double(row[i]);
+  }
+  __half2* pl = reinterpret_cast<__half2*>(planes + (size_t)m * n_planes * slot + (size_t)i * ld);
+  const size_t pslot = slot / 2;
+  for (int k = 2 * lane; k < ncols; k += 64) {
+    long long n[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long bits = row[k + h];
+      long long v = 0;
+      if ((k + h != i || keep_diag) && (bits & 0x7FFFFFFFFFFFFFFFll) != 0) {  // diagonal kept apart unless keep_diag
+        unsigned long long mant;
+        int e2;
+        f64_parts(bits, mant, e2);
+        const int sh = e2 + 62 - ex;  // n = mant 2^sh, rounded to an integer
+        unsigned long long q;
+        if (sh >= 0) q = mant << sh;
+        else if (sh > -64) q = (mant + (1ull << (-sh - 1))) >> (-sh);
+        else q = 0;
+        v = bits < 0 ? -(long long)q : (long long)q;
+      }
+      n[h] = v;
+    }
     for (int p = 0; p < n_planes; ++p) {
-      const int sh = 62 - beta * (p + 1);                      // weight of digit p: 2^sh
-      const long long dg = (n + (1ll << (sh - 1))) >> sh;      // nearest, |dg| <= 2^(beta-1)
-      n -= dg * (1ll << sh);                                   // |n| <= 2^(sh-1)
-      pl[p * slot + k] = __int2half_rn((int)dg);
+      const int sh = 62 - beta * (p + 1);  // weight of digit p: 2^sh
+      long long dg[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        dg[h] = (n[h] + (1ll << (sh - 1))) >> sh;  // nearest, |dg| <= 2^(beta-1)
+        n[h] -= dg[h] * (1ll << sh);               // |n| <= 2^(sh-1)
+      }
+      pl[p * pslot + (k >> 1)] = __halves2half2(__int2half_rn((int)dg[0]), __int2half_rn((int)dg[1]));
     }
   }
 }
@@ -322,16 +355,16 @@ int grid_for(size_t n) {
 
 cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st) {
   if (out.n_planes < 1 || out.n_planes * out.beta > 56 || out.beta < 2 || out.beta > 11) return cudaErrorInvalidValue;
-  split_rows_kernel<<<dim3(dp, 1), 256, 0, st>>>(M, dp, (__half*)out.planes, out.sigma, out.diag, out.n_planes,
-                                                 out.beta, nullptr);
+  split_rows_kernel<<<dim3((dp + 7) / 8, 1), 256, 0, st>>>(M, dp, dp, (__half*)out.planes, out.sigma, out.diag,
+                                                           out.n_planes, out.beta, nullptr, out.keep_diag);
   return cudaGetLastError();
 }
 
 cudaError_t split_rows_grouped(const double* M, int D, int n_mat, const int* mat_dp, SplitMat out,
                                cudaStream_t st) {
   if (out.n_planes < 1 || out.n_planes * out.beta > 56 || out.beta < 2 || out.beta > 11) return cudaErrorInvalidValue;
-  split_rows_kernel<<<dim3(D, n_mat), 256, 0, st>>>(M, D, (__half*)out.planes, out.sigma, out.diag, out.n_planes,
-                                                    out.beta, mat_dp);
+  split_rows_kernel<<<dim3((D + 7) / 8, n_mat), 256, 0, st>>>(M, D, D, (__half*)out.planes, out.sigma, out.diag,
+                                                              out.n_planes, out.beta, mat_dp, out.keep_diag);
   return cudaGetLastError();
 }
 
@@ -383,6 +416,7 @@ cudaError_t fp64e_plan(TcGemmArgs* a, int n_planes, int beta, int levels, int k_
     return b;
   };
   const double lim = std::ldexp(1.0, 62);
+  a->oz_unit_exp = -beta * (L - 1 + 2);
   if (bound(0, L - 1) < lim) {
     a->n_sg = 0;
     for (int g = 0; g < ng; ++g) a->group_shift[g] = beta * (L - 1 - group_level[g]);
@@ -403,6 +437,7 @@ cudaError_t fp64e_plan(TcGemmArgs* a, int n_planes, int beta, int levels, int k_
   }
   a->sg_weight[0] = std::ldexp(1.0, -beta * (split - 1 + 2));
   a->sg_weight[1] = std::ldexp(1.0, -beta * (L - 1 + 2));
+  a->oz_sh01 = beta * (L - 1 - (split - 1));
   return cudaSuccess;
 }
 
@@ -414,7 +449,7 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
 
 cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym, double* out,
                        const Fp64eExtra& x, int* status, int num_sms, cudaStream_t st, int levels) {
-  if (A.beta != B.beta || A.n_planes != B.n_planes) return cudaErrorInvalidValue;
+  if (A.beta != B.beta || A.n_planes != B.n_planes || A.keep_diag != B.keep_diag) return cudaErrorInvalidValue;
   TcGemmArgs a{};
   a.dp = dp;
   a.d_real = d_real;
@@ -426,13 +461,20 @@ cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
   a.cs = B.sigma;
   a.status = status;
   a.skip = x.skip;
-  a.a_full = A.full;
-  a.b_full = B.full;
+  // exact diagonal terms only for diagonal-free digits
+  a.a_full = A.keep_diag ? nullptr : A.full;
+  a.b_full = A.keep_diag ? nullptr : B.full;
   a.a_diag = A.diag;
   a.b_diag = B.diag;
   a.acc64 = x.acc64;
   a.xin64 = x.xin64;
   a.xin_mult = x.xin_mult;
+  {
+    int ex = 0;
+    const double f = std::frexp(x.xin_mult, &ex);
+    if (f != 0.5) return cudaErrorInvalidValue;  // the multiplier must be a power of two
+    a.xin_mult_exp = ex - 1;
+  }
   a.oz_ident = x.ident;
   a.partials = x.partials;
   const int kext = x.k_extent > 0 ? x.k_extent : d_real;

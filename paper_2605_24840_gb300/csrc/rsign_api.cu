@@ -186,6 +186,7 @@ cudaError_t fp64e_polish(Ctx& c, DevBuf& mem, double* xb[2], double* E, int dp, 
   SplitMat Xs{}, Es{};
   Xs.n_planes = Es.n_planes = P;
   Xs.beta = Es.beta = beta;
+  Xs.keep_diag = Es.keep_diag = 1;  // 54-bit digits of the whole rows: no exact diagonal terms needed
   long long* acc64 = nullptr;
   cudaError_t e;
   if ((e = mem.alloc(&Xs.planes, dd * 2 * P)) != cudaSuccess) return e;

@@ -148,6 +148,53 @@ __device__ __forceinline__ void load32_lp(const T* src, float* v) {
   }
 }
 
+// ---- integer-pipe conversions of the digit-plane sums (the FP64 pipe of
+// this GPU is ~2 FMA/clk/SM, its integer pipes are far wider)
+__device__ __forceinline__ int pow2_exp(double p) {  // p an exact power of two
+  return (int)((__double_as_longlong(p) >> 52) & 0x7FF) - 1023;
+}
+
+// v 2^e rounded to the nearest binary64 (ties to even), from integer ops only
+__device__ __forceinline__ double i128_scaled(__int128 v, int e) {
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  const unsigned __int128 m = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
+  int top = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading bit index
+  unsigned long long sig;
+  if (top <= 52) {
+    sig = lo << (52 - top);
+  } else {
+    const int sh = top - 52;
+    unsigned __int128 q = m >> sh;
+    const unsigned __int128 rem = m & ((((unsigned __int128)1) << sh) - 1);
+    const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+    if (q >> 53) {
+      q >>= 1;
+      ++top;
+    }
+    sig = (unsigned long long)q;
+  }
+  const int eb = top + e + 1023;
+  if (eb <= 0 || eb >= 2047) {  // outside the normal range: let the FP64 pipe handle it
+    const double f = (double)sig;
+    return ldexp(neg ? -f : f, top - 52 + e);
+  }
+  const unsigned long long bits =
+      ((unsigned long long)eb << 52) | (sig & 0xFFFFFFFFFFFFFull) | (neg ? (1ull << 63) : 0ull);
+  return __longlong_as_double((long long)bits);
+}
+
+// Final value of one element: the super-group sums V1 (last) and V0 combined
+// exactly in 128 bits, converted, scaled by sigma_i sigma_j 2^unit_exp (and
+// xin_mult when an FP64 input is added) through the exponent.
+__device__ __forceinline__ double oz_value(const TcGemmArgs& a, long long V1, long long V0, int e_ij) {
+  __int128 t = (__int128)V1;
+  if (a.n_sg == 2) t += ((__int128)V0) << a.oz_sh01;
+  return i128_scaled(t, e_ij + a.oz_unit_exp + (a.xin64 != nullptr ? a.xin_mult_exp : 0));
+}
+
 // Epilogue for one 32-column chunk held by one thread (row i, columns j0..j0+31).
 // moff: element offset of the tile's matrix in out / xin (grouped mode),
 // voff: its offset in the per-row vectors of TC_EPI_OZAKI;
@@ -268,7 +315,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
     const bool with_diag = last && a.a_full != nullptr;
     const double* rs = a.rs + voff;
     const double* cs = a.cs + voff;
-    const double ri = last ? rs[i] * (two ? 1.0 : a.final_scale) : 0.0;
+    const int ei = last ? pow2_exp(rs[i]) : 0;
     const double dai = with_diag ? a.a_diag[voff + i] : 0.0;
     const double* a_full = with_diag ? a.a_full + moff : nullptr;
     const double* b_full = with_diag ? a.b_full + moff : nullptr;
@@ -285,17 +332,16 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
         accp[e] = vv;
         continue;
       }
-      double x = two ? ((double)vv * a.sg_weight[1] + (double)a.acc64[moff + e] * a.sg_weight[0]) : (double)vv;
-      x *= ri * cs[j];
+      double x = oz_value(a, vv, two ? a.acc64[moff + e] : 0ll, ei + pow2_exp(cs[j]));
       if (with_diag) {
         // exact diagonal terms: d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
         const double dbj = a.b_diag[voff + j];
         x += dai * b_full[e] + a_full[e] * dbj - (i == j ? dai * dbj : 0.0);
       }
-      if (a.xin64 != nullptr) x = a.xin64[moff + e] + a.xin_mult * x;
+      if (a.xin64 != nullptr) x = a.xin64[moff + e] + x;
       if (a.oz_ident) {
         const bool real = i < d_real && j < d_real;
-        x = real ? ((i == j ? 1.0 : 0.0) - x) : 0.0;
+        x = real ? ((i == j) ? 1.0 - x : -x) : 0.0;
         const float xf = (float)x;
         if (real) accf = fmaf(mirror ? 2.0f * xf : xf, xf, accf);
       }
@@ -306,12 +352,99 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
   }
 }
 
+// TC_EPI_OZAKI on 128-column tiles: the int64 level sums stay in TMEM
+// (columns 256..511, unused by the two 128-column accumulators), so the
+// groups of a tile never touch global memory until the last one.  For the
+// 32-column chunk q of the tile the low words sit at columns 256 + 64 q + jj
+// and the high words at 256 + 64 q + 32 + jj (vaddr = the warp's lanes at
+// column 256 + 64 q).  Super-group 0's sum, once complete, is converted to
+// FP64 (times its weight) and parked in acc64 (as FP64) for the last group.
+// The TMEM loads and stores are warp-collective; every flag that selects
+// them depends on the group only.
+__device__ __forceinline__ void epilogue_oz_tmem(const TcGemmArgs& a, int i, int j0, int g, const float* v,
+                                                 double& acc1, size_t moff, size_t voff, int d_real,
+                                                 uint32_t vaddr) {
+  const int ld = a.dp;
+  const size_t row = (size_t)i * ld;
+  const bool two = a.n_sg == 2;
+  const int sg = two ? a.group_sg[g] : 0;
+  const bool first = two ? (a.group_first[g] != 0) : (g == 0);
+  const bool last = (g == a.n_groups - 1);
+  const bool sg_end = last || (two && a.group_sg[g + 1] != sg);
+  const int shift = a.group_shift[g];
+  uint32_t lo[32], hi[32];
+  if (!first) {
+    tmem_ld32u(vaddr, lo);
+    tmem_ld32u(vaddr + 32, hi);
+  }
+  long long V[32];
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj) {
+    V[jj] = (long long)__float2int_rn(v[jj]) * (1ll << shift);
+    if (!first) V[jj] += (long long)(((uint64_t)hi[jj] << 32) | (uint64_t)lo[jj]);
+  }
+  if (!sg_end) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      lo[jj] = (uint32_t)((uint64_t)V[jj] & 0xFFFFFFFFull);
+      hi[jj] = (uint32_t)((uint64_t)V[jj] >> 32);
+    }
+    tmem_st32u(vaddr, lo);
+    tmem_st32u(vaddr + 32, hi);
+    return;
+  }
+  long long* park = a.acc64 + moff;
+  if (!last) {  // end of super-group 0: park its sum
+#pragma unroll 4
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = j0 + jj;
+      if (a.sym && j < i) continue;
+      park[row + j] = V[jj];
+    }
+    return;
+  }
+  double* out = reinterpret_cast<double*>(a.out) + moff;
+  const bool with_diag = a.a_full != nullptr;
+  const double* rs = a.rs + voff;
+  const double* cs = a.cs + voff;
+  const int ei = pow2_exp(rs[i]);
+  const double dai = with_diag ? a.a_diag[voff + i] : 0.0;
+  const double* a_full = with_diag ? a.a_full + moff : nullptr;
+  const double* b_full = with_diag ? a.b_full + moff : nullptr;
+  float accf = 0.0f;
+#pragma unroll 4
+  for (int jj = 0; jj < 32; ++jj) {
+    const int j = j0 + jj;
+    const bool mirror = a.sym && j > i;
+    if (a.sym && j < i) continue;
+    const size_t e = row + j;
+    double x = oz_value(a, V[jj], two ? park[e] : 0ll, ei + pow2_exp(cs[j]));
+    if (with_diag) {
+      const double dbj = a.b_diag[voff + j];
+      x += dai * b_full[e] + a_full[e] * dbj - (i == j ? dai * dbj : 0.0);
+    }
+    if (a.xin64 != nullptr) x = a.xin64[moff + e] + x;
+    if (a.oz_ident) {
+      const bool real = i < d_real && j < d_real;
+      x = real ? ((i == j) ? 1.0 - x : -x) : 0.0;
+      const float xf = (float)x;
+      if (real) accf = fmaf(mirror ? 2.0f * xf : xf, xf, accf);
+    }
+    out[e] = x;
+    if (mirror) out[(size_t)j * ld + i] = x;
+  }
+  acc1 += (double)accf;
+}
+
 template <int EPI, typename T, int CL, int BN>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ TcGemmArgs args, const uint32_t idesc) {
   using C = Cfg<BN>;
   constexpr int STAGES = C::STAGES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
+  // 128-column digit-plane products keep their int64 sums in TMEM columns 256..511
+  constexpr bool OZ_TMEM = (EPI == TC_EPI_OZAKI && BN == 128);
+  constexpr uint32_t TMEM_ALLOC = OZ_TMEM ? 512u : C::TMEM_COLS;
   if (args.skip != nullptr && *args.skip != 0) return;  // uniform across the grid (and cluster)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -349,7 +482,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     prefetch_tensormap(&tmB);
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+    tmem_alloc(smem_u32(tmem_slot), TMEM_ALLOC);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -477,7 +610,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           tmem_ld32(taddr + (uint32_t)(c * 32), v);
           // chunk lies strictly above the diagonal for every row of this warp
           const bool above = j0 > wrow0 + 31;
-          epilogue_chunk<EPI, T>(args, i, j0, g, v, above, acc1, moff, voff, d_real);
+          if constexpr (OZ_TMEM) {
+            const uint32_t vaddr = tmem_base + ((uint32_t)(quad * 32) << 16) + 256u + (uint32_t)(c * 64);
+            epilogue_oz_tmem(args, i, j0, g, v, acc1, moff, voff, d_real, vaddr);
+          } else {
+            epilogue_chunk<EPI, T>(args, i, j0, g, v, above, acc1, moff, voff, d_real);
+          }
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&tempty[acc]));
@@ -500,7 +638,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem_base, C::TMEM_COLS);
+    tmem_dealloc(tmem_base, TMEM_ALLOC);
   }
 }
 
