@@ -218,6 +218,71 @@ rsign_status rsign_reflector_backward(const double* H, int64_t d, int32_t k, dou
                                       rsign_policy policy, const double* Rbar, double* Hbar,
                                       int32_t ckpt_every, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Shift policies along a sequence of slowly varying matrices H_0, H_1, ...
+ * (Sec. 4.4: Prop. 4.2 and the shift policies of Algorithm 1).
+ * ------------------------------------------------------------------------- */
+typedef enum {
+  RSIGN_SHIFT_MIDPOINT = 0,       /* refresh at every matrix: s = midpoint of the estimates    */
+  RSIGN_SHIFT_REUSE_REFRESH = 1,  /* keep s while its certified margin minus the drift bound
+                                     stays above `threshold`; otherwise refresh (Prop. 4.2)   */
+  RSIGN_SHIFT_DAMPED = 2          /* refresh at every matrix: blend of the previous shift and
+                                     the new midpoint, clipped into the certified interval    */
+} rsign_shift_policy;
+
+/* State carried from one matrix of the sequence to the next (host memory). */
+typedef struct {
+  double shift;        /* shift in use; NaN before the first refresh                       */
+  double lam_k_est;    /* Lanczos estimates of lam_k, lam_{k+1} at the last refresh         */
+  double lam_k1_est;
+  double eps;          /* their error bound (largest Ritz residual)                        */
+  double margin_cert;  /* certified margin of `shift` at the current matrix: the estimated
+                          margin minus eps at the refresh, minus every drift bound since    */
+  double drift_sum;    /* sum of the drift bounds since the last refresh                    */
+  int32_t refreshes;   /* endpoint estimations so far                                       */
+  int32_t reuses;      /* matrices that kept the previous shift                              */
+} rsign_shift_state;
+
+/* Report of one rsign_shift_update call. */
+typedef struct {
+  int32_t refreshed;     /* 1: new endpoint estimates were computed                          */
+  int32_t lanczos_iters; /* Lanczos steps of the refresh (0 when reused)                     */
+  double drift_ub;       /* upper bound of ||sym(H_new - H_old)||_2 (Weyl bound on the endpoint
+                            drift): min(||D||_F, (||D||_1 + ||D||_inf)/2), D = H_new - H_old;
+                            NaN without H_old                                               */
+  double drift_est;      /* power-step estimate of ||sym(D)||_2 (a lower bound), for comparison */
+  double margin_cert;    /* certified margin of the returned shift at H_new                  */
+} rsign_shift_report;
+
+/* Sets shift, estimates and margin to NaN and the counters to zero. */
+void rsign_shift_state_init(rsign_shift_state* state);
+
+/* Host-only rule of Prop. 4.2: 1 when the state's shift stays admissible at a
+ * matrix whose distance from the current one is at most drift_ub in the
+ * 2-norm, with certified margin margin_cert - drift_ub > max(0, threshold). */
+int32_t rsign_shift_can_reuse(const rsign_shift_state* state, double drift_ub, double threshold);
+
+/* Host-only damped midpoint: damping * s_prev + (1 - damping) * midpoint,
+ * clipped into (lam_k_est + eps, lam_k1_est - eps) shrunk by a quarter of its
+ * half-width on each side; the midpoint when s_prev is NaN or the interval empty. */
+double rsign_shift_damped(double s_prev, double lam_k_est, double lam_k1_est, double eps, double damping);
+
+/*
+ * rsign_shift_update -- the shift for H_new given the state left by H_old.
+ *   H_new, H_old  d x d (device or host); H_old = NULL at the first matrix.
+ *   REUSE_REFRESH: computes drift_ub on the GPU; if rsign_shift_can_reuse
+ *   holds, keeps state->shift and lowers state->margin_cert by drift_ub;
+ *   otherwise refreshes.  MIDPOINT and DAMPED always refresh.  A refresh runs
+ *   the GPU Lanczos of the automatic shift on H_new, sets the (damped)
+ *   midpoint and certifies it by m_hat > eps (Prop. 4.2); when that fails the
+ *   state's shift becomes NaN and RSIGN_ERR_GAP is returned.
+ *   threshold >= 0; damping in [0, 1] (DAMPED only).  The state is updated in
+ *   place; `report` is optional.  Blocking.
+ */
+rsign_status rsign_shift_update(const double* H_new, const double* H_old, int64_t d, int32_t k,
+                                rsign_shift_policy policy, double threshold, double damping,
+                                rsign_shift_state* state, rsign_shift_report* report, void* stream);
+
 /*
  * rsign_reflector_noalloc -- the FP64-policy reflector (same result as
  * rsign_reflector with RSIGN_FP64) for callers that cannot allocate device

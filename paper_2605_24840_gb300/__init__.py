@@ -80,6 +80,33 @@ class Options(ctypes.Structure):
     ]
 
 
+class ShiftPolicy(enum.IntEnum):
+    MIDPOINT = 0
+    REUSE_REFRESH = 1
+    DAMPED = 2
+
+
+class ShiftState(ctypes.Structure):
+    _fields_ = [
+        ("shift", ctypes.c_double), ("lam_k_est", ctypes.c_double), ("lam_k1_est", ctypes.c_double),
+        ("eps", ctypes.c_double), ("margin_cert", ctypes.c_double), ("drift_sum", ctypes.c_double),
+        ("refreshes", ctypes.c_int32), ("reuses", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ShiftReport(ctypes.Structure):
+    _fields_ = [
+        ("refreshed", ctypes.c_int32), ("lanczos_iters", ctypes.c_int32), ("drift_ub", ctypes.c_double),
+        ("drift_est", ctypes.c_double), ("margin_cert", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class RsignError(RuntimeError):
     def __init__(self, status, msg=""):
         self.status = Status(status)
@@ -127,6 +154,15 @@ def load():
                                                ctypes.POINTER(dbl), dbl, ctypes.c_int, ctypes.POINTER(Options),
                                                ctypes.POINTER(vp), ctypes.POINTER(Info), vp]
     lib.rsign_reflector_batched_ex.restype = ctypes.c_int
+    lib.rsign_shift_state_init.argtypes = [ctypes.POINTER(ShiftState)]
+    lib.rsign_shift_state_init.restype = None
+    lib.rsign_shift_can_reuse.argtypes = [ctypes.POINTER(ShiftState), dbl, dbl]
+    lib.rsign_shift_can_reuse.restype = i32
+    lib.rsign_shift_damped.argtypes = [dbl, dbl, dbl, dbl, dbl]
+    lib.rsign_shift_damped.restype = dbl
+    lib.rsign_shift_update.argtypes = [vp, vp, i64, i32, ctypes.c_int, dbl, dbl, ctypes.POINTER(ShiftState),
+                                       ctypes.POINTER(ShiftReport), vp]
+    lib.rsign_shift_update.restype = ctypes.c_int
     lib.rsign_reflector_backward.argtypes = [vp, i64, i32, dbl, ctypes.c_int, vp, vp, i32, vp]
     lib.rsign_reflector_backward.restype = ctypes.c_int
     lib.rsign_status_str.argtypes = [ctypes.c_int]
@@ -292,6 +328,42 @@ def reflector_batched(Hs, ks, ss, tol=1e-12, policy=Policy.FP64, outs=None, opti
     st = Status(lib.rsign_reflector_batched_ex(n, hp, dd, kk, sv, float(tol), int(policy), optp, rp, infos,
                                                _stream_ptr(stream, any_cuda)))
     return outs, list(infos), st
+
+
+def shift_state() -> ShiftState:
+    """A fresh shift-policy state (no shift yet)."""
+    st = ShiftState()
+    load().rsign_shift_state_init(ctypes.byref(st))
+    return st
+
+
+def shift_can_reuse(state: ShiftState, drift_ub: float, threshold: float = 0.0) -> bool:
+    """Prop. 4.2 reuse rule on the host (rsign_shift_can_reuse)."""
+    return bool(load().rsign_shift_can_reuse(ctypes.byref(state), float(drift_ub), float(threshold)))
+
+
+def shift_damped(s_prev, lam_k_est, lam_k1_est, eps, damping) -> float:
+    """Damped midpoint clipped into the certified interval (rsign_shift_damped)."""
+    return float(load().rsign_shift_damped(float(s_prev), float(lam_k_est), float(lam_k1_est), float(eps),
+                                           float(damping)))
+
+
+def shift_update(H_new, H_old, k, state: ShiftState, policy=ShiftPolicy.REUSE_REFRESH, threshold=0.0,
+                 damping=0.5, stream=None):
+    """Shift for H_new given the state left by H_old (rsign_shift_update).
+
+    Updates ``state`` in place and returns (status, report)."""
+    lib = load()
+    d = int(H_new.shape[0])
+    hp, hk, hc = _ptr_of(H_new, "H_new", (d, d))
+    if H_old is not None:
+        op, ok, oc = _ptr_of(H_old, "H_old", (d, d))
+    else:
+        op, ok, oc = None, None, False
+    rep = ShiftReport()
+    st = Status(lib.rsign_shift_update(hp, op, d, int(k), int(policy), float(threshold), float(damping),
+                                       ctypes.byref(state), ctypes.byref(rep), _stream_ptr(stream, hc or oc)))
+    return st, rep
 
 
 def reflector_backward(H, k, s, Rbar, policy=Policy.FP64, ckpt_every=4, out=None, stream=None):

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librsign.so")
-SOURCES = ["tc_gemm.cu", "f64_kernels.cu", "refine.cu", "lanczos.cu", "rsign_api.cu", "batched.cu", "noalloc.cu"]
+SOURCES = ["tc_gemm.cu", "f64_kernels.cu", "refine.cu", "lanczos.cu", "rsign_api.cu", "batched.cu", "shift.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
