@@ -62,7 +62,11 @@ typedef enum {
   RSIGN_BF16_POLISH = 4,  /* BF16 steps followed by `polish_steps` FP64 NS steps          */
   RSIGN_FP16_REFINE = 5,  /* FP16 steps, then commutator refinement sweeps with
                              FP64-grade products until the correction falls below tol   */
-  RSIGN_BF16_REFINE = 6   /* BF16 steps, then the same refinement                        */
+  RSIGN_BF16_REFINE = 6,  /* BF16 steps, then the same refinement                        */
+  RSIGN_FP32 = 7          /* FP32-class steps: iterates carried as FP16 hi/lo pairs (22-bit
+                             significands, the fused pair products hi*hi + hi*lo + lo*hi
+                             with FP32 accumulation), no FP64 stage: accuracy floor
+                             ~ u_fp32 ||H|| / gap                                        */
 } rsign_policy;
 
 /* Scaling rule for alpha (Sec. 4.3 scaling discussion). */
@@ -212,7 +216,11 @@ rsign_status rsign_reflector_batched_ex(int32_t n, const double* const* H, const
  * unrolled) with s and alpha held fixed: given Rbar = dL/dR (d x d),
  * returns Hbar = dL/dH (symmetrised, d x d).  The recurrence is run backward
  * over checkpoints of the forward iterates taken every `ckpt_every` steps.
- * The policy selects the arithmetic of the forward and backward steps.
+ * The policy selects the arithmetic of the forward and backward steps:
+ * FP64 (checkpointed FP64 recomputation); FP16/BF16 and *_REFINE (the
+ * stage-1 trajectory kept whole, tangent products in the operand type);
+ * *_POLISH (the same, preceded by the FP64 adjoint of the two FP64 polish
+ * steps of the default forward).  Device or host pointers; blocking.
  */
 rsign_status rsign_reflector_backward(const double* H, int64_t d, int32_t k, double s,
                                       rsign_policy policy, const double* Rbar, double* Hbar,
@@ -247,10 +255,11 @@ typedef struct {
 typedef struct {
   int32_t refreshed;     /* 1: new endpoint estimates were computed                          */
   int32_t lanczos_iters; /* Lanczos steps of the refresh (0 when reused)                     */
-  double drift_ub;       /* upper bound of ||sym(H_new - H_old)||_2 (Weyl bound on the endpoint
-                            drift): min(||D||_F, (||D||_1 + ||D||_inf)/2), D = H_new - H_old;
-                            NaN without H_old                                               */
-  double drift_est;      /* power-step estimate of ||sym(D)||_2 (a lower bound), for comparison */
+  double drift_ub;       /* the drift bound used (Weyl bound on the endpoint drift): the
+                            caller's drift_bound, else min(||D||_F, (||D||_1 + ||D||_inf)/2)
+                            for D = H_new - H_old; NaN without either                       */
+  double drift_est;      /* power-step estimate of ||sym(D)||_2 (a lower bound) when H_old is
+                            given, for comparison; NaN otherwise                             */
   double margin_cert;    /* certified margin of the returned shift at H_new                  */
 } rsign_shift_report;
 
@@ -270,9 +279,15 @@ double rsign_shift_damped(double s_prev, double lam_k_est, double lam_k1_est, do
 /*
  * rsign_shift_update -- the shift for H_new given the state left by H_old.
  *   H_new, H_old  d x d (device or host); H_old = NULL at the first matrix.
- *   REUSE_REFRESH: computes drift_ub on the GPU; if rsign_shift_can_reuse
- *   holds, keeps state->shift and lowers state->margin_cert by drift_ub;
- *   otherwise refreshes.  MIDPOINT and DAMPED always refresh.  A refresh runs
+ *   drift_bound   a caller-certified bound on ||H_new - H_old||_2 (for
+ *                 instance a Hessian Lipschitz constant times the step
+ *                 length), or NaN: then the GPU computes the rigorous bound
+ *                 min(||D||_F, (||D||_1 + ||D||_inf)/2) from H_old, which is
+ *                 tight for low-rank changes and up to sqrt(d) loose for
+ *                 spread-out ones.
+ *   REUSE_REFRESH: if rsign_shift_can_reuse holds for the drift bound, keeps
+ *   state->shift and lowers state->margin_cert by it; otherwise refreshes.
+ *   MIDPOINT and DAMPED always refresh.  A refresh runs
  *   the GPU Lanczos of the automatic shift on H_new, sets the (damped)
  *   midpoint and certifies it by m_hat > eps (Prop. 4.2); when that fails the
  *   state's shift becomes NaN and RSIGN_ERR_GAP is returned.
@@ -281,7 +296,8 @@ double rsign_shift_damped(double s_prev, double lam_k_est, double lam_k1_est, do
  */
 rsign_status rsign_shift_update(const double* H_new, const double* H_old, int64_t d, int32_t k,
                                 rsign_shift_policy policy, double threshold, double damping,
-                                rsign_shift_state* state, rsign_shift_report* report, void* stream);
+                                double drift_bound, rsign_shift_state* state, rsign_shift_report* report,
+                                void* stream);
 
 /*
  * rsign_reflector_noalloc -- the FP64-policy reflector (same result as

@@ -32,6 +32,7 @@ class Policy(enum.IntEnum):
     BF16_POLISH = 4
     FP16_REFINE = 5
     BF16_REFINE = 6
+    FP32 = 7
 
 
 class Status(enum.IntEnum):
@@ -160,7 +161,7 @@ def load():
     lib.rsign_shift_can_reuse.restype = i32
     lib.rsign_shift_damped.argtypes = [dbl, dbl, dbl, dbl, dbl]
     lib.rsign_shift_damped.restype = dbl
-    lib.rsign_shift_update.argtypes = [vp, vp, i64, i32, ctypes.c_int, dbl, dbl, ctypes.POINTER(ShiftState),
+    lib.rsign_shift_update.argtypes = [vp, vp, i64, i32, ctypes.c_int, dbl, dbl, dbl, ctypes.POINTER(ShiftState),
                                        ctypes.POINTER(ShiftReport), vp]
     lib.rsign_shift_update.restype = ctypes.c_int
     lib.rsign_reflector_backward.argtypes = [vp, i64, i32, dbl, ctypes.c_int, vp, vp, i32, vp]
@@ -349,10 +350,12 @@ def shift_damped(s_prev, lam_k_est, lam_k1_est, eps, damping) -> float:
 
 
 def shift_update(H_new, H_old, k, state: ShiftState, policy=ShiftPolicy.REUSE_REFRESH, threshold=0.0,
-                 damping=0.5, stream=None):
+                 damping=0.5, drift_bound=None, stream=None):
     """Shift for H_new given the state left by H_old (rsign_shift_update).
 
-    Updates ``state`` in place and returns (status, report)."""
+    drift_bound: a caller-certified bound on ||H_new - H_old||_2, or None for
+    the GPU's rigorous bound from H_old.  Updates ``state`` in place and
+    returns (status, report)."""
     lib = load()
     d = int(H_new.shape[0])
     hp, hk, hc = _ptr_of(H_new, "H_new", (d, d))
@@ -361,7 +364,8 @@ def shift_update(H_new, H_old, k, state: ShiftState, policy=ShiftPolicy.REUSE_RE
     else:
         op, ok, oc = None, None, False
     rep = ShiftReport()
-    st = Status(lib.rsign_shift_update(hp, op, d, int(k), int(policy), float(threshold), float(damping),
+    db = float("nan") if drift_bound is None else float(drift_bound)
+    st = Status(lib.rsign_shift_update(hp, op, d, int(k), int(policy), float(threshold), float(damping), db,
                                        ctypes.byref(state), ctypes.byref(rep), _stream_ptr(stream, hc or oc)))
     return st, rep
 
@@ -380,6 +384,46 @@ def reflector_backward(H, k, s, Rbar, policy=Policy.FP64, ckpt_every=4, out=None
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class SignReflector(torch.autograd.Function):
+        """R = sign(H - sI) with the hand-written Newton-Schulz adjoint as its backward.
+
+        forward: rsign_reflector (s = None: automatic shift, then frozen);
+        backward: rsign_reflector_backward with s and alpha held fixed."""
+
+        @staticmethod
+        def forward(ctx, H, k, s, policy, tol, ckpt_every):
+            R, info, st = reflector(H.detach(), k, s, tol=tol, policy=policy, check=True)
+            ctx.save_for_backward(H.detach())
+            ctx.k, ctx.s, ctx.policy, ctx.ckpt = int(k), float(info.shift), policy, int(ckpt_every)
+            return R
+
+        @staticmethod
+        def backward(ctx, Rbar):
+            (H,) = ctx.saved_tensors
+            Hbar = reflector_backward(H, ctx.k, ctx.s, Rbar.detach().contiguous(), policy=ctx.policy,
+                                      ckpt_every=ctx.ckpt)
+            return Hbar, None, None, None, None, None
+
+    return SignReflector
+
+
+_SIGN_FN = None
+
+
+def sign_reflector(H, k, s=None, policy=Policy.FP64, tol=1e-12, ckpt_every=4):
+    """Differentiable R_k = sign(H - sI) for a float64 CUDA tensor H (torch.autograd).
+
+    The gradient is the adjoint of the Newton-Schulz map with s and alpha
+    frozen (Gershgorin alpha, the default of the forward call)."""
+    global _SIGN_FN
+    if _SIGN_FN is None:
+        _SIGN_FN = _autograd_function()
+    return _SIGN_FN.apply(H, int(k), s, Policy(policy), float(tol), int(ckpt_every))
 
 
 # debug products (kernel-level tests)

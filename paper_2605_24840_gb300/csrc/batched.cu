@@ -290,7 +290,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
   if (opt_in) opt = *opt_in;
   if (n < 0 || (n > 0 && (!H || !d || !k || !s || !R))) return RSIGN_ERR_ARG;
   if (!(tol > 0.0) || !std::isfinite(tol)) return RSIGN_ERR_ARG;
-  if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_BF16_REFINE) return RSIGN_ERR_ARG;
+  if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_FP32) return RSIGN_ERR_ARG;
   if (opt.max_steps < 1 || opt.max_steps > 1000 || opt.polish_steps < 0) return RSIGN_ERR_ARG;
   if (opt.batch_tile != 0 && opt.batch_tile != 128 && opt.batch_tile != 256) return RSIGN_ERR_ARG;
   if (n == 0) return RSIGN_OK;
@@ -298,7 +298,8 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
   if (infos) std::memset(infos, 0, sizeof(rsign_info) * (size_t)n);
 
   // ---- partition: grouped matrices and the one-by-one rest
-  const bool refine = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE;
+  // refinement and the hi/lo FP32-class trajectory take the one-matrix path
+  const bool refine = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE || policy == RSIGN_FP32;
   Group g;
   std::vector<int> rest;
   for (int i = 0; i < n; ++i) {

@@ -411,7 +411,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   if (d64 < 2 || d64 > 16384) return d64 > 16384 ? RSIGN_ERR_UNSUPPORTED : RSIGN_ERR_ARG;
   if (k < 1 || k > d64 - 1) return RSIGN_ERR_ARG;
   if (!(tol > 0.0) || !std::isfinite(tol)) return RSIGN_ERR_ARG;
-  if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_BF16_REFINE) return RSIGN_ERR_ARG;
+  if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_FP32) return RSIGN_ERR_ARG;
   if (opt.max_steps < 1 || opt.max_steps > 1000 || opt.polish_steps < 0 || opt.max_sweeps < 0)
     return RSIGN_ERR_ARG;
   if (std::isinf(s)) return RSIGN_ERR_ARG;
@@ -566,7 +566,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     // twice the bits of the operand type): every product is the fused sum of
     // the pair products hi*hi + hi*lo + lo*hi, so the stored trajectory is an
     // accurate one and its derivative (the tangent recursion) is accurate too.
-    const bool split = refine && opt.low_split != 0;
+    const bool split = (refine && opt.low_split != 0) || policy == RSIGN_FP32;
     const int planes = split ? 2 : 1;
     std::vector<void*> xs, es;
     auto slot_x = [&](int m) -> void* {
@@ -771,8 +771,8 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
   if (!H || !Rbar || !Hbar) return RSIGN_ERR_ARG;
   if (d64 < 2 || d64 > 16384) return d64 > 16384 ? RSIGN_ERR_UNSUPPORTED : RSIGN_ERR_ARG;
   if (k < 1 || k > d64 - 1 || !std::isfinite(s)) return RSIGN_ERR_ARG;
-  if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_BF16_REFINE) return RSIGN_ERR_ARG;
-  if (policy == RSIGN_FP16_POLISH || policy == RSIGN_BF16_POLISH) return RSIGN_ERR_UNSUPPORTED;
+  if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_FP32) return RSIGN_ERR_ARG;
+  const bool polish = policy == RSIGN_FP16_POLISH || policy == RSIGN_BF16_POLISH;
   const int ck = ckpt_every > 0 ? ckpt_every : 4;
   Ctx c;
   c.st = st;
@@ -919,7 +919,7 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
   } else {
     // -------- low precision: the stage-1 trajectory kept whole, tangent products in FP16/BF16
     const int fmt = lp_fmt_of(policy);
-    const bool split = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE;
+    const bool split = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE || policy == RSIGN_FP32;
     const int planes = split ? 2 : 1;
     std::vector<void*> xs, es;
     auto slot = [&](std::vector<void*>& v, int m) -> void* {
@@ -974,6 +974,43 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
       TcGemmArgs up = sy;
       up.epi = TC_EPI_NS_UPDATE; up.out = xn; up.xin = xm;
       if (!c.ok(tc_gemm(up, xm, planes, em, planes, fmt, c.num_sms, st))) return fail();
+    }
+    if (polish) {
+      // -------- the FP64 polish steps after stage 1 (the default depth of the
+      // forward, rsign_options.polish_steps = 2): recomputed in FP64 from the
+      // stage-1 result, then G is taken back through them in FP64
+      constexpr int kPolish = 2;
+      std::vector<double*> xp(kPolish + 1, nullptr), ep(kPolish, nullptr);
+      for (auto& p : xp)
+        if (mem.alloc((void**)&p, dd * 8) != cudaSuccess) return fail();
+      for (auto& p : ep)
+        if (mem.alloc((void**)&p, dd * 8) != cudaSuccess) return fail();
+      double *P1 = nullptr, *Q = nullptr, *P2 = nullptr;
+      if (mem.alloc((void**)&P1, dd * 8) != cudaSuccess || mem.alloc((void**)&Q, dd * 8) != cudaSuccess ||
+          mem.alloc((void**)&P2, dd * 8) != cudaSuccess)
+        return fail();
+      if (!c.ok(to_f64(xs[M], fmt, dd, xp[0], st))) return fail();
+      for (int j = 0; j < kPolish; ++j) {
+        F64GemmArgs sy{};
+        sy.dp = dp; sy.d_real = d; sy.sym = 1; sy.epi = F64_EPI_NS_SYRK;
+        sy.A = xp[j]; sy.B = xp[j]; sy.out = ep[j]; sy.partials = partials;
+        F64GemmArgs up{};
+        up.dp = dp; up.d_real = d; up.sym = 1; up.epi = F64_EPI_NS_UPDATE;
+        up.A = xp[j]; up.B = ep[j]; up.xin = xp[j]; up.out = xp[j + 1]; up.partials = partials;
+        if (!c.ok(f64_gemm(sy, st)) || !c.ok(f64_gemm(up, st))) return fail();
+      }
+      for (int j = kPolish - 1; j >= 0; --j) {
+        F64GemmArgs g1{};
+        g1.dp = dp; g1.d_real = d; g1.sym = 0; g1.epi = F64_EPI_STORE; g1.scale = 1.0;
+        g1.A = G; g1.B = ep[j]; g1.out = P1;                        // G E_j
+        F64GemmArgs g2 = g1;
+        g2.A = xp[j]; g2.B = G; g2.out = Q;                         // X_j G
+        F64GemmArgs g3 = g1;
+        g3.sym = 1; g3.A = Q; g3.B = xp[j]; g3.out = P2;            // X_j G X_j
+        if (!c.ok(f64_gemm(g1, st)) || !c.ok(f64_gemm(g2, st)) || !c.ok(f64_gemm(g3, st)) ||
+            !c.ok(tangent_combine_f64(G, P1, P2, dp, st)))
+          return fail();
+      }
     }
     // backward tangent sweep in the operand type (hi planes), FP32 master G
     const int ntile = (dp / 32) * (dp / 32);

@@ -152,11 +152,13 @@ double rsign_shift_damped(double s_prev, double lam_k_est, double lam_k1_est, do
 
 rsign_status rsign_shift_update(const double* H_new, const double* H_old, int64_t d64, int32_t k,
                                 rsign_shift_policy policy, double threshold, double damping,
-                                rsign_shift_state* state, rsign_shift_report* report, void* stream) {
+                                double drift_bound, rsign_shift_state* state, rsign_shift_report* report,
+                                void* stream) {
   using namespace rsign;
   if (!H_new || !state || d64 < 2 || d64 > 16384 || k < 1 || k > d64 - 1) return RSIGN_ERR_ARG;
   if ((int)policy < RSIGN_SHIFT_MIDPOINT || (int)policy > RSIGN_SHIFT_DAMPED) return RSIGN_ERR_ARG;
   if (!(threshold >= 0.0) || !std::isfinite(threshold)) return RSIGN_ERR_ARG;
+  if (!std::isnan(drift_bound) && !(drift_bound >= 0.0 && std::isfinite(drift_bound))) return RSIGN_ERR_ARG;
   int sms = 0;
   const int ds = check_device(&sms);
   if (ds != RSIGN_OK) return (rsign_status)ds;
@@ -193,8 +195,8 @@ rsign_status rsign_shift_update(const double* H_new, const double* H_old, int64_
     Ho = p;
   }
 
-  // ---- drift bound of the step H_old -> H_new (Weyl)
-  if (Ho) {
+  // ---- drift bound of the step H_old -> H_new (Weyl), unless the caller gave one
+  if (Ho && std::isnan(drift_bound)) {
     double *rowabs = nullptr, *rowsq = nullptr, *colabs = nullptr, *red = nullptr, *x = nullptr, *y = nullptr;
     if (mem.alloc((void**)&rowabs, (size_t)d * 8) != cudaSuccess ||
         mem.alloc((void**)&rowsq, (size_t)d * 8) != cudaSuccess ||
@@ -226,8 +228,9 @@ rsign_status rsign_shift_update(const double* H_new, const double* H_old, int64_
     rep.drift_est = est;
     if (!std::isfinite(rep.drift_ub)) return fail(RSIGN_ERR_ARG);
   }
+  if (!std::isnan(drift_bound)) rep.drift_ub = drift_bound;  // the caller's certified bound
 
-  const bool can_reuse = policy == RSIGN_SHIFT_REUSE_REFRESH && Ho != nullptr &&
+  const bool can_reuse = policy == RSIGN_SHIFT_REUSE_REFRESH && std::isfinite(rep.drift_ub) &&
                          rsign_shift_can_reuse(state, rep.drift_ub, threshold) != 0;
   if (can_reuse) {
     state->margin_cert -= rep.drift_ub;

@@ -64,7 +64,8 @@ def test_backward_fp64_matches_finite_differences():
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (fd, an)
 
 
-@pytest.mark.parametrize("policy,tol", [("FP16_REFINE", 2e-2), ("BF16_REFINE", 1e-1), ("FP16", 1e-1)])
+@pytest.mark.parametrize("policy,tol", [("FP16_REFINE", 2e-2), ("BF16_REFINE", 1e-1), ("FP16", 1e-1),
+                                        ("FP16_POLISH", 1e-1), ("BF16_POLISH", 2e-1), ("FP32", 2e-2)])
 def test_backward_low_precision_close_to_daleckii_krein(policy, tol):
     torch = cuda_or_skip()
     rs = lib_or_fail()
@@ -86,3 +87,27 @@ def test_backward_rejects_bad_arguments():
         rs.reflector_backward(H, 0, 0.0, H)
     with pytest.raises(rs.RsignError):
         rs.reflector_backward(H, 2, float("nan"), H)
+
+
+def test_autograd_function_matches_backward_and_daleckii_krein():
+    # the adjoint workload's loss L = <G, R> + g^T R g through torch.autograd
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 256, 6
+    spec = workloads.controlled_spectrum(d, k, 5e-2, seed=505)
+    rng = np.random.default_rng(8)
+    Gm = rng.standard_normal((d, d))
+    Gm = 0.5 * (Gm + Gm.T)
+    g = rng.standard_normal(d)
+    H = torch.from_numpy(spec.H).cuda().requires_grad_(True)
+    R = rs.sign_reflector(H, k, 0.0, policy=rs.Policy.FP64)
+    Gt, gt = torch.from_numpy(Gm).cuda(), torch.from_numpy(g).cuda()
+    loss = (Gt * R).sum() + gt @ R @ gt
+    loss.backward()
+    Rbar = Gm + np.outer(g, g)
+    direct = rs.reflector_backward(spec.H, k, 0.0, Rbar, policy=rs.Policy.FP64)
+    assert np.max(np.abs(H.grad.cpu().numpy() - direct)) <= 1e-12 * np.abs(direct).max()
+    dk = _dk_gradient(spec, 0.0, Rbar)
+    assert np.linalg.norm(H.grad.cpu().numpy() - dk) / np.linalg.norm(dk) < 1e-8
+    # the forward value is the reflector itself
+    assert np.max(np.abs(R.detach().cpu().numpy() - oracle.reflector_from_basis(spec.Q, k))) < 1e-10

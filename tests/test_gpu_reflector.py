@@ -57,7 +57,7 @@ def test_fp64_ragged_sizes(d, k):
     assert abs(info.trace - (d - 2 * k)) < 1e-8
 
 
-@pytest.mark.parametrize("policy,floor", [("FP16", 2e-2), ("BF16", 2e-1)])
+@pytest.mark.parametrize("policy,floor", [("FP16", 2e-2), ("BF16", 2e-1), ("FP32", 1e-4)])
 def test_low_precision_stage(policy, floor):
     torch = cuda_or_skip()
     rs = lib_or_fail()
