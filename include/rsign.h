@@ -111,7 +111,8 @@ typedef struct {
   /* automatic shift (s = NaN), Sec. 4.3 / Prop. 4.1-4.2; NaN / 0 otherwise:          */
   double lam_k_est;        /* Lanczos estimate of lam_k                                */
   double lam_k1_est;       /* Lanczos estimate of lam_{k+1}                            */
-  double shift_eps;        /* endpoint error bound eps (largest Ritz residual)         */
+  double shift_eps;        /* endpoint error bound eps (largest Ritz residual bound plus a
+                              rounding allowance 16 sqrt(d) u ||T||)                    */
   double margin_lb;        /* guaranteed margin m_hat - eps of the chosen shift        */
   int32_t lanczos_iters;   /* Lanczos steps taken                                      */
   int32_t steps_pred;      /* NS steps the scalar recurrence predicts for eps_m(gamma) <= tol,

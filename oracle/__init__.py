@@ -238,6 +238,46 @@ def ns_steps(gamma: float, tol: float, max_steps: int = 1000) -> int:
     return m
 
 
+def scaled_ns_coeffs(l0: float, u0: float = 1.0, tol: float = 1e-15, max_steps: int = 200):
+    """Step scalings of the scaled Newton-Schulz sign iteration (Chen and Chow's
+    stable scaling, cited by the paper for GPU implementations, Sec. 3.5):
+    for a spectrum in [-1, -l] U [l, 1] the step X <- 1/2 a X (3I - a^2 X^2)
+    with a = sqrt(3 / (1 + l + l^2)) maps [l, 1] into [l', 1],
+    l' = 1/2 a l (3 - a^2 l^2) (the scaled cubic takes equal values at l and 1
+    and its maximum 1 at 1/a).  u0 >= the largest |eigenvalue| of X_0: the
+    interval is first normalised to [l0/u0, 1] and the first factor divided
+    by u0.  Returns [a_0, a_1, ...] up to the first a with |a - 1| <= tol
+    (after which the plain step, a = 1, is the scaled one)."""
+    l = float(l0) / float(u0)
+    out = []
+    for m in range(max_steps):
+        a = math.sqrt(3.0 / (1.0 + l + l * l))
+        if abs(a - 1.0) <= tol:
+            break
+        out.append(a / u0 if m == 0 else a)
+        l = 0.5 * a * l * (3.0 - a * a * l * l)
+    return out
+
+
+def scaled_ns_map(x, a: float):
+    """The scalar scaled step g(x) = 1/2 a x (3 - a^2 x^2)."""
+    x = np.asarray(x, dtype=np.float64)
+    return 0.5 * a * x * (3.0 - a * a * x * x)
+
+
+def scaled_ns_iterates(X0: np.ndarray, coeffs, steps: int):
+    """X_0..X_steps of the scaled iteration: step m applies the plain map of
+    Eq. NS to a_m X_m (a_m = 1 once the coefficient list is exhausted)."""
+    out = [_c(X0).copy()]
+    X = out[0]
+    for m in range(steps):
+        a = coeffs[m] if m < len(coeffs) else 1.0
+        Xn, _ = ns_step_rows(a * X, 0, X.shape[0])
+        X = Xn
+        out.append(X)
+    return out
+
+
 # --------------------------------------------------------------------------
 # Shift placement (Prop. 4.1, Prop. 4.2)
 # --------------------------------------------------------------------------

@@ -219,7 +219,8 @@ cudaError_t power_alpha(const double* A, int dp, double* x, double* y, int iters
 // ---------------------------------------------------------------------------
 struct LanczosResult {
   double lam_k, lam_k1;  // Ritz estimates of lam_k, lam_{k+1}
-  double eps_k, eps_k1;  // their residual bounds (an eigenvalue lies within each)
+  double eps_k, eps_k1;  // their residual bounds (an eigenvalue lies within each), each
+                         // plus a rounding allowance 16 sqrt(d) u ||T_m||
   int iters;             // Lanczos steps taken
   int converged;         // 1 when (lam_k1 - lam_k)/2 > 4 max(eps) was reached
 };

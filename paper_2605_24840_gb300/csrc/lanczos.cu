@@ -206,8 +206,16 @@ cudaError_t lanczos_endpoints(const double* A, int dp, int d, int k, int max_ite
         for (int q = 0; q < 2; ++q) tridiag_ritz(a.data(), b.data(), m, j0 + q, &th[q], &lc[q]);
         out->lam_k = th[0];
         out->lam_k1 = th[1];
-        out->eps_k = std::fabs(hb[m - 1] * lc[0]);
-        out->eps_k1 = std::fabs(hb[m - 1] * lc[1]);
+        // residual bounds |beta_m s_m| (exact arithmetic) plus a rounding
+        // allowance 16 sqrt(d) u ||T||, ||T|| <= its Gershgorin bound: without it
+        // a converged Krylov space (beta_m ~ 0) would claim to resolve gaps below
+        // the FP64 resolution of the eigenvalues
+        double tn = 0.0;
+        for (int i = 0; i < m; ++i)
+          tn = std::max(tn, std::fabs(a[i]) + (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0));
+        const double floor_r = 16.0 * std::sqrt((double)d) * 1.1102230246251565e-16 * tn;
+        out->eps_k = std::fabs(hb[m - 1] * lc[0]) + floor_r;
+        out->eps_k1 = std::fabs(hb[m - 1] * lc[1]) + floor_r;
         out->iters = m;
         const double eps = std::max(out->eps_k, out->eps_k1);
         const double mhat = 0.5 * (out->lam_k1 - out->lam_k);

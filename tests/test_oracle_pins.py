@@ -383,3 +383,81 @@ def test_allen_cahn_hessian_structure(oracle_mod):
     assert np.allclose(lam, np.linalg.eigvalsh(H), atol=1e-12 * np.abs(lam).max())
     c = eps * eps * n * n
     assert lam[-1] <= 8 * c + 2 + 1e-12 and lam[0] >= -1 - 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Scaled Newton-Schulz steps (the step scalings of the cited stable scaling)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("l", [1e-4, 3e-3, 1e-2, 0.1, 0.3, 0.7, 0.95])
+def test_scaled_step_equioscillates_on_its_interval(oracle_mod, l):
+    oracle = oracle_mod
+    a = oracle.scaled_ns_coeffs(l)[0]
+    g = lambda x: oracle.scaled_ns_map(x, a)
+    # equal values at both ends of [l, 1] and the maximum 1 inside
+    assert abs(float(g(l)) - float(g(1.0))) <= 4e-15  # 3 - a^2 cancels near a^2 = 3
+    xs = np.linspace(l, 1.0, 20001)
+    gx = g(xs)
+    assert gx.max() <= 1.0 + 4e-16
+    assert abs(float(g(1.0 / a)) - 1.0) <= 4e-16 and l <= 1.0 / a <= 1.0
+    # so the next interval is [g(l), 1], strictly larger at the bottom, signs kept
+    assert gx.min() >= float(g(l)) - 4e-15 and float(g(l)) > l
+    assert np.all(g(-xs) == -gx)
+
+
+def test_scaled_steps_reach_one_and_beat_the_plain_steps(oracle_mod):
+    oracle = oracle_mod
+    for l0 in (1e-3, 1e-2, 0.1):
+        c = oracle.scaled_ns_coeffs(l0)
+        l = l0
+        for a in c:
+            l = float(oracle.scaled_ns_map(l, a))
+        assert 1.0 - l <= 1e-13
+        # the plain recurrence needs more steps for the same bottom end
+        plain = oracle.ns_steps(l0, 1e-13)
+        assert len(c) < plain
+        assert all(1.0 <= a <= math.sqrt(3.0) for a in c)
+    assert oracle.scaled_ns_coeffs(1.0) == []  # an involution needs no scaled step
+
+
+def test_scaled_first_step_normalises_by_the_upper_bound(oracle_mod):
+    oracle = oracle_mod
+    # with |eigenvalues| up to u0 > 1 the first factor absorbs 1/u0 and no sign flips
+    l0, u0 = 2e-2, 1.05
+    c = oracle.scaled_ns_coeffs(l0, u0)
+    xs = np.linspace(l0, u0, 5001)
+    y = oracle.scaled_ns_map(xs, c[0])
+    assert np.all(y > 0) and y.max() <= 1.0 + 1e-15
+    # without the normalisation the same interval would flip the top eigenvalues
+    bad = oracle.scaled_ns_map(xs, oracle.scaled_ns_coeffs(l0)[0])
+    assert bad.min() < 0
+
+
+def test_scaled_iteration_on_a_diagonal_is_the_scalar_map(oracle_mod):
+    oracle = oracle_mod
+    d = np.array([-0.9, -0.02, 0.015, 0.4, 1.0])
+    c = oracle.scaled_ns_coeffs(0.015)
+    its = oracle.scaled_ns_iterates(np.diag(d), c, len(c) + 2)
+    x = d.copy()
+    for m in range(len(c) + 2):
+        x = oracle.scaled_ns_map(x, c[m] if m < len(c) else 1.0)
+        np.testing.assert_allclose(np.diag(its[m + 1]), x, rtol=0, atol=2e-15)
+        assert np.count_nonzero(its[m + 1] - np.diag(np.diag(its[m + 1]))) == 0
+    np.testing.assert_allclose(np.diag(its[-1]), np.sign(d), atol=1e-14)
+
+
+def test_scaled_iteration_reaches_the_reflector_brute_force(oracle_mod):
+    oracle = oracle_mod
+    rng = np.random.default_rng(11)
+    for d in (4, 6, 8):
+        Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+        lam = np.sort(np.concatenate([rng.uniform(-1, -0.05, 2), rng.uniform(0.05, 1, d - 2)]))
+        H = (Q * lam) @ Q.T
+        H = 0.5 * (H + H.T)
+        A = oracle.shifted(H, 0.0)
+        alpha = oracle.gershgorin_alpha(A)
+        l0 = alpha * np.min(np.abs(lam))
+        c = oracle.scaled_ns_coeffs(l0)
+        X = oracle.scaled_ns_iterates(alpha * A, c, len(c) + 3)[-1]
+        w, V = np.linalg.eigh(H)
+        R = V @ np.diag(np.sign(w)) @ V.T
+        assert np.max(np.abs(X - R)) < 1e-13
