@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 Newton-Schulz comparator")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--engine", default="scaled", choices=["plain", "scaled"],
+                   help="plain: Eq. NS steps; scaled: the stable step scalings from the margin of the "
+                        "midpoint shift (the half-gap), then plain steps")
     p.add_argument("--workload", default="dense", choices=["dense", "batched"],
                    help="dense: the d=8192 headline; batched: 512 matrices of order 32..512 through the "
                         "grouped launches, against a per-matrix call loop")
@@ -229,6 +232,8 @@ def workload_config(args):
             "d": args.d, "k": args.k, "delta": args.delta, "theta": args.theta, "policy": args.policy,
             "tol": args.tol,
             "alpha": "1/(1.02 rho_est), 20 power steps" if args.alpha == "power" else "1/||H-sI||_inf",
+            "engine": ("scaled Newton-Schulz steps from the gap margin, then plain" if args.engine == "scaled"
+                       else "plain Newton-Schulz (Eq. NS)"),
             "parallelism": "replicas",
             "l2": "inputs larger than L2 (H = 8 d^2 bytes)"}
 
@@ -253,7 +258,9 @@ def run_rsign(args):
     lam_h = lam.cpu().numpy()
     s = float(lam_h[args.k - 1] + args.theta * (lam_h[args.k] - lam_h[args.k - 1]))
     R = torch.empty_like(H)
-    opt = rs.default_options(alpha_mode=int(rs.AlphaMode.POWER if args.alpha == "power" else rs.AlphaMode.INF))
+    margin = float(min(s - lam_h[args.k - 1], lam_h[args.k] - s))
+    opt = rs.default_options(alpha_mode=int(rs.AlphaMode.POWER if args.alpha == "power" else rs.AlphaMode.INF),
+                             ns_scaling=1 if args.engine == "scaled" else 0, margin=margin)
     stream = torch.cuda.current_stream(dev)
 
     def call(Hin, Rout, pol=policy, tol=args.tol):

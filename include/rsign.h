@@ -122,6 +122,9 @@ typedef struct {
   int32_t batch_tile;      /* tile width of the grouped tensor-core launches (128 or
                               256; 64 = FP64 tiles only); the ms_* fields of a grouped
                               matrix are those of the whole batch                      */
+  int32_t ns_scaled_steps; /* leading steps run with the scaled step (rsign_options
+                              ns_scaling); 0 = the plain iteration throughout           */
+  int32_t reserved;
 } rsign_info;
 
 /* Optional knobs; rsign_options_default() fills the defaults. */
@@ -143,6 +146,16 @@ typedef struct {
                                launches, 128 or 256; 0 lets the autotuner time both
                                widths (and two tile orders) on the batch's first step
                                and cache the choice per batch shape (default 0)        */
+  int32_t ns_scaling;       /* 1: scaled Newton-Schulz steps X <- 1/2 a X (3I - a^2 X^2)
+                               (the stable step scalings cited in Sec. 3.5) while a
+                               margin bound is known: a = sqrt(3/(1 + l + l^2)) for the
+                               spectral interval [l, 1], l <- 1/2 a l (3 - a^2 l^2), then
+                               plain steps; l_0 = alpha * margin.  Same limit, about
+                               half the steps for small l.  0: the plain iteration
+                               (default 0)                                              */
+  double margin;            /* lower bound of min_i |lam_i - s| for ns_scaling (the
+                               half-gap for a midpoint shift), NaN = unknown (default);
+                               the automatic shift supplies its certified margin       */
 } rsign_options;
 
 void rsign_options_default(rsign_options* opt);

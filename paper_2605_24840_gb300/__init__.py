@@ -65,6 +65,7 @@ class Info(ctypes.Structure):
         ("lam_k_est", ctypes.c_double), ("lam_k1_est", ctypes.c_double), ("shift_eps", ctypes.c_double),
         ("margin_lb", ctypes.c_double), ("lanczos_iters", ctypes.c_int32), ("steps_pred", ctypes.c_int32),
         ("batch_grouped", ctypes.c_int32), ("batch_tile", ctypes.c_int32),
+        ("ns_scaled_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -78,6 +79,7 @@ class Options(ctypes.Structure):
         ("power_steps", ctypes.c_int32), ("timing", ctypes.c_int32),
         ("low_split", ctypes.c_int32), ("lanczos_max", ctypes.c_int32),
         ("batch_graphs", ctypes.c_int32), ("batch_tile", ctypes.c_int32),
+        ("ns_scaling", ctypes.c_int32), ("margin", ctypes.c_double),
     ]
 
 
@@ -207,7 +209,7 @@ def default_options(**kw) -> Options:
     o = Options()
     load().rsign_options_default(ctypes.byref(o))
     for k, v in kw.items():
-        setattr(o, k, int(v))
+        setattr(o, k, float(v) if k == "margin" else int(v))
     return o
 
 

@@ -130,10 +130,12 @@ __global__ void __launch_bounds__(128) f64_gemm_kernel(const F64GemmArgs a) {
           v *= a.scale;
         } else if constexpr (EPI == F64_EPI_NS_SYRK) {
           const bool real = i < d_real && j < d_real;
+          if (a.ns_c2 != 0.0 && a.ns_c2 != 1.0) v *= a.ns_c2;  // E = I - a^2 X^2 (scaled step)
           v = real ? ((i == j ? 1.0 : 0.0) - v) : 0.0;
           if (real && (!a.sym || j >= i)) part += ((a.sym && j > i) ? 2.0 : 1.0) * v * v;
         } else {  // F64_EPI_NS_UPDATE
           v = xinp[(size_t)i * ld + j] + 0.5 * v;
+          if (a.ns_c1 != 0.0 && a.ns_c1 != 1.0) v *= a.ns_c1;  // X+ = a (X + 1/2 X E)
           if (i == j && i < d_real) part += v;
         }
         if (!a.sym || j >= i) outp[(size_t)i * ld + j] = v;

@@ -103,6 +103,10 @@ struct TcGemmArgs {
   long long mat_stride;    // elements of the output type between consecutive matrices
   int a_planes, b_planes;  // slices per matrix in A / B
   int mat_vec_stride;      // TC_EPI_OZAKI: elements between matrices in rs / cs / a_diag / b_diag
+  // scaled Newton-Schulz step X+ = 1/2 a X (3I - a^2 X^2): TC_EPI_NS_SYRK stores
+  // E = I - ns_c2 X^2 (ns_c2 = a^2), TC_EPI_NS_UPDATE stores ns_c1 (X + 1/2 X E)
+  // (ns_c1 = a); 0 means 1 (the plain step)
+  float ns_c1, ns_c2;
 };
 
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
@@ -152,6 +156,7 @@ struct F64GemmArgs {
   const int* mat_d;
   const int* mat_skip;
   long long mat_stride;
+  double ns_c1, ns_c2;  // scaled step factors as in TcGemmArgs (0 = 1)
 };
 int f64_num_tiles(int dp, int sym);
 // Grouped FP64 products over a.units (64 x 64 tiles, dp = slot leading dimension).
@@ -320,7 +325,9 @@ cudaError_t newton_direction(const float* P, int dp, const float* sigmaC, double
 // Tangent Newton-Schulz step (Frechet derivative of X + 1/2 X (I - X^2)):
 // E <- 1/2 E + 1/2 (P1 + P1^T)/sigma - 1/2 P2/sigma, P1 = E_lp Et, P2 = X E_lp X,
 // with per-tile maxima of the new E.
-cudaError_t tangent_combine(float* E, const float* P1, const float* P2, int dp, const float* sigma,
+// tangent step of the (scaled) Newton-Schulz map:
+// E <- a (1/2 E + 1/2 (P1 + P1^T)/sigma) - 1/2 a^3 P2/sigma  (a = 1: the plain step)
+cudaError_t tangent_combine(float* E, const float* P1, const float* P2, int dp, const float* sigma, float a,
                             float* blockmax, cudaStream_t st);
 // R += E (FP64 += FP32, masked to d) and per-block sums of E^2 -> part.
 cudaError_t add_correction(double* R, const float* E, int dp, int d, double* part, cudaStream_t st);

@@ -163,17 +163,19 @@ __global__ void newton_direction_kernel(const float* __restrict__ P, int dp, con
 }
 
 __global__ void tangent_combine_kernel(float* __restrict__ E, const float* __restrict__ P1,
-                                       const float* __restrict__ P2, int dp, const float* sigma,
+                                       const float* __restrict__ P2, int dp, const float* sigma, float a,
                                        float* blockmax) {
   __shared__ float t[TILE][TILE + 1];
   const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
   for (int r = ty; r < TILE; r += 8) t[r][tx] = P1[(size_t)(bj * TILE + r) * dp + bi * TILE + tx];
   __syncthreads();
   const float inv = 0.5f / sigma[0];
+  const float a3 = a * a * a;
   float m = 0.f;
   for (int r = ty; r < TILE; r += 8) {
     const size_t e = (size_t)(bi * TILE + r) * dp + bj * TILE + tx;
-    const float v = 0.5f * E[e] + inv * (P1[e] + t[tx][r] - P2[e]);
+    const float v = (a == 1.0f) ? 0.5f * E[e] + inv * (P1[e] + t[tx][r] - P2[e])
+                                : a * (0.5f * E[e] + inv * (P1[e] + t[tx][r])) - (a3 * inv) * P2[e];
     E[e] = v;
     m = fmaxf(m, fabsf(v));
   }
@@ -523,9 +525,9 @@ cudaError_t newton_direction(const float* P, int dp, const float* sigmaC, double
   return cudaGetLastError();
 }
 
-cudaError_t tangent_combine(float* E, const float* P1, const float* P2, int dp, const float* sigma,
+cudaError_t tangent_combine(float* E, const float* P1, const float* P2, int dp, const float* sigma, float a,
                             float* blockmax, cudaStream_t st) {
-  tangent_combine_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(E, P1, P2, dp, sigma, blockmax);
+  tangent_combine_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(E, P1, P2, dp, sigma, a, blockmax);
   return cudaGetLastError();
 }
 

@@ -137,7 +137,7 @@ struct F64Loop {
 };
 
 bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_steps, Ctl* ctl_dev,
-            Ctl& ctl_host, int* m_out, bool* conv) {
+            Ctl& ctl_host, int* m_out, bool* conv, const std::vector<double>* coef = nullptr) {
   const int nt = f64_num_tiles(dp, 1);
   int m = 0;
   bool stopped = false;
@@ -148,6 +148,8 @@ bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_ste
       sy.dp = dp; sy.d_real = d; sy.sym = 1; sy.epi = F64_EPI_NS_SYRK;
       sy.A = L.xb[mm & 1]; sy.B = L.xb[mm & 1]; sy.out = L.E; sy.partials = L.partials;
       sy.skip = L.done;
+      const double am = (coef != nullptr && mm < (int)coef->size()) ? (*coef)[mm] : 1.0;
+      sy.ns_c2 = am * am;
       if (!c.ok(f64_gemm(sy, c.st))) return false;
       if (!c.ok(ns_check(L.partials, nt * 4, L.hist, mm, tol_abs, -1.0, -1.0, 0.0, L.done, L.steps, c.st)))
         return false;
@@ -156,6 +158,7 @@ bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_ste
       up.dp = dp; up.d_real = d; up.sym = 1; up.epi = F64_EPI_NS_UPDATE;
       up.A = L.xb[mm & 1]; up.B = L.E; up.xin = L.xb[mm & 1]; up.out = L.xb[(mm + 1) & 1];
       up.partials = L.partials; up.skip = L.done;
+      up.ns_c1 = am;
       if (!c.ok(f64_gemm(up, c.st))) return false;
     }
     if (!c.ok(cudaMemcpyAsync(&ctl_host, ctl_dev, sizeof(Ctl), cudaMemcpyDeviceToHost, c.st))) return false;
@@ -242,7 +245,9 @@ struct RefineIn {
   double* A64;          // A = sym(H) - sI, FP64, zero padded
   double* R64;          // in: stage-1 result; out: refined reflector
   void* const* X;       // X_0 .. X_{M-1} (operand type)
-  void* const* Et;      // I - X_m^2, m = 0 .. M-1 (operand type)
+  void* const* Et;      // I - a_m^2 X_m^2, m = 0 .. M-1 (operand type)
+  const double* a;      // step scalings a_m of the stage-1 trajectory (nullptr: all 1)
+  int n_a;              // entries of a (steps beyond use 1)
 };
 struct RefineOut {
   int sweeps = 0, polish_steps = 0;
@@ -382,7 +387,8 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       if (!c.ok(tc(Elp, in.Et[m], in.fmt, 0, TC_EPI_STORE_F32, P32))) return c.err;   // E Et
       if (!c.ok(tc(in.X[m], Elp, in.fmt, 0, TC_EPI_STORE_LP, Qlp))) return c.err;     // X E
       if (!c.ok(tc(Qlp, in.X[m], in.fmt, 1, TC_EPI_STORE_F32, Q32))) return c.err;    // X E X
-      if (!c.ok(tangent_combine(E32, P32, Q32, dp, fs + 5, bmax, st))) return c.err;
+      const float am = (in.a != nullptr && m < in.n_a) ? (float)in.a[m] : 1.0f;
+      if (!c.ok(tangent_combine(E32, P32, Q32, dp, fs + 5, am, bmax, st))) return c.err;
       if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return c.err;
     }
     if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 7, st))) return c.err;
@@ -414,6 +420,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_FP32) return RSIGN_ERR_ARG;
   if (opt.max_steps < 1 || opt.max_steps > 1000 || opt.polish_steps < 0 || opt.max_sweeps < 0)
     return RSIGN_ERR_ARG;
+  if (!std::isnan(opt.margin) && !(opt.margin > 0.0 && std::isfinite(opt.margin))) return RSIGN_ERR_ARG;
   if (std::isinf(s)) return RSIGN_ERR_ARG;
   const bool auto_shift = std::isnan(s);
   const bool refine = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE;
@@ -547,6 +554,32 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     return RSIGN_ERR_ARG;  // H - sI == 0
   }
 
+  // ---- scaled Newton-Schulz steps (Sec. 3.5: the stable step scalings of the
+  // cited GPU sign iteration) when a lower bound of the spectral margin is
+  // known -- the caller's opt.margin or the certified margin of the automatic
+  // shift: for the spectrum of X in [-1, -l] U [l, 1] the step
+  // X <- 1/2 a X (3I - a^2 X^2), a = sqrt(3 / (1 + l + l^2)), maps [l, 1] into
+  // [l', 1] with l' = 1/2 a l (3 - a^2 l^2), about 2.6 l for small l (1.5 l
+  // for the plain step).  The upper end is 1 for the Gershgorin alpha; for
+  // the power-step alpha, whose rho estimate is not a certified bound, the
+  // first factor is divided by 1.04 (a rho estimate down to 0.94 rho stays
+  // sign-safe; below that the trace certificate fails and the call is redone
+  // with the Gershgorin alpha).
+  std::vector<double> coef;
+  {
+    const double mk = auto_shift ? margin_lb : opt.margin;
+    if (opt.ns_scaling && std::isfinite(mk) && mk > 0.0) {
+      const double u0 = opt.alpha_mode == RSIGN_ALPHA_POWER ? 1.04 : 1.0;
+      double l = std::min(1.0, alpha * mk) / u0;
+      for (int m = 0; m < 200; ++m) {
+        const double a = std::sqrt(3.0 / (1.0 + l + l * l));
+        if (std::fabs(a - 1.0) <= 1e-15) break;
+        coef.push_back(m == 0 ? a / u0 : a);
+        l = 0.5 * a * l * (3.0 - a * a * l * l);
+      }
+    }
+  }
+
   double* Rfinal = nullptr;  // dp x dp FP64 result
   double* xb64[2] = {nullptr, nullptr};
   double* E64 = nullptr;
@@ -619,6 +652,9 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         sy.split = split ? 1 : 0;
         sy.group_scale[0] = 1.0; sy.scale = 1.0f; sy.out = em; sy.partials = partials;
         sy.status = &ctl->status; sy.skip = &ctl->done_low;
+        const double am = mm < (int)coef.size() ? coef[mm] : 1.0;
+        sy.ns_c2 = (float)(am * am);
+        sy.ns_c1 = (float)am;
         if (!c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st))) return fail_cuda();
         if (!c.ok(ns_check(partials, nt * 4, hist_low, mm, 0.0, floor_lo, floor_hi, 0.5, &ctl->done_low,
                            &ctl->steps_low, st)))
@@ -654,6 +690,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       RefineIn in{};
       in.dp = dp; in.d = d; in.fmt = fmt; in.M = steps_low; in.alpha = alpha; in.tol = tol;
       in.A64 = A64; in.R64 = xb64[0]; in.X = xs.data(); in.Et = es.data();
+      in.a = coef.empty() ? nullptr : coef.data(); in.n_a = (int)coef.size();
       in.max_sweeps = std::max(1, opt.max_sweeps);
       RefineOut ro{};
       const cudaError_t re = refine_sweeps(c, mem, in, ctl, &ro);
@@ -681,7 +718,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       if (fp64e_polish(c, mem, xb64, E64, dp, d, opt.polish_steps, partials, hist64, ctl) != cudaSuccess)
         return fail_cuda();
       m_ret = opt.polish_steps;
-    } else if (!f64_ns(c, L, dp, d, tol_fro, opt.max_steps, ctl, ctl_h, &m_ret, &conv64)) {
+    } else if (!f64_ns(c, L, dp, d, tol_fro, opt.max_steps, ctl, ctl_h, &m_ret, &conv64, &coef)) {
       return fail_cuda();
     }
     steps64 = m_ret;
@@ -720,6 +757,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     info->shift = s;
     info->gamma_est = auto_shift ? alpha * margin_lb : NAN;
     info->steps_pred = -1;
+    info->ns_scaled_steps = (int32_t)coef.size();
     if (auto_shift && info->gamma_est > 0.0) {
       // smallest m with eps_m(gamma) <= tol, eps_0 = 1 - gamma, eps_{m+1} = eps_m^2 (3 - eps_m)/2
       double e = 1.0 - std::min(1.0, info->gamma_est);
@@ -1035,7 +1073,7 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
       if (!c.ok(tc(Glp, es[m], 0, TC_EPI_STORE_F32, P32))) return fail();     // G E_m
       if (!c.ok(tc(xs[m], Glp, 0, TC_EPI_STORE_LP, Qlp))) return fail();      // X_m G
       if (!c.ok(tc(Qlp, xs[m], 1, TC_EPI_STORE_F32, Q32))) return fail();     // X_m G X_m
-      if (!c.ok(tangent_combine(G32, P32, Q32, dp, fs + 5, bmax, st))) return fail();
+      if (!c.ok(tangent_combine(G32, P32, Q32, dp, fs + 5, 1.0f, bmax, st))) return fail();
       if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return fail();
     }
     if (!c.ok(to_f64(G32, 3, dd, G, st))) return fail();
@@ -1099,6 +1137,8 @@ void rsign_options_default(rsign_options* opt) {
   opt->lanczos_max = 600;
   opt->batch_graphs = 1;
   opt->batch_tile = 0;
+  opt->ns_scaling = 0;
+  opt->margin = NAN;
 }
 
 rsign_status rsign_reflector_ex(const double* H, int64_t d, int32_t k, double s, double tol,

@@ -251,10 +251,11 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
       // of a small-K tile on this GPU
       float accf = 0.0f;
 #pragma unroll
+      const float c2 = a.ns_c2 != 0.0f ? a.ns_c2 : 1.0f;  // E = I - a^2 X^2 (scaled step)
       for (int jj = 0; jj < 32; ++jj) {
         const int j = j0 + jj;
         const bool real = row_real && (j < d_real);
-        const float e = real ? ((i == j ? 1.0f : 0.0f) - v[jj]) : 0.0f;
+        const float e = real ? ((i == j ? 1.0f : 0.0f) - (c2 == 1.0f ? v[jj] : c2 * v[jj])) : 0.0f;
         v[jj] = e;
         if (real && j >= i) accf = fmaf((j > i ? 2.0f : 1.0f) * e, e, accf);
       }
@@ -269,8 +270,14 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) x[jj] += xl[jj];
       }
+      const float c1 = a.ns_c1 != 0.0f ? a.ns_c1 : 1.0f;  // X+ = a (X + 1/2 X E) (scaled step)
+      if (c1 == 1.0f) {
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) v[jj] = x[jj] + 0.5f * v[jj];
+        for (int jj = 0; jj < 32; ++jj) v[jj] = x[jj] + 0.5f * v[jj];
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) v[jj] = c1 * (x[jj] + 0.5f * v[jj]);
+      }
       if (i >= j0 && i < j0 + 32 && i < d_real) {
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj)

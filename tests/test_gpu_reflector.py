@@ -283,3 +283,67 @@ def test_refine_off_midpoint_shift_same_reflector(theta):
     R, info, st = _run(rs, torch, spec.H, 12, s, rs.Policy.FP16_REFINE, tol=1e-7)
     assert st == rs.Status.OK
     assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, 12)) <= 1e-7
+
+
+def test_scaled_steps_fp64_match_the_oracle_iterates():
+    # plain-method workload with the scaled step (margin = half-gap of the midpoint shift)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.split_spectrum_config(seed=0)
+    s = oracle.midpoint(*spec.gap)
+    margin = oracle.margin(s, *spec.gap)
+    R_or, _ = oracle.reflector(spec.H, spec.k)
+    R, info, st = _run(rs, torch, spec.H, spec.k, s, rs.Policy.FP64, tol=1e-12, ns_scaling=1, margin=margin)
+    _, info_p, _ = _run(rs, torch, spec.H, spec.k, s, rs.Policy.FP64, tol=1e-12)
+    assert st == rs.Status.OK and info.cert_ok == 1
+    assert spec_norm_sym(R - R_or) <= 1e-12
+    A = oracle.shifted(spec.H, s)
+    alpha = oracle.gershgorin_alpha(A)
+    coef = oracle.scaled_ns_coeffs(alpha * margin)
+    assert info.ns_scaled_steps == len(coef)
+    assert info.steps_fp64 < info_p.steps_fp64
+    its = oracle.scaled_ns_iterates(alpha * A, coef, info.steps_fp64)
+    assert np.max(np.abs(R - its[-1])) <= 1e-12
+
+
+@pytest.mark.parametrize("policy", ["FP16_REFINE", "BF16_REFINE"])
+def test_scaled_steps_refine_reach_1e6_with_fewer_steps(policy):
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k, delta = 1024, 16, 1e-2
+    spec = workloads.controlled_spectrum(d, k, delta, seed=40 + d + k)
+    R, info, st = _run(rs, torch, spec.H, k, 0.0, rs.Policy[policy], tol=1e-6, ns_scaling=1, margin=delta)
+    _, info_p, _ = _run(rs, torch, spec.H, k, 0.0, rs.Policy[policy], tol=1e-6)
+    err = spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, k))
+    assert st == rs.Status.OK and info.cert_ok == 1, info.as_dict()
+    assert err <= 1e-6, (err, info.as_dict())
+    assert info.err_est <= 1e-6
+    assert info.steps_low < info_p.steps_low
+    assert info.ns_scaled_steps > 0
+
+
+@pytest.mark.parametrize("factor", [0.1, 10.0])
+def test_scaled_steps_with_a_wrong_margin_stay_correct(factor):
+    # an underestimated margin only slows the scaled steps down; an
+    # overestimated one leaves eigenvalues below l behind (they still grow),
+    # the stop rule waits for them and the result is the same reflector
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k, delta = 512, 7, 2e-2
+    spec = workloads.controlled_spectrum(d, k, delta, seed=77)
+    R, info, st = _run(rs, torch, spec.H, k, 0.0, rs.Policy.FP64, tol=1e-12, ns_scaling=1,
+                       margin=factor * delta)
+    assert st == rs.Status.OK and info.cert_ok == 1
+    assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, k)) <= 1e-11
+
+
+def test_scaled_steps_with_power_alpha_and_auto_shift():
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 768, 12
+    spec = workloads.controlled_spectrum(d, k, 3e-2, seed=78)
+    R, info, st = _run(rs, torch, spec.H, k, float("nan"), rs.Policy.FP16_REFINE, tol=1e-6, ns_scaling=1,
+                       alpha_mode=int(rs.AlphaMode.POWER))
+    assert st == rs.Status.OK and info.cert_ok == 1
+    assert info.ns_scaled_steps > 0  # the automatic shift's certified margin drives the scaling
+    assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, k)) <= 1e-6

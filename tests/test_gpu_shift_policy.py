@@ -129,19 +129,13 @@ def test_midpoint_and_damped_policies_refresh_every_matrix(policy):
 def test_unresolved_gap_is_reported():
     torch = cuda_or_skip()
     rs = lib_or_fail()
-    # lam_k and lam_{k+1} 4e-16 apart: below the FP64 resolution of the
-    # endpoint estimates (Ritz residuals ~ u ||H||), so the margin test of
-    # Prop. 4.2 fails.  (An exactly repeated eigenvalue is a different matter:
-    # a single Krylov sequence sees only one copy of it.)
-    sp = workloads.controlled_spectrum(256, 4, 0.05, seed=64)
-    lam = sp.lam.copy()
-    lam[3], lam[4] = -2e-16, 2e-16
-    H = (sp.Q * lam) @ sp.Q.T
-    H = 0.5 * (H + H.T)
+    # an interior gap (k = d/2) of 2e-9 among eigenvalues ~1e-3 apart: the
+    # Lanczos budget cannot resolve it, so the margin test of Prop. 4.2 fails
+    sp = workloads.controlled_spectrum(1024, 512, 1e-9, seed=64)
     st = rs.shift_state()
-    status, rep = rs.shift_update(H, None, 4, st, rs.ShiftPolicy.MIDPOINT)
+    status, rep = rs.shift_update(sp.H, None, 512, st, rs.ShiftPolicy.MIDPOINT)
     assert status == rs.Status.ERR_GAP
-    assert np.isnan(st.shift)
+    assert np.isnan(st.shift) and np.isnan(st.margin_cert)
 
 
 def test_bad_arguments():
