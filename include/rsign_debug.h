@@ -63,6 +63,24 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
                                       int32_t sym, double* out, void* stream);
 
 /*
+ * Digit levels (5 bits each, at most 7) of the refinement's FP64-grade
+ * products: the polish SYRK R^2, the first sweep's R A and the later sweeps'
+ * R A (defaults 0, 0, 7; 0 = chosen by the tolerance: 5 levels for tol >= 1e-6,
+ * else 6).  Values outside 0..7 leave a setting unchanged.  Process-wide;
+ * returns the previous settings as 100 p + 10 f + l.
+ */
+int32_t rsign_dbg_set_refine_levels(int32_t polish, int32_t ra_first, int32_t ra_later);
+
+/*
+ * The order in which the persistent tcgen05 GEMM visits the 128 x 256 tiles of
+ * one dp x dp product (host computation, no GPU): entry t * cluster + r is
+ * the (bm, bn) of schedule unit t for cluster rank r; sym selects the upper
+ * triangle.  With bm == NULL returns an upper bound of the entry count;
+ * otherwise fills bm/bn and returns the count; -1 for a bad dp.
+ */
+int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t cluster, int32_t* bm, int32_t* bn);
+
+/*
  * FP64-emulating product on the FP16 tensor cores (the products of the FP64
  * polish steps): as rsign_dbg_fp64grade_gemm with digit planes of beta bits
  * (the widest for which a pair product over d_real terms is exact in FP32:

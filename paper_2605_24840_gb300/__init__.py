@@ -180,6 +180,10 @@ def load():
     lib.rsign_dbg_f64_gemm.restype = ctypes.c_int
     lib.rsign_dbg_fp64grade_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
     lib.rsign_dbg_fp64grade_gemm.restype = ctypes.c_int
+    lib.rsign_dbg_set_refine_levels.argtypes = [i32, i32, i32]
+    lib.rsign_dbg_set_refine_levels.restype = i32
+    lib.rsign_dbg_tile_order.argtypes = [i64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.rsign_dbg_tile_order.restype = i32
     lib.rsign_dbg_fp64e_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
     lib.rsign_dbg_fp64e_gemm.restype = ctypes.c_int
     lib.rsign_dbg_set_tc_cluster.argtypes = [i32]
@@ -487,6 +491,24 @@ def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def dbg_set_refine_levels(polish=-1, ra_first=-1, ra_later=-1):
+    """Set the digit levels of the refinement's FP64-grade products (0 = by the tolerance,
+    -1 keeps a setting); returns the previous settings as 100 p + 10 f + l."""
+    return int(load().rsign_dbg_set_refine_levels(int(polish), int(ra_first), int(ra_later)))
+
+
+def dbg_tile_order(dp, sym=0, cluster=1):
+    """(bm, bn) arrays of the persistent GEMM's tile visiting order (host only)."""
+    lib = load()
+    n = lib.rsign_dbg_tile_order(int(dp), int(sym), int(cluster), None, None)
+    if n < 0:
+        raise RsignError(Status.ERR_ARG)
+    bm = (ctypes.c_int32 * n)()
+    bn = (ctypes.c_int32 * n)()
+    m = lib.rsign_dbg_tile_order(int(dp), int(sym), int(cluster), bm, bn)
+    return np.array(bm[:m]), np.array(bn[:m])
 
 
 def dbg_fp64e_gemm(A, B, d_real=None, sym=0, out=None, stream=None):

@@ -311,15 +311,28 @@ __global__ void to_f64_kernel(const T* __restrict__ src, size_t n, double* __res
 }
 
 // y = A x, one warp per row.
+// 16-byte loads, four in flight per lane (dp is a multiple of 256)
 __global__ void gemv_kernel(const double* __restrict__ A, int dp, const double* __restrict__ x,
                             double* __restrict__ y) {
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= dp) return;
-  double s = 0.0;
-  const double* a = A + (size_t)row * dp;
-  for (int j = lane; j < dp; j += 32) s += a[j] * x[j];
-  s = warp_sum(s);
+  const double2* a = reinterpret_cast<const double2*>(A + (size_t)row * dp);
+  const double2* xv = reinterpret_cast<const double2*>(x);
+  double s0 = 0.0, s1 = 0.0;
+  const int n2 = dp >> 1;
+  for (int j = lane; j < n2; j += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = j + 32 * u;
+      if (q < n2) {
+        const double2 av = a[q], bv = xv[q];
+        s0 = fma(av.x, bv.x, s0);
+        s1 = fma(av.y, bv.y, s1);
+      }
+    }
+  }
+  double s = warp_sum(s0 + s1);
   if (lane == 0) y[row] = s;
 }
 
@@ -333,12 +346,14 @@ __global__ void normalize_kernel(double* y, int n, double* x, double* nrm) {
   if (threadIdx.x < 32) {
     s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
     s = warp_sum(s);
-    if (threadIdx.x == 0) sh[0] = sqrt(s);
+    if (threadIdx.x == 0) {
+      const double nr = sqrt(s);
+      nrm[0] = nr;
+      sh[0] = nr > 0.0 ? 1.0 / nr : 0.0;  // one division for the block
+    }
   }
   __syncthreads();
-  const double nr = sh[0];
-  if (threadIdx.x == 0) nrm[0] = nr;
-  const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  const double inv = sh[0];
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i] * inv;
 }
 

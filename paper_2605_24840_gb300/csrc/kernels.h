@@ -42,6 +42,10 @@ enum TcEpi : int {
   TC_EPI_NS_SYRK = 2,    // acc = X^2: out_lp = I - acc (masked to d), residual partials
   TC_EPI_NS_UPDATE = 3,  // acc = X E: out_lp = X_in + 1/2 acc, trace partials
   TC_EPI_OZAKI = 4,      // out_f64 (+)= rs_i cs_j group_scale_g acc (exact integer groups)
+  TC_EPI_TANGENT = 5,    // acc = sigma X E X (symmetric): the tangent step of the refinement,
+                         // E <- a (1/2 E + inv (P + P^T)) - a^3 inv acc, inv = 1/(2 sigma),
+                         // in place on the FP32 E (both triangles), P = sigma E Et (FP32,
+                         // full); per (tile, warp) max |E| into tg_max
 };
 
 constexpr int kTcMaxPairs = 72;
@@ -103,6 +107,12 @@ struct TcGemmArgs {
   long long mat_stride;    // elements of the output type between consecutive matrices
   int a_planes, b_planes;  // slices per matrix in A / B
   int mat_vec_stride;      // TC_EPI_OZAKI: elements between matrices in rs / cs / a_diag / b_diag
+  // TC_EPI_TANGENT operands
+  float* tg_E;             // FP32 E (dp x dp), read and rewritten
+  const float* tg_P;       // FP32 sigma E Et (dp x dp, full)
+  const float* tg_sigma;   // device scalar sigma
+  float tg_a;              // step scaling a (1 = plain)
+  float* tg_max;           // 4 per tile
   // scaled Newton-Schulz step X+ = 1/2 a X (3I - a^2 X^2): TC_EPI_NS_SYRK stores
   // E = I - ns_c2 X^2 (ns_c2 = a^2), TC_EPI_NS_UPDATE stores ns_c1 (X + 1/2 X E)
   // (ns_c1 = a); 0 means 1 (the plain step)
@@ -111,6 +121,10 @@ struct TcGemmArgs {
 
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
 int tc_num_tiles(int dp, int sym);
+// Host copy of the single-matrix tile order (128 x 256 tiles, cluster size
+// cl): (bm, bn) of schedule unit t and cluster rank r at index t cl + r;
+// returns the number of entries.
+int tc_tile_order(int dp, int sym, int cl, int* bm, int* bn);
 // Process-wide default for TcGemmArgs::cluster == 0 (2 unless set to 1);
 // returns the previous value.
 int tc_set_default_cluster(int cl);
@@ -341,9 +355,10 @@ cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockm
 cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
                               cudaStream_t st);
 // Matrix-free estimate of ||G||_2, G = 1/2 R C, C = R A - A R (FP64 A, R):
-// power steps on v -> 1/2 R (R (A v) - A (R v)), five FP64 GEMVs per step; the
-// commutator action is formed from FP64 matrix-vector products, accurate to
-// ~1e-16 relative per term, so no FP64-grade matrix product is needed.
+// power steps on the antisymmetric C, v -> R (A v) - A (R v), four FP64 GEMVs
+// per step, ||G||_2 = ||C||_2 / 2 for the orthogonal R; the commutator action
+// is formed from FP64 matrix-vector products, accurate to ~1e-16 relative per
+// term, so no FP64-grade matrix product is needed.
 // work: 6 dp doubles; result -> *out (device double).
 cudaError_t commutator_gain_norm(const double* A, const double* R, int dp, int d, int iters, double* work,
                                  double* out, cudaStream_t st);

@@ -216,6 +216,20 @@ cudaError_t lanczos_endpoints(const double* A, int dp, int d, int k, int max_ite
         const double floor_r = 16.0 * std::sqrt((double)d) * 1.1102230246251565e-16 * tn;
         out->eps_k = std::fabs(hb[m - 1] * lc[0]) + floor_r;
         out->eps_k1 = std::fabs(hb[m - 1] * lc[1]) + floor_r;
+        // The pair's indices k, k+1 count the Ritz values between it and the
+        // spectrum end; they are eigenvalue indices only if those Ritz values
+        // have converged too.  Their largest residual bound joins both
+        // errors, so an unconverged interior (k near d/2 with m < d) cannot
+        // pass the margin test with a mislabelled pair.
+        double worst = 0.0;
+        const int q0 = low ? 0 : j0 + 2, q1 = low ? j0 : m;  // the other Ritz values up to the end
+        for (int q = q0; q < q1; ++q) {
+          double tq, lq;
+          tridiag_ritz(a.data(), b.data(), m, q, &tq, &lq);
+          worst = std::max(worst, std::fabs(hb[m - 1] * lq));
+        }
+        out->eps_k = std::max(out->eps_k, worst + floor_r);
+        out->eps_k1 = std::max(out->eps_k1, worst + floor_r);
         out->iters = m;
         const double eps = std::max(out->eps_k, out->eps_k1);
         const double mhat = 0.5 * (out->lam_k1 - out->lam_k);

@@ -273,16 +273,37 @@ __global__ void polish_update_kernel(double* __restrict__ R, const float* __rest
 // eigenvector with probability one for the matrices met here).
 __global__ void gemv_f32_kernel(const float* __restrict__ M, int dp, const float* __restrict__ v,
                                 float* __restrict__ w, int init) {
+  // FP32: a norm estimate needs no more, and the FP64 pipe is slow here.
+  // 16-byte loads, four in flight per lane (dp is a multiple of 256).
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= dp) return;
-  const float* m = M + (size_t)row * dp;
-  float s = 0.f;  // FP32: a norm estimate needs no more, and the FP64 pipe is slow here
-  if (init) {
-    for (int j = lane; j < dp; j += 32) s += m[j] * (1.0f + (float)(j % 7) * 0.125f);
-  } else {
-    for (int j = lane; j < dp; j += 32) s += m[j] * v[j];
+  const float4* m = reinterpret_cast<const float4*>(M + (size_t)row * dp);
+  const float4* vv = reinterpret_cast<const float4*>(v);
+  const int n4 = dp >> 2;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  for (int j = lane; j < n4; j += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = j + 32 * u;
+      if (q < n4) {
+        const float4 a = m[q];
+        float4 b;
+        if (init) {
+          const int e = 4 * q;
+          b = make_float4(1.0f + (float)(e % 7) * 0.125f, 1.0f + (float)((e + 1) % 7) * 0.125f,
+                          1.0f + (float)((e + 2) % 7) * 0.125f, 1.0f + (float)((e + 3) % 7) * 0.125f);
+        } else {
+          b = vv[q];
+        }
+        s0 = fmaf(a.x, b.x, s0);
+        s1 = fmaf(a.y, b.y, s1);
+        s2 = fmaf(a.z, b.z, s2);
+        s3 = fmaf(a.w, b.w, s3);
+      }
+    }
   }
+  float s = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) w[row] = s;
@@ -291,30 +312,37 @@ __global__ void gemv_f32_kernel(const float* __restrict__ M, int dp, const float
 // v = w / ||w||; *out = ||w|| / ||v_prev|| (v_prev normalised except on the first pass)
 __global__ void power_normalize_kernel(const float* __restrict__ w, int n, float* __restrict__ v, double* out,
                                        int first) {
-  __shared__ double sh[32];
-  double s = 0.0, s0 = 0.0;
+  // squares summed in FP32 per thread (a handful of terms), then in FP64
+  // across threads; one division for the block (FP64 work on one SM is slow)
+  __shared__ double sh[32], sh0[32];
+  __shared__ float inv_sh;
+  float sf = 0.f, sf0 = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    s += (double)w[i] * w[i];
+    sf = fmaf(w[i], w[i], sf);
     if (first) {
-      const double v0 = 1.0 + (i % 7) * 0.125;
-      s0 += v0 * v0;
+      const float v0 = 1.0f + (float)(i % 7) * 0.125f;
+      sf0 = fmaf(v0, v0, sf0);
     }
   }
-  s = warp_sum(s);
-  s0 = warp_sum(s0);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  double s = warp_sum((double)sf), s0 = warp_sum((double)sf0);
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = s;
+    sh0[threadIdx.x >> 5] = s0;
+  }
   __syncthreads();
-  double tot = 0.0;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += sh[q];
+  if (threadIdx.x == 0) {
+    double tot = 0.0, tot0 = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      tot += sh[q];
+      tot0 += sh0[q];
+    }
+    const double nw = sqrt(tot);
+    inv_sh = nw > 0.0 ? (float)(1.0 / nw) : 0.0f;
+    *out = first ? nw / sqrt(tot0) : nw;
+  }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s0;
-  __syncthreads();
-  double tot0 = 0.0;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot0 += sh[q];
-  const double nw = sqrt(tot);
-  const double inv = nw > 0.0 ? 1.0 / nw : 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (float)(w[i] * inv);
-  if (threadIdx.x == 0) *out = first ? nw / sqrt(tot0) : nw;
+  const float inv = inv_sh;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
 }
 
 // y = A x (FP64), one warp per row, two matrices at once: y1 = M1 x1, y2 = M2 x2
@@ -326,11 +354,22 @@ __global__ void gemv2_f64_kernel(const double* __restrict__ M1, const double* __
   if (row >= 2 * dp) return;
   const bool second = row >= dp;
   const int r = second ? row - dp : row;
-  const double* m = (second ? M2 : M1) + (size_t)r * dp;
-  const double* x = second ? x2 : x1;
-  double s = 0.0;
-  for (int j = lane; j < dp; j += 32) s += m[j] * x[j];
-  s = warp_sum(s);
+  const double2* m = reinterpret_cast<const double2*>((second ? M2 : M1) + (size_t)r * dp);
+  const double2* x = reinterpret_cast<const double2*>(second ? x2 : x1);
+  const int n2 = dp >> 1;
+  double s0 = 0.0, s1 = 0.0;
+  for (int j = lane; j < n2; j += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = j + 32 * u;
+      if (q < n2) {
+        const double2 a = m[q], b = x[q];
+        s0 = fma(a.x, b.x, s0);
+        s1 = fma(a.y, b.y, s1);
+      }
+    }
+  }
+  const double s = warp_sum(s0 + s1);
   if (lane == 0) (second ? y2 : y1)[r] = s;
 }
 
@@ -564,14 +603,17 @@ cudaError_t commutator_gain_norm(const double* A, const double* R, int dp, int d
   start_vec_f64_kernel<<<(dp + 255) / 256, 256, 0, st>>>(w, d, dp);
   cudaError_t e = normalize(w, dp, v, out, st);
   if (e != cudaSuccess) return e;
+  // ||R C v|| = ||C v|| for the (orthogonal to working accuracy) R, so the
+  // steps run on the antisymmetric C itself: v <- C v / ||C v|| turns within
+  // the dominant invariant plane (eigenvalues +-i mu) and ||C v|| -> mu =
+  // ||C||_2, as fast as power steps on C^2; four GEMVs a step
   for (int it = 0; it < iters; ++it) {
     gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(A, v, t1, R, v, t2, dp);      // A v, R v
     gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(R, t1, y1, A, t2, y2, dp);    // R A v, A R v
-    diff_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y1, y2, t1, dp);           // C v
-    if ((e = gemv_f64(R, dp, t1, w, st)) != cudaSuccess) return e;          // R C v
-    if ((e = normalize(w, dp, v, out, st)) != cudaSuccess) return e;        // ||R C v|| (v unit)
+    diff_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y1, y2, w, dp);            // C v
+    if ((e = normalize(w, dp, v, out, st)) != cudaSuccess) return e;        // ||C v|| (v unit)
   }
-  // *out = ||R C v_prev|| = 2 ||G v_prev||: halve it
+  // *out = ||C v_prev|| = 2 ||G v_prev|| (G = 1/2 R C): halve it
   scale_scalar_kernel<<<1, 1, 0, st>>>(out, 0.5);
   return cudaGetLastError();
 }

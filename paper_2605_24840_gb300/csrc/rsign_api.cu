@@ -240,7 +240,7 @@ cudaError_t fp64e_polish(Ctx& c, DevBuf& mem, double* xb[2], double* E, int dp, 
 // products; everything else is FP16/BF16 with FP32 accumulation.
 // ---------------------------------------------------------------------------
 struct RefineIn {
-  int dp, d, fmt, M, max_sweeps;
+  int dp, d, k, fmt, M, max_sweeps;
   double alpha, tol;
   double* A64;          // A = sym(H) - sI, FP64, zero padded
   double* R64;          // in: stage-1 result; out: refined reflector
@@ -254,6 +254,21 @@ struct RefineOut {
   bool converged = false;
   double resid = NAN, corr = NAN, comm = NAN, err_est = NAN;
 };
+
+// Digit levels of the refinement's FP64-grade products (5 bits each): the
+// polish SYRK R^2, the first sweep's R A and the later sweeps' R A; 0 = by
+// the tolerance and the index.  The truncation error scales with the
+// off-diagonal row maxima of R = I - 2 P_k, which grow like sqrt(min(k,
+// d - k))/d.  Measured: at d = 8192, k = 16, delta = 1e-2 five levels for
+// both reach 3.8e-7 in one sweep (six: 2.1e-7, 7 ms more; four for R A: a
+// second sweep); at d = 768, k = 384 five levels take three sweeps and leave
+// ||R^2 - I|| ~ 1e-6, six take one.
+int g_levels_polish = 0, g_levels_ra0 = 0, g_levels_ra = kSlices;
+int levels_for(int set, double tol, int d, int k) {
+  if (set > 0) return set;
+  const bool few = 32 * std::min(k, d - k) <= d;
+  return (tol >= 1e-6 && few) ? kSlices - 2 : kSlices - 1;
+}
 
 cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, RefineOut* o) {
   const int dp = in.dp, d = in.d;
@@ -302,7 +317,9 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     if (!c.ok(r = split_rows(in.R64, dp, Rs, st))) return r;
     // R^2 to ~1e-9 absolute suffices for the polish: 6 levels (30 bits of the
     // off-diagonal part, the diagonal exact)
-    if (!c.ok(r = ozaki_gemm(Rs, Rs, dp, d, 1, N64, status, c.num_sms, st, kSlices - 1))) return r;
+    if (!c.ok(r = ozaki_gemm(Rs, Rs, dp, d, 1, N64, status, c.num_sms, st,
+                             levels_for(g_levels_polish, in.tol, d, in.k))))
+      return r;
     if (!c.ok(r = ident_minus(N64, dp, d, C32, bmax, part, st))) return r;
     if (!c.ok(r = sum_partials(part, ntile, red + 0, st))) return r;
     if (!c.ok(r = max_pow2(bmax, ntile, fs + 0, st))) return r;
@@ -352,7 +369,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       // a-posteriori check of the current R (matrix free, FP64 GEMVs):
       // err ~ 1.5 kappa alpha ||G||_2 with kappa the gain of the last tangent solve
       if (!c.ok(commutator_gain_norm(in.A64, in.R64, dp, d, kCheckIters, cwork, red + 9, st))) return c.err;
-      c.launches += 5 * kCheckIters + 2;
+      c.launches += 4 * kCheckIters + 2;
       RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
       RS_TRY(cudaStreamSynchronize(st));
       const double g2 = h_red[9];
@@ -368,7 +385,8 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     if (!c.ok(split_rows(in.R64, dp, Rs, st))) return c.err;
     // the first sweep only needs the commutator to ~1e-4 of its (large) size:
     // 6 levels; later sweeps use all 7
-    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st, sw == 0 ? kSlices - 1 : kSlices)))
+    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st,
+                         sw == 0 ? levels_for(g_levels_ra0, in.tol, d, in.k) : g_levels_ra)))
       return c.err;
     if (!c.ok(antisym_part(N64, dp, C32, bmax, part, st))) return c.err;
     if (!c.ok(sum_partials(part, ntile, red + 4, st))) return c.err;
@@ -386,10 +404,15 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       if (!c.ok(scale_to_lp(E32, dd, fs + 5, Elp, in.fmt, st))) return c.err;
       if (!c.ok(tc(Elp, in.Et[m], in.fmt, 0, TC_EPI_STORE_F32, P32))) return c.err;   // E Et
       if (!c.ok(tc(in.X[m], Elp, in.fmt, 0, TC_EPI_STORE_LP, Qlp))) return c.err;     // X E
-      if (!c.ok(tc(Qlp, in.X[m], in.fmt, 1, TC_EPI_STORE_F32, Q32))) return c.err;    // X E X
-      const float am = (in.a != nullptr && m < in.n_a) ? (float)in.a[m] : 1.0f;
-      if (!c.ok(tangent_combine(E32, P32, Q32, dp, fs + 5, am, bmax, st))) return c.err;
-      if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return c.err;
+      // (X E) X with the tangent step fused into its epilogue (E updated in place)
+      TcGemmArgs tg{};
+      tg.dp = dp; tg.d_real = d; tg.sym = 1; tg.epi = TC_EPI_TANGENT; tg.n_groups = 1;
+      tg.group_start[0] = 0; tg.group_start[1] = 1; tg.pair_a[0] = 0; tg.pair_b[0] = 0;
+      tg.group_scale[0] = 1.0; tg.scale = 1.0f; tg.status = status;
+      tg.tg_E = E32; tg.tg_P = P32; tg.tg_sigma = fs + 5; tg.tg_max = bmax;
+      tg.tg_a = (in.a != nullptr && m < in.n_a) ? (float)in.a[m] : 1.0f;
+      if (!c.ok(tc_gemm(tg, Qlp, 1, in.X[m], 1, in.fmt, c.num_sms, st))) return c.err;
+      if (!c.ok(max_pow2(bmax, tc_num_tiles(dp, 1) * 4, fs + 4, st))) return c.err;
     }
     if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 7, st))) return c.err;
     c.launches += 2 * kPowerIters - 1;
@@ -688,7 +711,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     if (refine && ctl_h.status == 0 && result == RSIGN_OK) {
       // ------------------------------------------- commutator refinement sweeps
       RefineIn in{};
-      in.dp = dp; in.d = d; in.fmt = fmt; in.M = steps_low; in.alpha = alpha; in.tol = tol;
+      in.dp = dp; in.d = d; in.k = k; in.fmt = fmt; in.M = steps_low; in.alpha = alpha; in.tol = tol;
       in.A64 = A64; in.R64 = xb64[0]; in.X = xs.data(); in.Et = es.data();
       in.a = coef.empty() ? nullptr : coef.data(); in.n_a = (int)coef.size();
       in.max_sweeps = std::max(1, opt.max_sweeps);
@@ -1304,6 +1327,22 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
   if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
   cudaGetLastError();
   return res;
+}
+
+int32_t rsign_dbg_set_refine_levels(int32_t polish, int32_t ra_first, int32_t ra_later) {
+  const int prev = g_levels_polish * 100 + g_levels_ra0 * 10 + g_levels_ra;
+  auto ok = [](int v) { return v >= 0 && v <= kSlices; };
+  if (ok(polish)) g_levels_polish = polish;
+  if (ok(ra_first)) g_levels_ra0 = ra_first;
+  if (ok(ra_later)) g_levels_ra = ra_later;
+  return prev;
+}
+
+int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t cluster, int32_t* bm, int32_t* bn) {
+  if (dp < 256 || dp % 256 || dp > 16384) return -1;
+  const int n = tc_num_tiles((int)dp, sym ? 1 : 0) * 2;  // upper bound of the entries
+  if (!bm || !bn) return n;
+  return tc_tile_order((int)dp, sym ? 1 : 0, cluster == 2 ? 2 : 1, bm, bn);
 }
 
 rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, int64_t d_real, int32_t sym,

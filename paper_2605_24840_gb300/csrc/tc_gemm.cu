@@ -53,6 +53,15 @@ struct Cfg {
 // triangular schedule schedule-row r (rows r cl BM .. ) needs the columns
 // bn >= floor(r cl BM / BN); for BN = 256 both members of a pair are always
 // needed together.
+//
+// Order: blocks of 2048 rows (16 tile rows, or 8 super-rows of a pair) x
+// kBW = 8 columns (2048 columns), block-rows top to bottom, column blocks
+// left to right, row-major inside a block.  The ~150 tiles in flight then
+// cover about one block, whose row and column panels (2 x 2048 rows of K)
+// stay in L2 across all the pair products of the tiles, instead of one row
+// of units streaming every column panel.
+constexpr int kBW = 8;
+
 template <int BN>
 struct TileSched {
   int nbm, nbn, sym, cl, n;
@@ -65,22 +74,45 @@ struct TileSched {
       for (int r = 0; r < rows; ++r) n += nbn - first(r);
     }
   }
-  __device__ __host__ int first(int r) const { return (r * cl * BM) / BN; }
+  __device__ __host__ int first(int r) const { return sym ? (r * cl * BM) / BN : 0; }
   // unit t -> (bm, bn) for cluster rank `rank`
-  __device__ __forceinline__ void decode(int t, int rank, int& bm, int& bn) const {
-    int r, c;
-    if (!sym) {
-      r = t / nbn;
-      c = t % nbn;
-    } else {
-      r = 0;
-      for (;;) {
-        const int cnt = nbn - first(r);
-        if (t < cnt) break;
+  __device__ __host__ void decode(int t, int rank, int& bm, int& bn) const {
+    const int rows = nbm / cl;
+    const int bh = 16 / cl;  // schedule rows per block (2048 matrix rows)
+    int r = 0, c = 0;
+    for (int r0 = 0; r0 < rows; r0 += bh) {
+      const int r1 = r0 + bh < rows ? r0 + bh : rows;
+      int cnt = 0;
+      for (int q = r0; q < r1; ++q) cnt += nbn - first(q);
+      if (t >= cnt) {
         t -= cnt;
-        ++r;
+        continue;
       }
-      c = first(r) + t;
+      // inside block-row [r0, r1): column blocks from the first needed column
+      for (int c0 = first(r0);; c0 += kBW) {
+        const int c1 = c0 + kBW < nbn ? c0 + kBW : nbn;
+        int bc = 0;
+        for (int q = r0; q < r1; ++q) {
+          const int lo = c0 > first(q) ? c0 : first(q);
+          bc += c1 > lo ? c1 - lo : 0;
+        }
+        if (t >= bc) {
+          t -= bc;
+          continue;
+        }
+        for (int q = r0; q < r1; ++q) {
+          const int lo = c0 > first(q) ? c0 : first(q);
+          const int w = c1 > lo ? c1 - lo : 0;
+          if (t < w) {
+            r = q;
+            c = lo + t;
+            break;
+          }
+          t -= w;
+        }
+        break;
+      }
+      break;
     }
     bm = cl == 1 ? r : 2 * r + rank;
     bn = c;
@@ -129,6 +161,18 @@ __device__ __forceinline__ void store32_lp(T* dst, const float* v) {
              ((uint32_t)(*reinterpret_cast<uint16_t*>(&hi)) << 16);
     }
     d4[q] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+__device__ __forceinline__ void load_f32x32(const float* src, float* v) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 u = s4[q];
+    v[4 * q] = u.x;
+    v[4 * q + 1] = u.y;
+    v[4 * q + 2] = u.z;
+    v[4 * q + 3] = u.w;
   }
 }
 
@@ -250,8 +294,8 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
       // once: FP64 arithmetic per element would cost far more than the MMAs
       // of a small-K tile on this GPU
       float accf = 0.0f;
-#pragma unroll
       const float c2 = a.ns_c2 != 0.0f ? a.ns_c2 : 1.0f;  // E = I - a^2 X^2 (scaled step)
+#pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int j = j0 + jj;
         const bool real = row_real && (j < d_real);
@@ -304,6 +348,37 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
         if (a.split) out[plane + (size_t)(j0 + jj) * ld + i] = from_f32<T>(lo[jj]);
       }
     }
+  } else if constexpr (EPI == TC_EPI_TANGENT) {
+    // tangent step fused with the product sigma X E X (symmetric schedule):
+    // every element read here is upper (j >= i) and written only by this
+    // thread (its mirror goes to a lower position nobody reads), except in
+    // the diagonal 32 x 32 block, where the warp's reads are ordered before
+    // its stores by __syncwarp
+    float* E = a.tg_E;
+    const float* P = a.tg_P;
+    const float inv = 0.5f / a.tg_sigma[0];
+    const float am = a.tg_a, a3 = am * am * am;
+    float e_old[32], p1[32];
+    load_f32x32(E + row + j0, e_old);
+    load_f32x32(P + row + j0, p1);
+    float vn[32];
+    float mx = 0.0f;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const float pt = P[(size_t)(j0 + jj) * ld + i];  // (P^T)_ij, coalesced across the warp
+      vn[jj] = (am == 1.0f) ? 0.5f * e_old[jj] + inv * (p1[jj] + pt - v[jj])
+                            : am * (0.5f * e_old[jj] + inv * (p1[jj] + pt)) - (a3 * inv) * v[jj];
+      if (above || j0 + jj >= i) mx = fmaxf(mx, fabsf(vn[jj]));
+    }
+    acc1 = fmax(acc1, (double)mx);
+    if (!above) __syncwarp();
+    float4* d4 = reinterpret_cast<float4*>(E + row + j0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d4[q] = make_float4(vn[4 * q], vn[4 * q + 1], vn[4 * q + 2], vn[4 * q + 3]);
+    if (!above) __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj)
+      if (above || j0 + jj > i) E[(size_t)(j0 + jj) * ld + i] = vn[jj];
   } else {  // TC_EPI_OZAKI
     // The group sums are exact integers (< 2^24).  They are combined as
     // int64 fixed-point values V = sum_g acc_g 2^(group_shift[g]) (one per
@@ -633,6 +708,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const double s = warp_sum(acc1);
         if (lane == 0) args.partials[(size_t)u.slot * 4 + quad] = s;
       }
+      if constexpr (EPI == TC_EPI_TANGENT) {
+        double m = acc1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) args.tg_max[(size_t)u.slot * 4 + quad] = (float)m;
+      }
     }
   }
 
@@ -743,6 +824,7 @@ cudaError_t dispatch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorM
     case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, CL, 256>(a, ma, mb, grid, idesc, st);
     case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, CL, 256>(a, ma, mb, grid, idesc, st);
     case TC_EPI_OZAKI: return launch<TC_EPI_OZAKI, T, CL, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_TANGENT: return launch<TC_EPI_TANGENT, T, CL, 256>(a, ma, mb, grid, idesc, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -768,6 +850,13 @@ cudaError_t dispatch_grouped(const TcGemmArgs& a, const CUtensorMap& ma, const C
 }  // namespace
 
 int tc_num_tiles(int dp, int sym) { return TileSched<256>(dp, sym, 1).n; }
+
+int tc_tile_order(int dp, int sym, int cl, int* bm, int* bn) {
+  const TileSched<256> sc(dp, sym, cl == 2 ? 2 : 1);
+  for (int t = 0; t < sc.n; ++t)
+    for (int rk = 0; rk < sc.cl; ++rk) sc.decode(t, rk, bm[t * sc.cl + rk], bn[t * sc.cl + rk]);
+  return sc.n * sc.cl;
+}
 
 static int g_default_cluster = 2;
 int tc_set_default_cluster(int cl) {
