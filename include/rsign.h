@@ -98,8 +98,11 @@ typedef struct {
                               a-posteriori check (REFINE): 2 ||G||_2 from FP64 power
                               steps on v -> 1/2 R (R A v - A R v); NaN otherwise       */
   double err_est;          /* a-posteriori estimate of ||R - sign(H - sI)||_2 (REFINE):
-                              1.5 kappa alpha ||G||_2, G = 1/2 R (R A - A R), kappa the
-                              gain of the last tangent solve; NaN for other policies   */
+                              max(1.5 kappa alpha ||G||_2, ||C||_2 / g): G = 1/2 R C,
+                              C = R A - A R, kappa the gain of the last tangent solve,
+                              g the eigenvalue gap of the 2 x 2 Rayleigh-Ritz projection
+                              of A on the dominant plane of C (at least 2 mu when a
+                              margin mu is known); NaN for other policies              */
   double tol_fro;          /* the residual threshold applied: max(tol, 16 d u_64)      */
   double ms_total;         /* device time of the call, ms (CUDA events on `stream`)    */
   double ms_low;           /* device time of the low-precision stage, ms               */
@@ -124,7 +127,20 @@ typedef struct {
                               matrix are those of the whole batch                      */
   int32_t ns_scaled_steps; /* leading steps run with the scaled step (rsign_options
                               ns_scaling); 0 = the plain iteration throughout           */
-  int32_t reserved;
+  int32_t refine_levels;   /* REFINE: 5-bit digit levels of the first sweep's FP64-grade
+                              R A product (5..7, from the truncation model: the error it
+                              leaves after the sweep ~ 2^(-5L) s_A s_R sqrt(d) / mu <=
+                              tol/2, s the largest row scales of the digit splits, mu the
+                              margin or a lower bound from the stage-1 step count)     */
+  double err_bound;        /* REFINE with a known margin mu (rsign_options.margin or the
+                              certified margin of the automatic shift): bound of
+                              ||R - sign(H - sI)||_2 from the last check, 1 - sqrt(1 - 2c),
+                              c = ||R A - A R||_2 / (2 mu) + ||R^2 - I||_2 / 2 (inf if
+                              2c >= 1); with rsign_options.refine_stop = RSIGN_STOP_BOUND
+                              the refinement stops on err_bound <= tol instead of err_est
+                              <= tol.  Both 2-norms are FP64 power-step
+                              estimates (commutator_norm and the check's power steps on
+                              R^2 - I).  NaN otherwise                                  */
 } rsign_info;
 
 /* Optional knobs; rsign_options_default() fills the defaults. */
@@ -156,7 +172,21 @@ typedef struct {
   double margin;            /* lower bound of min_i |lam_i - s| for ns_scaling (the
                                half-gap for a midpoint shift), NaN = unknown (default);
                                the automatic shift supplies its certified margin       */
+  int32_t refine_stop;      /* REFINE stop test: RSIGN_STOP_ESTIMATE (default) stops on
+                               err_est <= tol; RSIGN_STOP_BOUND stops on err_bound <= tol
+                               and needs a margin (rsign_options.margin or the automatic
+                               shift), else RSIGN_ERR_ARG.  The bound divides the
+                               commutator by the whole gap 2 mu, so broadband rounding
+                               noise in R (large eigenvalue differences) inflates it:
+                               it can stay above tol at errors far below tol           */
+  int32_t reserved_opt;
 } rsign_options;
+
+/* Stop tests of the refinement sweeps (rsign_options.refine_stop). */
+typedef enum {
+  RSIGN_STOP_ESTIMATE = 0,
+  RSIGN_STOP_BOUND = 1
+} rsign_refine_stop;
 
 void rsign_options_default(rsign_options* opt);
 

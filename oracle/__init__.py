@@ -16,7 +16,8 @@ passage of the paper it restates:
   * the midpoint shift (Prop. 4.1) and the inexact-shift admissibility
     margin (Prop. 4.2);
   * alpha = 1/||A||_inf (Sec. 4.3 scaling discussion);
-  * the Daleckii-Krein derivative of sign (used to check the adjoint).
+  * the Daleckii-Krein derivative of sign (used to check the adjoint);
+  * the commutator error bound of a refined reflector (Sylvester argument).
 
 Pins: every function here is checked in ``tests/test_oracle_pins.py`` against
 closed forms, library routines, brute force on tiny inputs and hand-derived
@@ -304,6 +305,25 @@ def reuse_admissible(m_hat: float, eps: float, drift: float):
     endpoint drift (bounded by ||H_{n+1} - H_n||_2 via Weyl) is below m_hat - eps.
     Returns (certified, guaranteed margin)."""
     return (drift < m_hat - eps), m_hat - eps - drift
+
+
+def commutator_error_bound(comm2: float, margin_: float, rho: float = 0.0) -> float:
+    """A-posteriori bound of ||R - sign(A)||_2 for a symmetric R from the
+    commutator C = R A - A R, the margin mu = min |lam_i(A)| and rho = ||R^2 - I||_2.
+
+    Not printed in the paper; it is the standard Sylvester-equation argument
+    (Bhatia-Davis-McIntosh) for the refined reflector of the commutator
+    refinement.  With S = sign(A) and F = R - S, split F in the eigenbasis of A
+    into the blocks between the negative and positive eigenspaces (F_off) and
+    within them (F_same).  F_off solves F_off A_+ - A_- F_off = C_off with
+    A_- <= -mu and A_+ >= mu, so ||F_off|| <= ||C||/(2 mu); R^2 - I = S F + F S
+    + F^2 gives ||F_same|| <= (rho + ||F||^2)/2.  Hence f = ||F|| satisfies
+    f <= c + f^2/2, c = ||C||/(2 mu) + rho/2, and on the branch connected to S
+    (f < 1): f <= 1 - sqrt(1 - 2c).  Returns inf when 2c >= 1."""
+    c = comm2 / (2.0 * margin_) + 0.5 * rho
+    if not (2.0 * c < 1.0):
+        return math.inf
+    return 2.0 * c / (1.0 + math.sqrt(1.0 - 2.0 * c))
 
 
 # --------------------------------------------------------------------------

@@ -65,7 +65,8 @@ class Info(ctypes.Structure):
         ("lam_k_est", ctypes.c_double), ("lam_k1_est", ctypes.c_double), ("shift_eps", ctypes.c_double),
         ("margin_lb", ctypes.c_double), ("lanczos_iters", ctypes.c_int32), ("steps_pred", ctypes.c_int32),
         ("batch_grouped", ctypes.c_int32), ("batch_tile", ctypes.c_int32),
-        ("ns_scaled_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("ns_scaled_steps", ctypes.c_int32), ("refine_levels", ctypes.c_int32),
+        ("err_bound", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -80,7 +81,13 @@ class Options(ctypes.Structure):
         ("low_split", ctypes.c_int32), ("lanczos_max", ctypes.c_int32),
         ("batch_graphs", ctypes.c_int32), ("batch_tile", ctypes.c_int32),
         ("ns_scaling", ctypes.c_int32), ("margin", ctypes.c_double),
+        ("refine_stop", ctypes.c_int32), ("reserved_opt", ctypes.c_int32),
     ]
+
+
+class RefineStop(enum.IntEnum):
+    ESTIMATE = 0
+    BOUND = 1
 
 
 class ShiftPolicy(enum.IntEnum):

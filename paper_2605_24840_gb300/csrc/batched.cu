@@ -152,11 +152,15 @@ __global__ void batch_to_f64_kernel(const T* __restrict__ X0, const T* __restric
 // matrices that stay active and ctr[1] the finished blocks: the last block
 // sets all_done (1 once no matrix is active) and clears both counters.
 constexpr int kCheckWarps = 4;
+// trp (nullable): trace partials of the current iterates (from the grouped
+// update, same slots); a floor or stagnation stop of matrix m then also needs
+// |trace X_m - (d_m - 2 k_m)| <= 1/2 + 2 u sqrt(d_m).
 __global__ void batch_check_kernel(const double* __restrict__ partials, const int* __restrict__ slot_begin,
                                    int n, const int* __restrict__ dv, int mode, double tol, double u,
                                    int max_steps, int* __restrict__ done, int* __restrict__ steps,
                                    double* __restrict__ prev, double* __restrict__ resid,
-                                   int* __restrict__ all_done, int* __restrict__ ctr) {
+                                   int* __restrict__ all_done, int* __restrict__ ctr,
+                                   const double* __restrict__ trp, const int* __restrict__ kv) {
   __shared__ int active;
   if (threadIdx.x == 0) active = 0;
   __syncthreads();
@@ -164,16 +168,22 @@ __global__ void batch_check_kernel(const double* __restrict__ partials, const in
   const int m = blockIdx.x * kCheckWarps + (threadIdx.x >> 5);
   if (m < n && done[m] == 0) {  // uniform across the warp
     const int q0 = slot_begin[m] * 4, q1 = slot_begin[m + 1] * 4;
-    double s = 0.0;
-    for (int q = q0 + lane; q < q1; q += 32) s += partials[q];
+    double s = 0.0, tr = 0.0;
+    for (int q = q0 + lane; q < q1; q += 32) {
+      s += partials[q];
+      if (trp != nullptr) tr += trp[q];
+    }
     s = warp_sum(s);
+    tr = warp_sum(tr);
     if (lane == 0) {
       const double r = sqrt(fmax(s, 0.0));
       const double d = (double)dv[m];
       const int mm = steps[m];
       const double tol_abs = mode == 0 ? 0.0 : (mode == 1 ? fmax(tol, 16.0 * d * kEps64) : -1.0);
       bool stop = r < tol_abs;
-      if (u > 0.0) {
+      const bool trace_ok = trp == nullptr || mm == 0 ||
+                            fabs(tr - (d - 2.0 * kv[m])) <= 0.5 + 2.0 * u * sqrt(d);
+      if (u > 0.0 && trace_ok) {
         const double flo = 2.0 * u * sqrt(d), fhi = 16.0 * u * sqrt(d);
         if (r <= flo) stop = true;
         if (mm >= 1 && r <= fhi && r >= 0.5 * prev[m]) stop = true;
@@ -360,7 +370,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     // ---- per-matrix control arrays (one int and one double allocation)
     // ints: d, dp_lp(128), dp_lp(256), dp64, done, steps, flags, done64, steps64,
     //       slot_begin (lp: n+1, f64: n+1), status, all_done, all_done64
-    enum { I_D = 0, I_DP128, I_DP256, I_DP64, I_DONE, I_STEPS, I_FLAGS, I_DONE64, I_STEPS64, I_N };
+    enum { I_D = 0, I_DP128, I_DP256, I_DP64, I_DONE, I_STEPS, I_FLAGS, I_DONE64, I_STEPS64, I_K, I_N };
     const size_t n_int = (size_t)I_N * ng + 3 * (size_t)(ng + 1) + 6;
     int* ib = nullptr;
     double* db = nullptr;
@@ -387,6 +397,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     std::vector<int> dp128(ng), dp256(ng), dp64(ng);
     for (int m = 0; m < ng; ++m) {
       h_int[(size_t)I_D * ng + m] = g.d[m];
+      h_int[(size_t)I_K * ng + m] = g.k[m];
       dp128[m] = round_up(g.d[m], 128);
       dp256[m] = round_up(g.d[m], 256);
       dp64[m] = round_up(g.d[m], kF64Tile);
@@ -448,9 +459,11 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         n_slots_max = std::max(n_slots_max, ulp[c].size());
       }
     }
+    double* trpart = nullptr;  // trace partials of the grouped updates
     if (mem.alloc((void**)&A64, nel * 8) != cudaSuccess ||
         mem.alloc((void**)&rowpart, (size_t)ng * (D / 32) * D * 8) != cudaSuccess ||
-        mem.alloc((void**)&partials, n_slots_max * 4 * 8) != cudaSuccess)
+        mem.alloc((void**)&partials, n_slots_max * 4 * 8) != cudaSuccess ||
+        mem.alloc((void**)&trpart, n_slots_max * 4 * 8) != cudaSuccess)
       return fail_cuda();
     {
       dim3 grid(D / 32, D / 32, ng), block(32, 8);
@@ -618,6 +631,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
       mat_dp_sel = ia(I_DP128);
       TcGemmArgs up = sy;
       up.epi = TC_EPI_NS_UPDATE;
+      up.partials = trpart;
       const double u = fmt ? 0.00390625 : 0.00048828125;  // unit roundoff of the operand type
       const int max_steps = opt.max_steps;
       auto step = [&](int gs, cudaStream_t s2, bool last) -> bool {
@@ -626,7 +640,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         if (tc_gemm_grouped(sy, tile_bn, xm, ng, xm, ng, fmt, num_sms, s2) != cudaSuccess) return false;
         batch_check_kernel<<<check_blocks, 32 * kCheckWarps, 0, s2>>>(
             partials, slot_use, ng, ia(I_D), 0, tol, u, max_steps, ia(I_DONE), ia(I_STEPS), da(D_PREV),
-            da(D_RESID), all_done, ctr);
+            da(D_RESID), all_done, ctr, trpart, ia(I_K));
         if (cudaGetLastError() != cudaSuccess) return false;
         if (last) return true;
         TcGemmArgs a = up;
@@ -700,7 +714,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         if (fp64e_gemm(Xs, Xs, D, dmax, 1, e64, sq, status, num_sms, s2, P) != cudaSuccess) return false;
         batch_check_kernel<<<check_blocks, 32 * kCheckWarps, 0, s2>>>(
             partials, slot_sel, ng, ia(I_D), 2, tol, 0.0, max_steps, ia(I_DONE64), ia(I_STEPS64),
-            da(D_PREV), da(D_RESID), all_done64, ctr);
+            da(D_PREV), da(D_RESID), all_done64, ctr, nullptr, nullptr);
         if (cudaGetLastError() != cudaSuccess) return false;
         if (last) return true;
         Es.full = e64;
@@ -729,7 +743,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         if (f64_gemm_grouped(a, s2) != cudaSuccess) return false;
         batch_check_kernel<<<check_blocks, 32 * kCheckWarps, 0, s2>>>(
             partials, slot_64, ng, ia(I_D), mode, tol, 0.0, max_steps, ia(I_DONE64), ia(I_STEPS64),
-            da(D_PREV), da(D_RESID), all_done64, ctr);
+            da(D_PREV), da(D_RESID), all_done64, ctr, nullptr, nullptr);
         if (cudaGetLastError() != cudaSuccess) return false;
         if (last) return true;
         F64GemmArgs b = sy;
@@ -807,6 +821,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         inf->correction_fro = NAN;
         inf->commutator_norm = NAN;
         inf->err_est = NAN;
+        inf->err_bound = NAN;
         inf->tol_fro = tol_fro;
         inf->ms_total = ms_total;
         inf->ms_low = low ? ms_low : 0.0;

@@ -232,23 +232,37 @@ __global__ void sum_kernel(const double* __restrict__ x, int n, double* out) {
   }
 }
 
+// tr: optional trace partials of the current iterate (n_tr values); a floor
+// or stagnation stop then also needs |trace - tr_target| <= tr_tol, so a
+// residual that sits in the floor band while a few eigenvalues are still far
+// from +-1 (the slow first phase of the iteration) cannot stop it.
 __global__ void ns_check_kernel(const double* __restrict__ x, int n, double* hist, int m, double tol_abs,
-                                double floor_lo, double floor_hi, double ratio, int* done, int* steps) {
-  __shared__ double sh[32];
-  double s = 0.0;
+                                double floor_lo, double floor_hi, double ratio, int* done, int* steps,
+                                const double* __restrict__ tr, int n_tr, double tr_target, double tr_tol) {
+  __shared__ double sh[32], sh2[32];
+  double s = 0.0, t = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  if (tr != nullptr)
+    for (int i = threadIdx.x; i < n_tr; i += blockDim.x) t += tr[i];
   s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = s;
+    sh2[threadIdx.x >> 5] = t;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
     s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    t = (threadIdx.x < (blockDim.x >> 5)) ? sh2[threadIdx.x] : 0.0;
     s = warp_sum(s);
+    t = warp_sum(t);
     if (threadIdx.x == 0) {
       const double r = sqrt(fmax(s, 0.0));
       if (*done == 0) {  // after a stop the partials are stale: leave hist alone
         hist[m] = r;
-        bool stop = r < tol_abs || r <= floor_lo;
-        if (!stop && m >= 1 && r <= floor_hi && r >= ratio * hist[m - 1]) stop = true;
+        const bool trace_ok = tr == nullptr || fabs(t - tr_target) <= tr_tol;
+        bool stop = r < tol_abs || (trace_ok && r <= floor_lo);
+        if (!stop && trace_ok && m >= 1 && r <= floor_hi && r >= ratio * hist[m - 1]) stop = true;
         if (stop) {
           *done = 1;
           *steps = m;
@@ -463,6 +477,11 @@ cudaError_t inf_norm_finish(const double* rowpart, int dp, double* rowsum, doubl
   return cudaGetLastError();
 }
 
+cudaError_t max_f64(const double* x, int n, double* out, cudaStream_t st) {
+  max_kernel<<<1, 1024, 0, st>>>(x, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t scale_convert(const double* src, size_t n, const double* scale_dev, double mult, void* dst,
                           int fmt, cudaStream_t st) {
   const int g = grid_for(n);
@@ -508,8 +527,10 @@ cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_
 }
 
 cudaError_t ns_check(const double* partials, int n, double* hist, int m, double tol_abs, double floor_lo,
-                     double floor_hi, double ratio, int* done, int* steps, cudaStream_t st) {
-  ns_check_kernel<<<1, 1024, 0, st>>>(partials, n, hist, m, tol_abs, floor_lo, floor_hi, ratio, done, steps);
+                     double floor_hi, double ratio, int* done, int* steps, cudaStream_t st,
+                     const double* tr, int n_tr, double tr_target, double tr_tol) {
+  ns_check_kernel<<<1, 1024, 0, st>>>(partials, n, hist, m, tol_abs, floor_lo, floor_hi, ratio, done, steps, tr,
+                                      n_tr, tr_target, tr_tol);
   return cudaGetLastError();
 }
 

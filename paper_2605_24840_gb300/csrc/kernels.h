@@ -212,10 +212,12 @@ cudaError_t copy_pad(const double* src, int d, double* dst, int dp, cudaStream_t
 //   r < tol_abs                                   (converged), or
 //   r <= floor_lo, or (m >= 1 && r <= floor_hi && r >= ratio * hist[m-1])
 //                                                 (low-precision floor reached)
-// and on a stop *done = 1, *steps = m.
+// where the two floor stops also need |sum(tr) - tr_target| <= tr_tol when
+// trace partials tr are given; on a stop *done = 1, *steps = m.
 cudaError_t ns_check(const double* partials, int n, double* hist, int m, double tol_abs,
                      double floor_lo, double floor_hi, double ratio, int* done, int* steps,
-                     cudaStream_t st);
+                     cudaStream_t st, const double* tr = nullptr, int n_tr = 0, double tr_target = 0.0,
+                     double tr_tol = 0.0);
 // Adjoint helpers (FP64): G <- 1/2 G + 1/2 (P1 + P1^T - P2) (the transposed
 // Frechet step of X + 1/2 X (I - X^2), P1 = G E, P2 = X G X); dst = scale/2 (src + src^T).
 cudaError_t tangent_combine_f64(double* G, const double* P1, const double* P2, int dp, cudaStream_t st);
@@ -328,6 +330,8 @@ cudaError_t antisym_part(const double* N, int dp, float* C, float* blockmax, dou
 cudaError_t absmax_tiles(const float* M, int dp, float* blockmax, cudaStream_t st);
 // out[0] = max of n floats; out[1] = 2^-ceil(log2 out[0]) (1 if out[0] == 0).
 cudaError_t max_pow2(const float* x, int n, float* out, cudaStream_t st);
+// out[0] = max(0, max_i x_i), out[1] = 1 / out[0] (0 if the max is 0); one block
+cudaError_t max_f64(const double* x, int n, double* out, cudaStream_t st);
 // dst (FP16/BF16) = src * scale[0]   (scale a device float)
 cudaError_t scale_to_lp(const float* src, size_t n, const float* scale, void* dst, int fmt,
                         cudaStream_t st);

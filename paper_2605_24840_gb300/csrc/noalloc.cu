@@ -195,6 +195,7 @@ extern "C" rsign_status rsign_reflector_noalloc(const double* H, int64_t d64, in
     info->correction_fro = NAN;
     info->commutator_norm = NAN;
     info->err_est = NAN;
+    info->err_bound = NAN;
     info->tol_fro = tol_fro;
     info->launches = 6 + 3 * (int64_t)m;
     info->workspace_bytes = 0;

@@ -345,10 +345,14 @@ __global__ void power_normalize_kernel(const float* __restrict__ w, int n, float
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
 }
 
-// y = A x (FP64), one warp per row, two matrices at once: y1 = M1 x1, y2 = M2 x2
+// y = A x (FP64), one warp per row, two matrices at once: y1 = M1 x1, y2 =
+// M2 x2, and optionally a second vector against either matrix (y1b = M1 x1b,
+// y2b = M2 x2b; nullptr: none), read from the same pass over the rows
 __global__ void gemv2_f64_kernel(const double* __restrict__ M1, const double* __restrict__ x1,
-                                 double* __restrict__ y1, const double* __restrict__ M2,
-                                 const double* __restrict__ x2, double* __restrict__ y2, int dp) {
+                                 double* __restrict__ y1, const double* __restrict__ x1b,
+                                 double* __restrict__ y1b, const double* __restrict__ M2,
+                                 const double* __restrict__ x2, double* __restrict__ y2,
+                                 const double* __restrict__ x2b, double* __restrict__ y2b, int dp) {
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= 2 * dp) return;
@@ -356,28 +360,83 @@ __global__ void gemv2_f64_kernel(const double* __restrict__ M1, const double* __
   const int r = second ? row - dp : row;
   const double2* m = reinterpret_cast<const double2*>((second ? M2 : M1) + (size_t)r * dp);
   const double2* x = reinterpret_cast<const double2*>(second ? x2 : x1);
+  const double2* xb = reinterpret_cast<const double2*>(second ? x2b : x1b);
   const int n2 = dp >> 1;
-  double s0 = 0.0, s1 = 0.0;
-  for (int j = lane; j < n2; j += 128) {
+  double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
+  if (xb == nullptr) {
+    for (int j = lane; j < n2; j += 128) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int q = j + 32 * u;
-      if (q < n2) {
-        const double2 a = m[q], b = x[q];
-        s0 = fma(a.x, b.x, s0);
-        s1 = fma(a.y, b.y, s1);
+      for (int u = 0; u < 4; ++u) {
+        const int q = j + 32 * u;
+        if (q < n2) {
+          const double2 a = m[q], b = x[q];
+          s0 = fma(a.x, b.x, s0);
+          s1 = fma(a.y, b.y, s1);
+        }
+      }
+    }
+  } else {
+    for (int j = lane; j < n2; j += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = j + 32 * u;
+        if (q < n2) {
+          const double2 a = m[q], b = x[q], c = xb[q];
+          s0 = fma(a.x, b.x, s0);
+          s1 = fma(a.y, b.y, s1);
+          t0 = fma(a.x, c.x, t0);
+          t1 = fma(a.y, c.y, t1);
+        }
       }
     }
   }
   const double s = warp_sum(s0 + s1);
-  if (lane == 0) (second ? y2 : y1)[r] = s;
+  const double t = warp_sum(t0 + t1);
+  if (lane == 0) {
+    (second ? y2 : y1)[r] = s;
+    if (xb != nullptr) (second ? y2b : y1b)[r] = t;
+  }
 }
 
 __global__ void scale_scalar_kernel(double* x, double f) { x[0] *= f; }
 
-__global__ void diff_kernel(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c,
-                            int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c[i] = a[i] - b[i];
+// out[0..2] = a.b, c.e, f.g over n entries (one block)
+__global__ void dot3_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                            const double* __restrict__ c, const double* __restrict__ e,
+                            const double* __restrict__ f, const double* __restrict__ g, int n,
+                            double* __restrict__ out) {
+  __shared__ double sh[3][32];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    s0 = fma(a[i], b[i], s0);
+    s1 = fma(c[i], e[i], s1);
+    s2 = fma(f[i], g[i], s2);
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[0][wid] = s0;
+    sh[1][wid] = s1;
+    sh[2][wid] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[threadIdx.x][q];
+    out[threadIdx.x] = t;
+  }
+}
+
+// c = a - b and f = e - g (two differences in one pass)
+__global__ void diff2_kernel(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c,
+                             const double* __restrict__ e, const double* __restrict__ g, double* __restrict__ f,
+                             int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    c[i] = a[i] - b[i];
+    f[i] = e[i] - g[i];
+  }
 }
 
 __global__ void start_vec_f64_kernel(double* y, int d, int dp) {
@@ -409,15 +468,24 @@ cudaError_t split_rows_grouped(const double* M, int D, int n_mat, const int* mat
   return cudaGetLastError();
 }
 
+int fp64e_planes(int beta) { return beta > 0 ? (54 + beta - 1) / beta : 0; }
+
 int fp64e_beta(int k_extent) {
-  // largest digit width whose single-pair group sum stays exact in FP32:
-  // 2^(2 beta - 2) K <= 2^24
-  for (int b = 7; b >= 4; --b)
-    if (std::ldexp(1.0, 2 * b - 2) * (double)k_extent <= std::ldexp(1.0, 24)) return b;
+  // the widest digit whose pair products are exact in FP32 (2^(2 beta - 2) K
+  // <= 2^24 for one pair) and whose full product fits the kernel's limits:
+  // P (P + 1) / 2 pair products and one group per (level, max_pairs pairs)
+  for (int b = 7; b >= 5; --b) {
+    const double bound1 = std::ldexp(1.0, 2 * b - 2) * (double)k_extent;
+    const int max_pairs = (int)std::floor(std::ldexp(1.0, 24) / bound1);
+    if (max_pairs < 1) continue;
+    const int P = fp64e_planes(b);
+    if (P * (P + 1) / 2 > kTcMaxPairs) continue;
+    int groups = 0;
+    for (int t = 0; t < P; ++t) groups += (t + 1 + max_pairs - 1) / max_pairs;
+    if (groups <= kTcMaxGroups) return b;
+  }
   return 0;
 }
-
-int fp64e_planes(int beta) { return beta > 0 ? (54 + beta - 1) / beta : 0; }
 
 cudaError_t fp64e_plan(TcGemmArgs* a, int n_planes, int beta, int levels, int k_extent) {
   const int L = levels < 1 ? 1 : (levels > n_planes ? n_planes : levels);
@@ -593,27 +661,48 @@ cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int it
 
 cudaError_t commutator_gain_norm(const double* A, const double* R, int dp, int d, int iters, double* work,
                                  double* out, cudaStream_t st) {
-  double* v = work;           // current unit vector
+  double* vb[2] = {work, work + 10 * dp};  // unit vectors of the commutator steps (alternating)
   double* t1 = work + dp;     // A v
   double* t2 = work + 2 * dp; // R v
   double* y1 = work + 3 * dp; // R A v
   double* y2 = work + 4 * dp; // A R v
-  double* w = work + 5 * dp;  // C v, then R C v
+  double* w = work + 5 * dp;  // C v
+  double* z = work + 6 * dp;  // current unit vector of the involution-residual steps
+  double* t3 = work + 7 * dp; // R z
+  double* y3 = work + 8 * dp; // R R z
+  double* w3 = work + 9 * dp; // (R^2 - I) z
+  double* t4 = work + 11 * dp;  // A v_last
+  double* t5 = work + 12 * dp;  // R v_last (unused)
+  if (iters < 1) return cudaErrorInvalidValue;
   const int blocks2 = (2 * dp + 7) / 8;
   start_vec_f64_kernel<<<(dp + 255) / 256, 256, 0, st>>>(w, d, dp);
-  cudaError_t e = normalize(w, dp, v, out, st);
+  cudaError_t e = normalize(w, dp, vb[0], out, st);
   if (e != cudaSuccess) return e;
+  if ((e = normalize(w, dp, z, out + 1, st)) != cudaSuccess) return e;
   // ||R C v|| = ||C v|| for the (orthogonal to working accuracy) R, so the
   // steps run on the antisymmetric C itself: v <- C v / ||C v|| turns within
   // the dominant invariant plane (eigenvalues +-i mu) and ||C v|| -> mu =
-  // ||C||_2, as fast as power steps on C^2; four GEMVs a step
+  // ||C||_2, as fast as power steps on C^2.  Power steps on the symmetric
+  // N = R^2 - I ride along in the same passes over A and R (R applied to two
+  // vectors per pass).  Four GEMVs a step
   for (int it = 0; it < iters; ++it) {
-    gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(A, v, t1, R, v, t2, dp);      // A v, R v
-    gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(R, t1, y1, A, t2, y2, dp);    // R A v, A R v
-    diff_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y1, y2, w, dp);            // C v
-    if ((e = normalize(w, dp, v, out, st)) != cudaSuccess) return e;        // ||C v|| (v unit)
+    const double* v = vb[it & 1];
+    double* vn = vb[(it + 1) & 1];
+    gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(A, v, t1, nullptr, nullptr, R, v, t2, z, t3, dp);  // A v; R v, R z
+    gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(R, t1, y1, t3, y3, A, t2, y2, nullptr, nullptr, dp);  // R A v, R R z; A R v
+    diff2_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y1, y2, w, y3, z, w3, dp);  // C v, N z
+    if ((e = normalize(w, dp, vn, out, st)) != cudaSuccess) return e;       // ||C v|| (v unit)
+    if ((e = normalize(w3, dp, z, out + 1, st)) != cudaSuccess) return e;   // ||N z|| (z unit)
   }
-  // *out = ||C v_prev|| = 2 ||G v_prev|| (G = 1/2 R C): halve it
+  // Rayleigh-Ritz on the last plane {v_prev, v_last = C v_prev / ||C v_prev||}
+  // (orthonormal: v^T C v = 0 for the antisymmetric C): the entries of the
+  // 2 x 2 projection of A, out[2..4] = v_prev.A v_prev, v_last.A v_prev,
+  // v_last.A v_last
+  const double* v_prev = vb[(iters - 1) & 1];
+  const double* v_last = vb[iters & 1];
+  gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(A, v_last, t4, nullptr, nullptr, R, v_last, t5, nullptr, nullptr, dp);
+  dot3_kernel<<<1, 1024, 0, st>>>(v_prev, t1, v_last, t1, v_last, t4, dp, out + 2);
+  // out[0] = ||C v_prev|| = 2 ||G v_prev|| (G = 1/2 R C): halve it
   scale_scalar_kernel<<<1, 1, 0, st>>>(out, 0.5);
   return cudaGetLastError();
 }

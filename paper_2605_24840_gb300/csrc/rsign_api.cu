@@ -248,26 +248,56 @@ struct RefineIn {
   void* const* Et;      // I - a_m^2 X_m^2, m = 0 .. M-1 (operand type)
   const double* a;      // step scalings a_m of the stage-1 trajectory (nullptr: all 1)
   int n_a;              // entries of a (steps beyond use 1)
+  double margin;        // lower bound of min |lam_i(A)| (NaN: unknown)
+  double mu_lb;         // margin, or a lower bound from the stage-1 step count
+  bool stop_on_bound;   // stop test on the bound (needs margin) instead of the estimate
 };
 struct RefineOut {
   int sweeps = 0, polish_steps = 0;
   bool converged = false;
-  double resid = NAN, corr = NAN, comm = NAN, err_est = NAN;
+  double resid = NAN, corr = NAN, comm = NAN, err_est = NAN, err_bound = NAN, rho = NAN;
+  int levels_ra0 = 0;
 };
 
 // Digit levels of the refinement's FP64-grade products (5 bits each): the
 // polish SYRK R^2, the first sweep's R A and the later sweeps' R A; 0 = by
-// the tolerance and the index.  The truncation error scales with the
-// off-diagonal row maxima of R = I - 2 P_k, which grow like sqrt(min(k,
-// d - k))/d.  Measured: at d = 8192, k = 16, delta = 1e-2 five levels for
-// both reach 3.8e-7 in one sweep (six: 2.1e-7, 7 ms more; four for R A: a
-// second sweep); at d = 768, k = 384 five levels take three sweeps and leave
-// ||R^2 - I|| ~ 1e-6, six take one.
+// rule.  Polish: the truncation error scales with the off-diagonal row maxima
+// of R = I - 2 P_k, which grow like sqrt(min(k, d - k))/d; five levels when
+// the index is small against d (measured at d = 8192, k = 16), else six.
 int g_levels_polish = 0, g_levels_ra0 = 0, g_levels_ra = kSlices;
 int levels_for(int set, double tol, int d, int k) {
   if (set > 0) return set;
   const bool few = 32 * std::min(k, d - k) <= d;
   return (tol >= 1e-6 && few) ? kSlices - 2 : kSlices - 1;
+}
+
+// First sweep's R A: the commutator's truncation error reaches the
+// correction through the gain of L_sign, up to 1/(2 mu) on the components
+// between the two eigenspaces (and largest there when the spectrum next to
+// the gap is sparse).  Model: error after the sweep ~ 2^(-5L) s_A s_R sqrt(d)
+// / mu, s the largest power-of-two row scales of the two digit splits.
+// Measured at L = 5: it over-predicts 7x..14x on the Allen-Cahn Hessian
+// (d = 1024, 4096; k = 1, 2, 4) and matches within 1.5x on controlled
+// spectra (d = 8192, k = 16; d = 768, k = 384, which needs six levels).  The
+// smallest L in 5..7 with a predicted error <= tol / 2.
+int levels_ra0(double tol, double sA, double sR, int d, double mu) {
+  for (int L = kSlices - 2; L < kSlices; ++L)
+    if (std::ldexp(1.0, -5 * L) * sA * sR * std::sqrt((double)d) <= 0.5 * tol * mu) return L;
+  return kSlices;
+}
+
+// Lower bound of the scaled margin from a plain trajectory that stopped
+// after m steps: an eigenvalue x_0 = gamma reaches p_m(gamma) >= 0.9 only for
+// gamma above the root of p_m(gamma) = 0.9 (the map is increasing on [0, 1]).
+double gamma_from_steps(int m) {
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    const double g = 0.5 * (lo + hi);
+    double x = g;
+    for (int q = 0; q < m; ++q) x = 0.5 * x * (3.0 - x * x);
+    (x >= 0.9 ? hi : lo) = g;
+  }
+  return hi;
 }
 
 cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, RefineOut* o) {
@@ -301,7 +331,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   RS_TRY(mem.alloc((void**)&bmax, (size_t)ntile * 4));
   RS_TRY(mem.alloc((void**)&part, (size_t)std::max(ntile, 1024) * 8));
   RS_TRY(mem.alloc((void**)&fs, 16 * 4));
-  RS_TRY(mem.alloc((void**)&red, 16 * 8));
+  RS_TRY(mem.alloc((void**)&red, 24 * 8));
   int* status = &ctl->status;
 
   auto tc = [&](const void* A, const void* B, int fmt, int sym, int epi, void* out) {
@@ -335,7 +365,8 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   // the split trajectory's floor, and the sweep's own polish step follows the
   // correction (measured: the same error after one sweep with or without it).
   RS_TRY(c.ok(split_rows(in.A64, dp, As, st)) ? cudaSuccess : c.err);
-  double h_red[16];
+  RS_TRY(c.ok(max_f64(As.sigma, dp, red + 16, st)) ? cudaSuccess : c.err);  // s_A
+  double h_red[24];
   if (in.M == 0) {
     // X_0 was already at the low-precision floor (A a scaled near-involution):
     // there is no trajectory to differentiate; the polish alone finishes R.
@@ -362,20 +393,45 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   constexpr int kPowerIters = 24;
   constexpr int kCheckIters = 12;
   double* cwork = nullptr;
-  RS_TRY(mem.alloc((void**)&cwork, (size_t)6 * dp * 8));
+  RS_TRY(mem.alloc((void**)&cwork, (size_t)13 * dp * 8));
   double kappa = NAN;
   for (int sw = 0; sw <= in.max_sweeps; ++sw) {
     if (sw >= 1) {
       // a-posteriori check of the current R (matrix free, FP64 GEMVs):
       // err ~ 1.5 kappa alpha ||G||_2 with kappa the gain of the last tangent solve
       if (!c.ok(commutator_gain_norm(in.A64, in.R64, dp, d, kCheckIters, cwork, red + 9, st))) return c.err;
-      c.launches += 4 * kCheckIters + 2;
+      c.launches += 5 * kCheckIters + 6;
       RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
       RS_TRY(cudaStreamSynchronize(st));
       const double g2 = h_red[9];
       o->comm = 2.0 * g2;  // ||R A - A R||_2 = 2 ||G||_2 for an orthogonal R
-      o->err_est = 1.5 * kappa * in.alpha * g2;
-      if (!(g2 > 0.0) || o->err_est <= in.tol) {
+      o->rho = h_red[10];
+      const bool mu_known = std::isfinite(in.margin) && in.margin > 0.0;
+      // Estimate: the larger of two gains applied to the commutator.  kappa,
+      // the gain ||E||_2 / ||E_0||_2 of the last tangent solve, follows the
+      // previous error's directions; the Rayleigh-Ritz gap g of A on the
+      // dominant plane of C (the 2 x 2 projection from the check) gives the
+      // gain 1/g of the component that dominates C now: a single error
+      // component F between eigenpairs i, j has ||C||_2 = |lam_i - lam_j| ||F||_2.
+      // The second catches errors that the last solve left between
+      // eigenvalues next to the gap (clustered spectra).
+      const double a11 = h_red[11], a12 = h_red[12], a22 = h_red[13];
+      double g_rr = std::sqrt((a11 - a22) * (a11 - a22) + 4.0 * a12 * a12);
+      if (mu_known) g_rr = std::max(g_rr, 2.0 * in.margin);
+      const double est_rr = g_rr > 0.0 ? o->comm / g_rr : INFINITY;
+      o->err_est = std::max(1.5 * kappa * in.alpha * g2, est_rr);
+      // With a known margin mu the error is bounded outright (Sylvester
+      // argument): F = R - sign(A) has its blocks between the two eigenspaces
+      // of A bounded by ||C||_2 / (2 mu) and its blocks within them by
+      // (||R^2 - I||_2 + ||F||^2) / 2, so ||F||_2 <= 1 - sqrt(1 - 2c) with
+      // c = ||C||_2 / (2 mu) + ||R^2 - I||_2 / 2, both 2-norms from the power
+      // steps of the check.
+      if (mu_known) {
+        const double cb = o->comm / (2.0 * in.margin) + 0.5 * o->rho;
+        o->err_bound = 2.0 * cb < 1.0 ? 2.0 * cb / (1.0 + std::sqrt(1.0 - 2.0 * cb)) : INFINITY;
+      }
+      const bool stop = in.stop_on_bound ? (mu_known && o->err_bound <= in.tol) : o->err_est <= in.tol;
+      if (!(g2 > 0.0) || stop) {
         o->converged = true;
         break;
       }
@@ -383,11 +439,19 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     }
     // commutator C = R A - A R from the FP64-grade product N = R A
     if (!c.ok(split_rows(in.R64, dp, Rs, st))) return c.err;
-    // the first sweep only needs the commutator to ~1e-4 of its (large) size:
-    // 6 levels; later sweeps use all 7
-    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st,
-                         sw == 0 ? levels_for(g_levels_ra0, in.tol, d, in.k) : g_levels_ra)))
-      return c.err;
+    // the first sweep's levels from the truncation model; later sweeps use all 7
+    int lev = g_levels_ra;
+    if (sw == 0) {
+      lev = g_levels_ra0;
+      if (lev <= 0) {
+        if (!c.ok(max_f64(Rs.sigma, dp, red + 18, st))) return c.err;  // s_R
+        RS_TRY(cudaMemcpyAsync(h_red + 16, red + 16, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RS_TRY(cudaStreamSynchronize(st));
+        lev = levels_ra0(in.tol, h_red[16], h_red[18], d, in.mu_lb);
+      }
+    }
+    o->levels_ra0 = sw == 0 ? lev : o->levels_ra0;
+    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st, lev))) return c.err;
     if (!c.ok(antisym_part(N64, dp, C32, bmax, part, st))) return c.err;
     if (!c.ok(sum_partials(part, ntile, red + 4, st))) return c.err;
     if (!c.ok(max_pow2(bmax, ntile, fs + 2, st))) return c.err;
@@ -447,6 +511,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   if (std::isinf(s)) return RSIGN_ERR_ARG;
   const bool auto_shift = std::isnan(s);
   const bool refine = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE;
+  if (opt.refine_stop != RSIGN_STOP_ESTIMATE && opt.refine_stop != RSIGN_STOP_BOUND) return RSIGN_ERR_ARG;
+  if (refine && opt.refine_stop == RSIGN_STOP_BOUND && !auto_shift && std::isnan(opt.margin)) return RSIGN_ERR_ARG;
 
   Ctx c;
   c.st = st;
@@ -466,7 +532,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   Ctl ctl_h;
   std::memset(&ctl_h, 0, sizeof(ctl_h));
   int steps_low = 0, steps64 = 0, sweeps_done = 0;
-  double corr_fro = NAN, comm_norm = NAN, err_est = NAN;
+  double corr_fro = NAN, comm_norm = NAN, err_est = NAN, err_bound = NAN;
+  int refine_levels = 0;
   bool conv64 = true;
   double resid = NAN;
   std::vector<double> hist_h;
@@ -654,6 +721,22 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     const double floor_lo = 2.0 * u * std::sqrt((double)d);
     const double floor_hi = 16.0 * u * std::sqrt((double)d);
     const int nt = tc_num_tiles(dp, 1);
+    // With the scaled steps the floor tests wait until the recurrence of
+    // the interval's bottom end has come within u of 1: before that a small
+    // residual is no sign of convergence.
+    int m_min = 0;
+    {
+      double l = std::min(1.0, alpha * (auto_shift ? margin_lb : opt.margin));
+      for (size_t q = 0; q < coef.size() && 1.0 - l > u; ++q) {
+        l = 0.5 * coef[q] * l * (3.0 - coef[q] * coef[q] * l * l);
+        m_min = (int)q + 1;
+      }
+    }
+    // trace guard of the floor tests: the trace of the iterate (from the
+    // update epilogue, in its own partials) within 1/2 + 2 u sqrt(d) of d - 2k
+    double* tr_part = nullptr;
+    if (mem.alloc((void**)&tr_part, (size_t)nt * 4 * 8) != cudaSuccess) return fail_cuda();
+    const double tr_tol = 0.5 + 2.0 * u * std::sqrt((double)d);
     int m = 0;
     bool stopped = false;
     while (m <= opt.max_steps && !stopped) {
@@ -679,12 +762,14 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         sy.ns_c2 = (float)(am * am);
         sy.ns_c1 = (float)am;
         if (!c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st))) return fail_cuda();
-        if (!c.ok(ns_check(partials, nt * 4, hist_low, mm, 0.0, floor_lo, floor_hi, 0.5, &ctl->done_low,
-                           &ctl->steps_low, st)))
+        const bool floors = mm >= m_min;
+        if (!c.ok(ns_check(partials, nt * 4, hist_low, mm, 0.0, floors ? floor_lo : -1.0, floors ? floor_hi : -1.0,
+                           0.5, &ctl->done_low, &ctl->steps_low, st, mm >= 1 ? tr_part : nullptr, nt * 4,
+                           (double)(d - 2 * k), tr_tol)))
           return fail_cuda();
         if (mm == opt.max_steps) break;
         TcGemmArgs up = sy;
-        up.epi = TC_EPI_NS_UPDATE; up.out = xn; up.xin = xm;
+        up.epi = TC_EPI_NS_UPDATE; up.out = xn; up.xin = xm; up.partials = tr_part;
         if (!c.ok(tc_gemm(up, xm, planes, em, planes, fmt, c.num_sms, st))) return fail_cuda();
       }
       if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -715,6 +800,11 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       in.A64 = A64; in.R64 = xb64[0]; in.X = xs.data(); in.Et = es.data();
       in.a = coef.empty() ? nullptr : coef.data(); in.n_a = (int)coef.size();
       in.max_sweeps = std::max(1, opt.max_sweeps);
+      in.margin = auto_shift ? margin_lb : opt.margin;
+      in.stop_on_bound = opt.refine_stop == RSIGN_STOP_BOUND;
+      in.mu_lb = (std::isfinite(in.margin) && in.margin > 0.0)
+                     ? in.margin
+                     : (coef.empty() ? gamma_from_steps(steps_low) / alpha : NAN);
       RefineOut ro{};
       const cudaError_t re = refine_sweeps(c, mem, in, ctl, &ro);
       if (re != cudaSuccess) return fail_cuda();
@@ -724,6 +814,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       corr_fro = ro.corr;
       comm_norm = ro.comm;
       err_est = ro.err_est;
+      err_bound = ro.err_bound;
+      refine_levels = ro.levels_ra0;
       if (!ro.converged && result == RSIGN_OK) result = RSIGN_ERR_NOCONV;
     }
   } else {
@@ -797,6 +889,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     info->correction_fro = corr_fro;
     info->commutator_norm = comm_norm;
     info->err_est = err_est;
+    info->err_bound = err_bound;
+    info->refine_levels = refine_levels;
     info->tol_fro = tol_fro;
     if (opt.timing) {
       float t = 0.f;
@@ -1162,6 +1256,8 @@ void rsign_options_default(rsign_options* opt) {
   opt->batch_tile = 0;
   opt->ns_scaling = 0;
   opt->margin = NAN;
+  opt->refine_stop = RSIGN_STOP_ESTIMATE;
+  opt->reserved_opt = 0;
 }
 
 rsign_status rsign_reflector_ex(const double* H, int64_t d, int32_t k, double s, double tol,

@@ -83,6 +83,15 @@ def test_argument_errors_need_no_gpu(rs):
         st = lib.rsign_reflector(hp, d, k, s, tol, pol, R.ctypes.data, ctypes.byref(info), None)
         assert st == rs.Status.ERR_ARG, (d, k, s, tol, pol, st)
     assert lib.rsign_apply(None, 4, H.ctypes.data, 1, R.ctypes.data, None) == rs.Status.ERR_ARG
+    # stopping the refinement on the bound needs a margin (or the automatic shift)
+    o = rs.default_options(refine_stop=int(rs.RefineStop.BOUND))
+    st = lib.rsign_reflector_ex(H.ctypes.data, 4, 1, 0.0, 1e-6, int(rs.Policy.FP16_REFINE), ctypes.byref(o),
+                                R.ctypes.data, ctypes.byref(info), None)
+    assert st == rs.Status.ERR_ARG
+    o.refine_stop = 2
+    st = lib.rsign_reflector_ex(H.ctypes.data, 4, 1, 0.0, 1e-6, int(rs.Policy.FP64), ctypes.byref(o),
+                                R.ctypes.data, ctypes.byref(info), None)
+    assert st == rs.Status.ERR_ARG
 
 
 @pytest.mark.parametrize("m,seed", [(1, 0), (2, 1), (7, 2), (60, 3), (200, 4)])

@@ -111,3 +111,33 @@ def test_autograd_function_matches_backward_and_daleckii_krein():
     assert np.linalg.norm(H.grad.cpu().numpy() - dk) / np.linalg.norm(dk) < 1e-8
     # the forward value is the reflector itself
     assert np.max(np.abs(R.detach().cpu().numpy() - oracle.reflector_from_basis(spec.Q, k))) < 1e-10
+
+
+@pytest.mark.parametrize("policy,tol", [("FP32", 2e-2), ("BF16_POLISH", 2e-1), ("FP64", 1e-8)])
+def test_backward_adjoint_workload_d2048(policy, tol):
+    # the adjoint workload: d = 2048 controlled spectrum, k = 8, half-gap 1e-2,
+    # checkpoints every 4 iterates; against the oracle's Daleckii-Krein gradient
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 2048, 8
+    spec = workloads.controlled_spectrum(d, k, 1e-2, seed=504)
+    Rbar = _loss_seed(d, 9)
+    Hbar = rs.reflector_backward(torch.from_numpy(spec.H).cuda(), k, 0.0, torch.from_numpy(Rbar).cuda(),
+                                 policy=rs.Policy[policy], ckpt_every=4).cpu().numpy()
+    dk = _dk_gradient(spec, 0.0, Rbar)
+    rel = np.linalg.norm(Hbar - dk) / np.linalg.norm(dk)
+    assert rel < tol, rel
+    if policy == "FP64":
+        # central finite differences of the FP64 forward, step 1e-6
+        rng = np.random.default_rng(10)
+        W = rng.standard_normal((d, d))
+        W = 0.5 * (W + W.T) / np.linalg.norm(W)
+        h = 1e-6
+        Hd = torch.from_numpy(spec.H).cuda()
+        Wd = torch.from_numpy(W).cuda()
+        Rp, _, _ = rs.reflector(Hd + h * Wd, k, 0.0, tol=1e-14, policy=rs.Policy.FP64, check=False)
+        Rm, _, _ = rs.reflector(Hd - h * Wd, k, 0.0, tol=1e-14, policy=rs.Policy.FP64, check=False)
+        Rb = torch.from_numpy(Rbar).cuda()
+        fd = float(((Rp - Rm) * Rb).sum()) / (2 * h)
+        an = float(np.sum(Hbar * W))
+        assert abs(fd - an) <= 1e-4 * max(1.0, abs(an)), (fd, an)

@@ -1,0 +1,114 @@
+"""GPU parity on the Allen-Cahn-shaped Hessian (Sec. 5.3 workload): a PDE
+Hessian whose low end of the spectrum is clustered near the gap, unlike the
+controlled spectra.  The reference reflector comes from LAPACK's eigh on the
+host (the oracle's eigh route); the shift is the oracle's midpoint of the
+k-th gap and the margin its half-width.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import cuda_or_skip, lib_or_fail, spec_norm_sym
+
+pytestmark = pytest.mark.gpu
+
+_CACHE = {}
+
+
+def _problem(n):
+    if n not in _CACHE:
+        H, _ = workloads.allen_cahn_hessian(n=n, seed=1)
+        w, V = np.linalg.eigh(H)
+        _CACHE[n] = (H, w, V)
+    return _CACHE[n]
+
+
+def _run(rs, torch, H, k, s, policy, tol, **opt):
+    Hd = torch.from_numpy(np.ascontiguousarray(H)).cuda()
+    R, info, st = rs.reflector(Hd, k, s, tol=tol, policy=policy, options=rs.default_options(**opt), check=False)
+    torch.cuda.synchronize()
+    return R.cpu().numpy(), info, st
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+@pytest.mark.parametrize("scaled", [0, 1])
+def test_allen_cahn_fp64(k, scaled):
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    H, w, V = _problem(32)
+    s = oracle.midpoint(w[k - 1], w[k])
+    m = oracle.margin(s, w[k - 1], w[k])
+    R, info, st = _run(rs, torch, H, k, s, rs.Policy.FP64, 1e-12, ns_scaling=scaled, margin=m)
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert spec_norm_sym(R - oracle.reflector_from_basis(V, k)) <= 1e-9
+
+
+@pytest.mark.parametrize("policy", ["FP16_REFINE", "BF16_REFINE"])
+@pytest.mark.parametrize("k", [1, 2, 4])
+@pytest.mark.parametrize("scaled", [0, 1])
+def test_allen_cahn_refine_reaches_1e6(policy, k, scaled):
+    # the eigenvalues next to the gap are clustered: the error the first
+    # sweep leaves sits between them, where the gain of the last tangent solve
+    # underestimates it; the Rayleigh-Ritz gain of the check sees it
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    H, w, V = _problem(32)
+    s = oracle.midpoint(w[k - 1], w[k])
+    m = oracle.margin(s, w[k - 1], w[k])
+    R, info, st = _run(rs, torch, H, k, s, rs.Policy[policy], 1e-6, ns_scaling=scaled, margin=m)
+    err = spec_norm_sym(R - oracle.reflector_from_basis(V, k))
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert err <= 1e-6, (err, info.as_dict())
+    assert info.err_est <= 1e-6
+    # the commutator bound (margin known) holds
+    assert err <= info.err_bound * 1.05, (err, info.err_bound)
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_allen_cahn_stop_on_bound_is_honest(k):
+    # stopping on the bound: either the bound reaches the tolerance or the call
+    # reports no convergence with the bound above it; the bound holds
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    H, w, V = _problem(32)
+    s = oracle.midpoint(w[k - 1], w[k])
+    m = oracle.margin(s, w[k - 1], w[k])
+    R, info, st = _run(rs, torch, H, k, s, rs.Policy.FP16_REFINE, 1e-6, ns_scaling=1, margin=m,
+                       refine_stop=int(rs.RefineStop.BOUND), max_sweeps=2)
+    err = spec_norm_sym(R - oracle.reflector_from_basis(V, k))
+    if st == rs.Status.OK:
+        assert info.err_bound <= 1e-6
+    else:
+        assert st == rs.Status.ERR_NOCONV and info.err_bound > 1e-6 and info.sweeps_refine == 2
+    assert err <= info.err_bound * 1.05, (err, info.err_bound)
+
+
+@pytest.mark.parametrize("policy", ["FP16", "BF16", "FP32", "FP16_POLISH", "BF16_POLISH"])
+@pytest.mark.parametrize("scaled", [0, 1])
+def test_allen_cahn_low_precision_certifies(policy, scaled):
+    # the stop rule must not stop before the iterates have the right index
+    # (the trace guard): every low-precision policy certifies
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    H, w, V = _problem(32)
+    k = 2
+    s = oracle.midpoint(w[k - 1], w[k])
+    m = oracle.margin(s, w[k - 1], w[k])
+    R, info, st = _run(rs, torch, H, k, s, rs.Policy[policy], 1e-12, ns_scaling=scaled, margin=m)
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert abs(info.trace - (H.shape[0] - 2 * k)) < 0.5
+
+
+def test_allen_cahn_d4096_refine():
+    # the full-size grid (64 x 64, d = 4096)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    H, w, V = _problem(64)
+    k = 2
+    s = oracle.midpoint(w[k - 1], w[k])
+    m = oracle.margin(s, w[k - 1], w[k])
+    R, info, st = _run(rs, torch, H, k, s, rs.Policy.FP16_REFINE, 1e-6, ns_scaling=1, margin=m)
+    err = spec_norm_sym(R - oracle.reflector_from_basis(V, k))
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert err <= 1e-6 and err <= info.err_bound * 1.05, (err, info.as_dict())

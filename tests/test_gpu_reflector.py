@@ -347,3 +347,21 @@ def test_scaled_steps_with_power_alpha_and_auto_shift():
     assert st == rs.Status.OK and info.cert_ok == 1
     assert info.ns_scaled_steps > 0  # the automatic shift's certified margin drives the scaling
     assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, k)) <= 1e-6
+
+
+def test_refine_stop_on_bound_certifies_a_controlled_spectrum():
+    # with the margin known and the bound as the stop test the returned R is
+    # certified: ||R - R_exact||_2 <= err_bound <= tol.  (The bound needs the
+    # rounding noise of R small against the margin: d = 4096, half-gap 5e-2.)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k, delta = 4096, 16, 5e-2
+    H, lam, Q = workloads.controlled_spectrum_torch(d, k, delta, seed=92)
+    R, info, st = rs.reflector(H, k, 0.0, tol=1e-6, policy=rs.Policy.FP16_REFINE, check=False,
+                               options=rs.default_options(ns_scaling=1, margin=delta,
+                                                          refine_stop=int(rs.RefineStop.BOUND)))
+    Qk = Q[:, :k]
+    D = R - (torch.eye(d, dtype=torch.float64, device=R.device) - 2.0 * Qk @ Qk.T)
+    err = float(torch.linalg.eigvalsh(0.5 * (D + D.T)).abs().max())
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert info.err_bound <= 1e-6 and err <= info.err_bound, (err, info.as_dict())

@@ -461,3 +461,73 @@ def test_scaled_iteration_reaches_the_reflector_brute_force(oracle_mod):
         w, V = np.linalg.eigh(H)
         R = V @ np.diag(np.sign(w)) @ V.T
         assert np.max(np.abs(X - R)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# commutator error bound of a refined reflector (Sylvester argument)
+# ---------------------------------------------------------------------------
+def _expm_antisym(K):
+    # exp of an antisymmetric matrix through the eigen-decomposition of the
+    # Hermitian matrix iK (an orthogonal result)
+    w, U = np.linalg.eigh(1j * K)
+    return np.real((U * np.exp(-1j * w)) @ U.conj().T)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_commutator_bound_holds_brute_force(oracle_mod, seed):
+    # random spectra with a known margin, reflectors rotated away from sign(A)
+    # (exact involutions) and scaled off the involution set: the true error
+    # never exceeds the bound
+    rng = np.random.default_rng(100 + seed)
+    d = 24
+    mu = 10.0 ** rng.uniform(-3, -1)
+    k = int(rng.integers(1, d))
+    lam = np.concatenate([-mu - rng.exponential(0.5, k), mu + rng.exponential(0.5, d - k)])
+    lam[0], lam[-1] = -mu, mu  # the margin is attained on both sides
+    V, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    A = (V * lam) @ V.T
+    S = (V * np.sign(lam)) @ V.T
+    for eps in (1e-8, 1e-5, 1e-3):
+        K = rng.standard_normal((d, d))
+        Q = _expm_antisym(eps * (K - K.T))
+        R = Q @ S @ Q.T
+        eta = rng.uniform(-eps, eps, d)
+        R = R + eps * 0.1 * ((V * eta) @ V.T)  # leaves the involution set
+        R = 0.5 * (R + R.T)
+        comm = np.linalg.norm(R @ A - A @ R, 2)
+        rho = np.linalg.norm(R @ R - np.eye(d), 2)
+        err = np.linalg.norm(R - S, 2)
+        b = oracle_mod.commutator_error_bound(comm, mu, rho)
+        assert err <= b * (1 + 1e-9) + 1e-14, (eps, err, b)
+
+
+def test_commutator_bound_is_tight_on_a_two_by_two_rotation(oracle_mod):
+    # A = diag(-mu, mu), R = the reflector S rotated by theta: ||R - S|| =
+    # 2 sin theta and ||R A - A R|| = 2 mu sin 2 theta, so the bound is
+    # sin 2 theta + O(theta^2): the ratio tends to 1 (a bound with mu in place
+    # of 2 mu would tend to 2)
+    mu = 0.3
+    A = np.diag([-mu, mu])
+    S = np.diag([-1.0, 1.0])
+    for th in (1e-3, 1e-5):
+        c, s = math.cos(th), math.sin(th)
+        Q = np.array([[c, -s], [s, c]])
+        R = Q @ S @ Q.T
+        comm = np.linalg.norm(R @ A - A @ R, 2)
+        assert comm == pytest.approx(2 * mu * math.sin(2 * th), rel=1e-9)
+        err = np.linalg.norm(R - S, 2)
+        b = oracle_mod.commutator_error_bound(comm, mu, 0.0)
+        assert err <= b and b / err < 1 + 2 * th
+
+
+def test_commutator_bound_residual_term_is_tight_for_commuting_errors(oracle_mod):
+    # R = S (1 + eta) commutes with A: C = 0, ||R - S|| = eta and ||R^2 - I|| =
+    # 2 eta + eta^2, so the bound is eta + O(eta^2)
+    mu = 0.1
+    for eta in (1e-9, 1e-6):
+        S = np.diag([-1.0, -1.0, 1.0])
+        R = S * (1 + eta)
+        rho = np.linalg.norm(R @ R - np.eye(3), 2)
+        b = oracle_mod.commutator_error_bound(0.0, mu, rho)
+        assert eta * (1 - 1e-6) <= b <= eta * (1 + 4 * eta) + 1e-15
+    assert oracle_mod.commutator_error_bound(1.0, 1.0, 0.0) == math.inf
