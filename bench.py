@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-policy", default="FP16_POLISH")
     p.add_argument("--no-loop", action="store_true", help="batched: skip the per-matrix call loop")
+    p.add_argument("--batch-tile", type=int, default=0, choices=[0, 128, 256],
+                   help="batched: force the grouped tile width (0: the library's autotuner)")
     return p.parse_args()
 
 
@@ -394,7 +396,8 @@ def run_batched(args):
     stream = torch.cuda.current_stream(dev)
 
     def batched():
-        return rs.reflector_batched(Hs, ks, ss, tol=1e-12, policy=policy, outs=Rs)
+        return rs.reflector_batched(Hs, ks, ss, tol=1e-12, policy=policy, outs=Rs,
+                                    options=rs.default_options(batch_tile=args.batch_tile))
 
     for _ in range(args.warmup):
         _, infos, st = batched()

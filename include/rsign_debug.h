@@ -91,6 +91,25 @@ int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t cluster, int32_t* 
 rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, int64_t d_real, int32_t sym,
                                   double* out, void* stream);
 
+/*
+ * y = M x for device FP64 M (dp x dp, dp a multiple of 256) and x (dp) in the
+ * double-float arithmetic of the refinement's a-posteriori check: M and x
+ * split into hi + lo FP32 pairs, exact product splitting and TwoSum
+ * accumulation on the FP32 pipe, lanes combined in FP64.  y: device FP64.
+ */
+rsign_status rsign_dbg_gemv_df(const double* M, const double* x, int64_t dp, double* y, void* stream);
+
+/*
+ * The matrix-free check of the refinement on device FP64 A, R (dp x dp, dp a
+ * multiple of 256, logical order d): `iters` power steps on C = R A - A R and
+ * on N = R^2 - I from the check's fixed start vector.  out (host, 5 doubles):
+ * ||C v||/2 at the last step (the estimate of ||G||_2), ||N z|| at the last
+ * step, and the 2 x 2 projection of A on the last commutator plane
+ * (v_prev.A v_prev, v_last.A v_prev, v_last.A v_last).
+ */
+rsign_status rsign_dbg_commutator_check(const double* A, const double* R, int64_t dp, int64_t d, int32_t iters,
+                                        double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -193,6 +193,10 @@ def load():
     lib.rsign_dbg_tile_order.restype = i32
     lib.rsign_dbg_fp64e_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
     lib.rsign_dbg_fp64e_gemm.restype = ctypes.c_int
+    lib.rsign_dbg_gemv_df.argtypes = [vp, vp, i64, vp, vp]
+    lib.rsign_dbg_gemv_df.restype = ctypes.c_int
+    lib.rsign_dbg_commutator_check.argtypes = [vp, vp, i64, i64, i32, vp, vp]
+    lib.rsign_dbg_commutator_check.restype = ctypes.c_int
     lib.rsign_dbg_set_tc_cluster.argtypes = [i32]
     lib.rsign_dbg_set_tc_cluster.restype = i32
     lib.rsign_dbg_tridiag_ritz.argtypes = [dp, dp, i32, i32, dp, dp]
@@ -530,6 +534,31 @@ def dbg_fp64e_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def dbg_gemv_df(M, x, stream=None):
+    """y = M x (device FP64) in the double-float arithmetic of the refinement check."""
+    torch = _torch()
+    lib = load()
+    dp = int(M.shape[0])
+    y = torch.empty(dp, dtype=torch.float64, device=M.device)
+    st = Status(lib.rsign_dbg_gemv_df(M.data_ptr(), x.data_ptr(), dp, y.data_ptr(), _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return y
+
+
+def dbg_commutator_check(A, R, d=None, iters=12, stream=None):
+    """The refinement's matrix-free check on device A, R: returns (||G||_2 est,
+    ||R^2 - I||_2 est, (a11, a12, a22) of the 2 x 2 Rayleigh-Ritz projection)."""
+    lib = load()
+    dp = int(A.shape[0])
+    out = (ctypes.c_double * 5)()
+    st = Status(lib.rsign_dbg_commutator_check(A.data_ptr(), R.data_ptr(), dp, int(d or dp), int(iters), out,
+                                               _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return out[0], out[1], (out[2], out[3], out[4])
 
 
 def build(force=False, verbose=False):

@@ -260,10 +260,51 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(dou
   return __double2bfloat16(x);
 }
 
+// eight FP16/BF16 values (one 16-byte load) to FP32
+template <typename T>
+__device__ __forceinline__ void load8_lp(const T* src, float* v) {
+  const uint4 u = *reinterpret_cast<const uint4*>(src);
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    uint16_t lo = (uint16_t)(w[h] & 0xFFFFu), hi = (uint16_t)(w[h] >> 16);
+    v[2 * h] = to_f32<T>(*reinterpret_cast<T*>(&lo));
+    v[2 * h + 1] = to_f32<T>(*reinterpret_cast<T*>(&hi));
+  }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// sum_j r_j^2 over the first ncols (a multiple of 8) entries of a row of an
+// FP16/BF16 operand (hi, plus lo at r + plane when split), by one warp: FP32
+// sums of eight squares added in FP64, then the warp sum.  Every lane gets
+// the result.  Zero entries beyond the logical order leave it unchanged, so
+// any padded ncols gives the same bits.
+template <typename T>
+__device__ __forceinline__ double row_sumsq_warp(const T* r, size_t plane, int split, int ncols, int lane) {
+  double acc = 0.0;
+  for (int j0 = 8 * lane; j0 < ncols; j0 += 256) {
+    float h[8], l[8];
+    load8_lp<T>(r + j0, h);
+    if (split) {
+      load8_lp<T>(r + plane + j0, l);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) l[q] = 0.0f;
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float v = h[q] + l[q];
+      s = fmaf(v, v, s);
+    }
+    acc += (double)s;
+  }
+  return warp_sum(acc);
 }
 
 }  // namespace rsign

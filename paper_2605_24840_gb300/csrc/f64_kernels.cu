@@ -316,6 +316,24 @@ __global__ void split_to_f64_kernel(const T* __restrict__ src, size_t n, double*
     dst[i] = (double)to_f32<T>(src[i]) + (double)to_f32<T>(src[n + i]);
 }
 
+// out[i] = sum_j x_ij^2 of the FP16/BF16 operand x = hi (+ lo) of a Newton-
+// Schulz product: the exact diagonal of X^2 (row_sumsq_warp).  The tensor
+// cores accumulate the diagonal's K positive terms with a downward bias that
+// grows with K (about 4e-9 per term measured on this GPU: 7e-5 at K = 16384),
+// which moves the fixed point of the iteration to |x| = 1 + bias/2 and the
+// trace of the iterate by (d - 2k) bias/2 (0.6 at d = 16384).  Skipped (no
+// writes) once *skip is set.
+template <typename T>
+__global__ void row_sumsq_kernel(const T* __restrict__ x, size_t plane, int split, int dp, int d,
+                                 float* __restrict__ out, const int* __restrict__ skip) {
+  if (skip != nullptr && *skip) return;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= dp) return;
+  const double acc = row < d ? row_sumsq_warp<T>(x + (size_t)row * dp, plane, split, dp, lane) : 0.0;
+  if (lane == 0) out[row] = (float)acc;
+}
+
 template <typename T>
 __global__ void to_f64_kernel(const T* __restrict__ src, size_t n, double* __restrict__ dst) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -324,26 +342,43 @@ __global__ void to_f64_kernel(const T* __restrict__ src, size_t n, double* __res
   }
 }
 
-// y = A x, one warp per row.
-// 16-byte loads, four in flight per lane (dp is a multiple of 256)
+// y = A x (FP64)
 __global__ void gemv_kernel(const double* __restrict__ A, int dp, const double* __restrict__ x,
                             double* __restrict__ y) {
+  // one warp per row; eight 16-byte loads in flight per lane (a GEMV is
+  // latency-bound per warp), the matrix streamed past L1 (__ldcs), x cached
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= dp) return;
   const double2* a = reinterpret_cast<const double2*>(A + (size_t)row * dp);
   const double2* xv = reinterpret_cast<const double2*>(x);
   double s0 = 0.0, s1 = 0.0;
-  const int n2 = dp >> 1;
-  for (int j = lane; j < n2; j += 128) {
+  const int n2 = dp >> 1;  // a multiple of 128: full chunks of 256, then at most one of 128
+  int j = lane;
+  for (; j + 224 < n2; j += 256) {
+    double2 av[8], bv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      av[u] = __ldcs(a + j + 32 * u);
+      bv[u] = xv[j + 32 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      s0 = fma(av[u].x, bv[u].x, s0);
+      s1 = fma(av[u].y, bv[u].y, s1);
+    }
+  }
+  if (j < n2) {
+    double2 av[4], bv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int q = j + 32 * u;
-      if (q < n2) {
-        const double2 av = a[q], bv = xv[q];
-        s0 = fma(av.x, bv.x, s0);
-        s1 = fma(av.y, bv.y, s1);
-      }
+      av[u] = __ldcs(a + j + 32 * u);
+      bv[u] = xv[j + 32 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      s0 = fma(av[u].x, bv[u].x, s0);
+      s1 = fma(av[u].y, bv[u].y, s1);
     }
   }
   double s = warp_sum(s0 + s1);
@@ -394,11 +429,6 @@ __global__ void symmetrize_scale_kernel(const double* __restrict__ S, int dp, do
     const size_t e = (size_t)(bi * 32 + r) * dp + bj * 32 + tx;
     D[e] = 0.5 * scale * (S[e] + t[tx][r]);
   }
-}
-
-__global__ void init_vec_kernel(double* x, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] = 1.0 + (i % 7) * 0.125;
 }
 
 __global__ void alpha_from_rho_kernel(const double* nrm, double c, double* scal) {
@@ -474,6 +504,16 @@ cudaError_t ingest(const double* H, int d, int dp, double s, double* A, double* 
 cudaError_t inf_norm_finish(const double* rowpart, int dp, double* rowsum, double* scal, cudaStream_t st) {
   rowsum_kernel<<<(dp + 255) / 256, 256, 0, st>>>(rowpart, dp, rowsum);
   max_kernel<<<1, 1024, 0, st>>>(rowsum, dp, scal);
+  return cudaGetLastError();
+}
+
+cudaError_t row_sumsq(const void* x, int fmt, int split, int dp, int d, float* out, const int* skip,
+                      cudaStream_t st) {
+  const size_t plane = (size_t)dp * dp;
+  const int blocks = (dp + 7) / 8;
+  if (fmt == 0) row_sumsq_kernel<__half><<<blocks, 256, 0, st>>>((const __half*)x, plane, split, dp, d, out, skip);
+  else row_sumsq_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)x, plane, split, dp, d, out,
+                                                                  skip);
   return cudaGetLastError();
 }
 
@@ -560,15 +600,8 @@ cudaError_t symmetrize_scale(const double* src, int dp, double scale, double* ds
   return cudaGetLastError();
 }
 
-cudaError_t power_alpha(const double* A, int dp, double* x, double* y, int iters, double c, double* scal,
-                        cudaStream_t st) {
-  init_vec_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y, dp);
-  normalize_kernel<<<1, 1024, 0, st>>>(y, dp, x, scal + 4);
-  for (int it = 0; it < iters; ++it) {
-    gemv_kernel<<<(dp + 7) / 8, 256, 0, st>>>(A, dp, x, y);
-    normalize_kernel<<<1, 1024, 0, st>>>(y, dp, x, scal + 4);  // scal[4] = ||A x_prev||
-  }
-  alpha_from_rho_kernel<<<1, 32, 0, st>>>(scal + 4, c, scal);
+cudaError_t alpha_from_rho(const double* nrm, double c, double* scal, cudaStream_t st) {
+  alpha_from_rho_kernel<<<1, 32, 0, st>>>(nrm, c, scal);
   return cudaGetLastError();
 }
 

@@ -117,6 +117,9 @@ struct TcGemmArgs {
   // E = I - ns_c2 X^2 (ns_c2 = a^2), TC_EPI_NS_UPDATE stores ns_c1 (X + 1/2 X E)
   // (ns_c1 = a); 0 means 1 (the plain step)
   float ns_c1, ns_c2;
+  // TC_EPI_NS_SYRK: exact squared row norms of the operand X (nullable): the
+  // diagonal of X^2 is taken from here instead of the tensor-core sum
+  const float* ns_diag;
 };
 
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
@@ -199,6 +202,11 @@ cudaError_t to_f64(const void* src, int src_fmt, size_t n, double* dst, cudaStre
 cudaError_t scale_convert_split(const double* src, size_t n, const double* scale_dev, void* dst,
                                 int fmt, cudaStream_t st);
 cudaError_t split_to_f64(const void* src, int fmt, size_t n, double* dst, cudaStream_t st);
+// out[i] = sum_j x_ij^2 (FP32 result, FP64 accumulation) of the dp x dp
+// FP16/BF16 operand x (hi + lo planes when split), rows >= d get 0; no work
+// once *skip (nullable) is set.
+cudaError_t row_sumsq(const void* x, int fmt, int split, int dp, int d, float* out, const int* skip,
+                      cudaStream_t st);
 // Deterministic sum of n partials -> out[0]; out[1] = sqrt(out[0]) when sqrt_out.
 cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_t st);
 // y = A x for dp x dp FP64 A (row-major), x,y length dp.
@@ -226,14 +234,6 @@ cudaError_t symmetrize_scale(const double* src, int dp, double scale, double* ds
 cudaError_t trace_f64(const double* X, int dp, int d, double* out, cudaStream_t st);
 // Power-iteration helpers: x <- y / ||y||_2, norm stored in *nrm.
 cudaError_t normalize(double* y, int n, double* x, double* nrm, cudaStream_t st);
-// Scaling by power steps (Sec. 4.3: alpha close to 1/||H - sI||_2 enlarges the
-// scaled margin gamma): rho_est = ||A v_m|| after `iters` steps from a fixed
-// start vector (a lower bound of rho(A) converging from below); then
-// scal[1] = alpha = 1 / (c rho_est), scal[3] = rho_est.  alpha rho < sqrt(3)
-// keeps every sign (f(t) = t(3 - t^2)/2 > 0 on (0, sqrt(3))) as long as
-// rho_est > rho / (c sqrt(3)); the trace certificate checks it.
-cudaError_t power_alpha(const double* A, int dp, double* x, double* y, int iters, double c, double* scal,
-                        cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Automatic shift (lanczos.cu).
@@ -358,14 +358,34 @@ cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockm
 // v, w: dp-float work vectors.
 cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
                               cudaStream_t st);
-// Matrix-free estimate of ||G||_2, G = 1/2 R C, C = R A - A R (FP64 A, R):
-// power steps on the antisymmetric C, v -> R (A v) - A (R v), four FP64 GEMVs
-// per step, ||G||_2 = ||C||_2 / 2 for the orthogonal R; the commutator action
-// is formed from FP64 matrix-vector products, accurate to ~1e-16 relative per
-// term, so no FP64-grade matrix product is needed.
-// work: 6 dp doubles; result -> *out (device double).
-cudaError_t commutator_gain_norm(const double* A, const double* R, int dp, int d, int iters, double* work,
+// hi = fl32(x), lo = fl32(x - hi) (lo nullable): x = hi + lo to 2^-48
+// relative, the operand form of the double-float GEMVs below.
+cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, cudaStream_t st);
+// y = M x in double-float arithmetic (M, x as hi + lo FP32 pairs; dp a
+// multiple of 256), y in FP64.
+cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y, int dp,
+                    cudaStream_t st);
+// Matrix-free estimate of ||G||_2, G = 1/2 R C, C = R A - A R: power steps on
+// the antisymmetric C, v -> R (A v) - A (R v), and in the same passes power
+// steps on N = R^2 - I.  The matrix-vector products run on the FP32 pipe in
+// double-float arithmetic (matrices and vectors as hi + lo FP32 pairs, exact
+// product splitting and TwoSum accumulation per lane, lanes combined in
+// FP64): ~2^-46 relative per term, FP64-class, at HBM speed (GB300's FP64
+// pipe would bound FP64 GEMVs at ~0.6 T FMA/s).
+// A_hi/A_lo: split of A (split_f32); R_hi/R_lo: dp^2-float buffers that
+// receive the split of R.  work: 12 dp doubles; fwork: 12 dp floats.
+// out[0] = ||G||_2 estimate, out[1] = ||N||_2 estimate, out[2..4] = the 2 x 2
+// Rayleigh-Ritz projection of A on the last plane of the commutator steps.
+cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const double* R, float* R_hi,
+                                 float* R_lo, int dp, int d, int iters, double* work, float* fwork,
                                  double* out, cudaStream_t st);
+// Scaling by power steps (Sec. 4.3: alpha close to 1/||H - sI||_2 enlarges the
+// scaled margin gamma): with rho_est = nrm[0] from power steps (a lower bound
+// of rho(A) converging from below), scal[3] = rho_est and scal[1] = alpha =
+// 1 / (c rho_est).  alpha rho < sqrt(3) keeps every sign (f(t) = t(3 - t^2)/2
+// > 0 on (0, sqrt(3))) as long as rho_est > rho / (c sqrt(3)); the trace
+// certificate checks it.
+cudaError_t alpha_from_rho(const double* nrm, double c, double* scal, cudaStream_t st);
 // R += 1/2 P / sigma (P FP32 symmetric product R_lp Et_lp).
 cudaError_t polish_update(double* R, const float* P, int dp, const float* sigma, cudaStream_t st);
 

@@ -8,6 +8,7 @@
 // and therefore accumulate exactly in the FP32 TMEM accumulator of the
 // tcgen05 GEMM.  The only rounding is the FP64 sum over levels in the
 // epilogue and the truncation after kSlices digits (35 bits).
+#include <type_traits>
 #include "common.cuh"
 #include "kernels.h"
 
@@ -274,7 +275,8 @@ __global__ void polish_update_kernel(double* __restrict__ R, const float* __rest
 __global__ void gemv_f32_kernel(const float* __restrict__ M, int dp, const float* __restrict__ v,
                                 float* __restrict__ w, int init) {
   // FP32: a norm estimate needs no more, and the FP64 pipe is slow here.
-  // 16-byte loads, four in flight per lane (dp is a multiple of 256).
+  // One warp per row, eight 16-byte loads in flight per lane, the matrix
+  // streamed past L1 (dp is a multiple of 256).
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= dp) return;
@@ -282,27 +284,34 @@ __global__ void gemv_f32_kernel(const float* __restrict__ M, int dp, const float
   const float4* vv = reinterpret_cast<const float4*>(v);
   const int n4 = dp >> 2;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  for (int j = lane; j < n4; j += 128) {
+  auto chunk = [&](int j, auto n_c) {
+    constexpr int NC = decltype(n_c)::value;
+    float4 a[NC], b[NC];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NC; ++u) {
       const int q = j + 32 * u;
-      if (q < n4) {
-        const float4 a = m[q];
-        float4 b;
-        if (init) {
-          const int e = 4 * q;
-          b = make_float4(1.0f + (float)(e % 7) * 0.125f, 1.0f + (float)((e + 1) % 7) * 0.125f,
-                          1.0f + (float)((e + 2) % 7) * 0.125f, 1.0f + (float)((e + 3) % 7) * 0.125f);
-        } else {
-          b = vv[q];
-        }
-        s0 = fmaf(a.x, b.x, s0);
-        s1 = fmaf(a.y, b.y, s1);
-        s2 = fmaf(a.z, b.z, s2);
-        s3 = fmaf(a.w, b.w, s3);
+      a[u] = __ldcs(m + q);
+      if (init) {
+        const int e = 4 * q;
+        b[u] = make_float4(1.0f + (float)(e % 7) * 0.125f, 1.0f + (float)((e + 1) % 7) * 0.125f,
+                           1.0f + (float)((e + 2) % 7) * 0.125f, 1.0f + (float)((e + 3) % 7) * 0.125f);
+      } else {
+        b[u] = vv[q];
       }
     }
-  }
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      s0 = fmaf(a[u].x, b[u].x, s0);
+      s1 = fmaf(a[u].y, b[u].y, s1);
+      s2 = fmaf(a[u].z, b[u].z, s2);
+      s3 = fmaf(a[u].w, b[u].w, s3);
+    }
+  };
+  // n4 is a multiple of 64: full chunks of 256, then at most one of 128 and one of 64
+  int j = lane;
+  for (; j + 224 < n4; j += 256) chunk(j, std::integral_constant<int, 8>{});
+  if (j + 96 < n4) { chunk(j, std::integral_constant<int, 4>{}); j += 128; }
+  if (j + 32 < n4) { chunk(j, std::integral_constant<int, 2>{}); j += 64; }
   float s = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -345,56 +354,160 @@ __global__ void power_normalize_kernel(const float* __restrict__ w, int n, float
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
 }
 
-// y = A x (FP64), one warp per row, two matrices at once: y1 = M1 x1, y2 =
-// M2 x2, and optionally a second vector against either matrix (y1b = M1 x1b,
-// y2b = M2 x2b; nullptr: none), read from the same pass over the rows
-__global__ void gemv2_f64_kernel(const double* __restrict__ M1, const double* __restrict__ x1,
-                                 double* __restrict__ y1, const double* __restrict__ x1b,
-                                 double* __restrict__ y1b, const double* __restrict__ M2,
-                                 const double* __restrict__ x2, double* __restrict__ y2,
-                                 const double* __restrict__ x2b, double* __restrict__ y2b, int dp) {
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= 2 * dp) return;
-  const bool second = row >= dp;
-  const int r = second ? row - dp : row;
-  const double2* m = reinterpret_cast<const double2*>((second ? M2 : M1) + (size_t)r * dp);
-  const double2* x = reinterpret_cast<const double2*>(second ? x2 : x1);
-  const double2* xb = reinterpret_cast<const double2*>(second ? x2b : x1b);
-  const int n2 = dp >> 1;
-  double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
-  if (xb == nullptr) {
-    for (int j = lane; j < n2; j += 128) {
+// ---- double-float GEMVs (FP64-class products on the FP32 pipe)
+// One (matrix, vectors) job: y = M x and optionally y_b = M x_b from the same
+// pass over M's rows; M, x, x_b as hi + lo FP32 pairs; y in FP64 and, when
+// yhi is given, also split.
+struct GemvDfJob {
+  const float* mhi;
+  const float* mlo;
+  const float* xhi;
+  const float* xlo;
+  const float* xbhi;  // nullable: no second vector
+  const float* xblo;
+  double* y;
+  float* yhi;  // nullable: no split output
+  float* ylo;
+  double* yb;
+  float* ybhi;
+  float* yblo;
+};
+struct GemvDfArgs {
+  GemvDfJob job[2];
+  int n_jobs;
+  int dp;
+};
+
+// s + c += (ah + al)(xh + xl): the product ah xh split exactly into p + e by
+// an FMA, the cross terms ah xl + al xh (and e) added to the compensation c,
+// p added to s by TwoSum with its rounding error into c (al xl, below 2^-48
+// of the product, is dropped).  The _rn intrinsics keep the compiler from
+// contracting the TwoSum into FMAs.
+__device__ __forceinline__ void df_acc(float& s, float& c, float ah, float al, float xh, float xl) {
+  const float p = __fmul_rn(ah, xh);
+  const float e = fmaf(ah, xh, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c += err + fmaf(ah, xl, fmaf(al, xh, e));
+}
+
+template <bool TWO>
+__device__ __forceinline__ void gemv_df_row(const GemvDfJob& J, int r, int dp, int lane) {
+  const float4* mh = reinterpret_cast<const float4*>(J.mhi + (size_t)r * dp);
+  const float4* ml = reinterpret_cast<const float4*>(J.mlo + (size_t)r * dp);
+  const float4* xh = reinterpret_cast<const float4*>(J.xhi);
+  const float4* xl = reinterpret_cast<const float4*>(J.xlo);
+  const float4* bh = reinterpret_cast<const float4*>(J.xbhi);
+  const float4* bl = reinterpret_cast<const float4*>(J.xblo);
+  // four independent (s, c) pairs per vector, one per float4 component
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+  float sb[4] = {0.f, 0.f, 0.f, 0.f}, cb[4] = {0.f, 0.f, 0.f, 0.f};
+  auto chunk = [&](int q0, auto n_c) {
+    constexpr int U = decltype(n_c)::value;
+    float4 ah[U], al[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = j + 32 * u;
-        if (q < n2) {
-          const double2 a = m[q], b = x[q];
-          s0 = fma(a.x, b.x, s0);
-          s1 = fma(a.y, b.y, s1);
-        }
+    for (int u = 0; u < U; ++u) {
+      ah[u] = __ldcs(mh + q0 + 32 * u);
+      al[u] = __ldcs(ml + q0 + 32 * u);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + 32 * u;
+      const float4 vh = xh[q], vl = xl[q];
+      df_acc(s[0], c[0], ah[u].x, al[u].x, vh.x, vl.x);
+      df_acc(s[1], c[1], ah[u].y, al[u].y, vh.y, vl.y);
+      df_acc(s[2], c[2], ah[u].z, al[u].z, vh.z, vl.z);
+      df_acc(s[3], c[3], ah[u].w, al[u].w, vh.w, vl.w);
+      if (TWO) {
+        const float4 wh = bh[q], wl = bl[q];
+        df_acc(sb[0], cb[0], ah[u].x, al[u].x, wh.x, wl.x);
+        df_acc(sb[1], cb[1], ah[u].y, al[u].y, wh.y, wl.y);
+        df_acc(sb[2], cb[2], ah[u].z, al[u].z, wh.z, wl.z);
+        df_acc(sb[3], cb[3], ah[u].w, al[u].w, wh.w, wl.w);
       }
     }
-  } else {
-    for (int j = lane; j < n2; j += 128) {
+  };
+  // n4 = dp / 4 is a multiple of 64: chunks of 4 float4 per lane (128 per
+  // warp), then at most one chunk of 2
+  const int n4 = dp >> 2;
+  int q0 = lane;
+  for (; q0 + 96 < n4; q0 += 128) chunk(q0, std::integral_constant<int, 4>{});
+  if (q0 + 32 < n4) chunk(q0, std::integral_constant<int, 2>{});
+  double t = 0.0, tb = 0.0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = j + 32 * u;
-        if (q < n2) {
-          const double2 a = m[q], b = x[q], c = xb[q];
-          s0 = fma(a.x, b.x, s0);
-          s1 = fma(a.y, b.y, s1);
-          t0 = fma(a.x, c.x, t0);
-          t1 = fma(a.y, c.y, t1);
-        }
+  for (int q = 0; q < 4; ++q) {
+    t += (double)s[q] + (double)c[q];
+    if (TWO) tb += (double)sb[q] + (double)cb[q];
+  }
+  t = warp_sum(t);
+  if (TWO) tb = warp_sum(tb);
+  if (lane == 0) {
+    J.y[r] = t;
+    if (J.yhi != nullptr) {
+      const float h = __double2float_rn(t);
+      J.yhi[r] = h;
+      J.ylo[r] = __double2float_rn(t - (double)h);
+    }
+    if (TWO) {
+      J.yb[r] = tb;
+      if (J.ybhi != nullptr) {
+        const float h = __double2float_rn(tb);
+        J.ybhi[r] = h;
+        J.yblo[r] = __double2float_rn(tb - (double)h);
       }
     }
   }
-  const double s = warp_sum(s0 + s1);
-  const double t = warp_sum(t0 + t1);
-  if (lane == 0) {
-    (second ? y2 : y1)[r] = s;
-    if (xb != nullptr) (second ? y2b : y1b)[r] = t;
+}
+
+// one warp per row; rows [0, dp) belong to job 0, [dp, 2 dp) to job 1
+__global__ void gemv_df_kernel(const GemvDfArgs a) {
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= a.n_jobs * a.dp) return;
+  const int jb = gw >= a.dp ? 1 : 0;
+  const int r = gw - jb * a.dp;
+  const GemvDfJob& J = a.job[jb];
+  if (J.xbhi != nullptr) gemv_df_row<true>(J, r, a.dp, lane);
+  else gemv_df_row<false>(J, r, a.dp, lane);
+}
+
+__global__ void split_f32_kernel(const double* __restrict__ src, size_t n, float* __restrict__ hi,
+                                 float* __restrict__ lo) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double x = src[i];
+    const float h = __double2float_rn(x);
+    hi[i] = h;
+    if (lo != nullptr) lo[i] = __double2float_rn(x - (double)h);
+  }
+}
+
+// v = w / ||w|| in FP64 and as hi + lo FP32 pairs; *out = ||w|| (one block)
+__global__ void normalize_split_kernel(const double* __restrict__ w, int n, double* __restrict__ v,
+                                       float* __restrict__ vhi, float* __restrict__ vlo, double* out) {
+  __shared__ double sh[32];
+  __shared__ double inv_sh;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(w[i], w[i], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += sh[q];
+    const double nw = sqrt(tot);
+    inv_sh = nw > 0.0 ? 1.0 / nw : 0.0;
+    *out = nw;
+  }
+  __syncthreads();
+  const double inv = inv_sh;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = w[i] * inv;
+    v[i] = x;
+    const float h = __double2float_rn(x);
+    vhi[i] = h;
+    vlo[i] = __double2float_rn(x - (double)h);
   }
 }
 
@@ -659,49 +772,85 @@ cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int it
   return cudaGetLastError();
 }
 
-cudaError_t commutator_gain_norm(const double* A, const double* R, int dp, int d, int iters, double* work,
+cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y, int dp,
+                    cudaStream_t st) {
+  GemvDfArgs a{};
+  a.n_jobs = 1;
+  a.dp = dp;
+  a.job[0] = GemvDfJob{M_hi, M_lo, x_hi, x_lo, nullptr, nullptr, y, nullptr, nullptr, nullptr, nullptr, nullptr};
+  gemv_df_kernel<<<(dp + 7) / 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, cudaStream_t st) {
+  split_f32_kernel<<<grid_for(n), 256, 0, st>>>(src, n, hi, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const double* R, float* R_hi,
+                                 float* R_lo, int dp, int d, int iters, double* work, float* fwork,
                                  double* out, cudaStream_t st) {
-  double* vb[2] = {work, work + 10 * dp};  // unit vectors of the commutator steps (alternating)
-  double* t1 = work + dp;     // A v
-  double* t2 = work + 2 * dp; // R v
-  double* y1 = work + 3 * dp; // R A v
-  double* y2 = work + 4 * dp; // A R v
-  double* w = work + 5 * dp;  // C v
-  double* z = work + 6 * dp;  // current unit vector of the involution-residual steps
-  double* t3 = work + 7 * dp; // R z
-  double* y3 = work + 8 * dp; // R R z
-  double* w3 = work + 9 * dp; // (R^2 - I) z
-  double* t4 = work + 11 * dp;  // A v_last
-  double* t5 = work + 12 * dp;  // R v_last (unused)
   if (iters < 1) return cudaErrorInvalidValue;
-  const int blocks2 = (2 * dp + 7) / 8;
+  // FP64 vectors
+  double* vb[2] = {work, work + dp};  // unit vectors of the commutator steps (alternating)
+  double* t1 = work + 2 * dp;         // A v
+  double* t2 = work + 3 * dp;         // R v
+  double* y1 = work + 4 * dp;         // R A v
+  double* y2 = work + 5 * dp;         // A R v
+  double* w = work + 6 * dp;          // C v
+  double* z = work + 7 * dp;          // unit vector of the involution-residual steps
+  double* t3 = work + 8 * dp;         // R z
+  double* y3 = work + 9 * dp;         // R R z
+  double* w3 = work + 10 * dp;        // (R^2 - I) z
+  double* t4 = work + 11 * dp;        // A v_last
+  // hi/lo FP32 copies of the vectors that enter a product
+  float* vbh[2] = {fwork, fwork + 2 * dp};
+  float* vbl[2] = {fwork + dp, fwork + 3 * dp};
+  float *zh = fwork + 4 * dp, *zl = fwork + 5 * dp;
+  float *t1h = fwork + 6 * dp, *t1l = fwork + 7 * dp;
+  float *t2h = fwork + 8 * dp, *t2l = fwork + 9 * dp;
+  float *t3h = fwork + 10 * dp, *t3l = fwork + 11 * dp;
+  const size_t dd = (size_t)dp * dp;
+  split_f32_kernel<<<grid_for(dd), 256, 0, st>>>(R, dd, R_hi, R_lo);
   start_vec_f64_kernel<<<(dp + 255) / 256, 256, 0, st>>>(w, d, dp);
-  cudaError_t e = normalize(w, dp, vb[0], out, st);
-  if (e != cudaSuccess) return e;
-  if ((e = normalize(w, dp, z, out + 1, st)) != cudaSuccess) return e;
+  normalize_split_kernel<<<1, 1024, 0, st>>>(w, dp, vb[0], vbh[0], vbl[0], out);
+  normalize_split_kernel<<<1, 1024, 0, st>>>(w, dp, z, zh, zl, out + 1);
+  const int blocks2 = (2 * dp + 7) / 8;
   // ||R C v|| = ||C v|| for the (orthogonal to working accuracy) R, so the
   // steps run on the antisymmetric C itself: v <- C v / ||C v|| turns within
   // the dominant invariant plane (eigenvalues +-i mu) and ||C v|| -> mu =
   // ||C||_2, as fast as power steps on C^2.  Power steps on the symmetric
-  // N = R^2 - I ride along in the same passes over A and R (R applied to two
-  // vectors per pass).  Four GEMVs a step
+  // N = R^2 - I ride along in the same passes over A and R.
   for (int it = 0; it < iters; ++it) {
-    const double* v = vb[it & 1];
-    double* vn = vb[(it + 1) & 1];
-    gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(A, v, t1, nullptr, nullptr, R, v, t2, z, t3, dp);  // A v; R v, R z
-    gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(R, t1, y1, t3, y3, A, t2, y2, nullptr, nullptr, dp);  // R A v, R R z; A R v
+    const int cur = it & 1, nxt = (it + 1) & 1;
+    GemvDfArgs p1{};
+    p1.n_jobs = 2;
+    p1.dp = dp;
+    p1.job[0] = GemvDfJob{A_hi, A_lo, vbh[cur], vbl[cur], nullptr, nullptr, t1, t1h, t1l, nullptr, nullptr, nullptr};
+    p1.job[1] = GemvDfJob{R_hi, R_lo, vbh[cur], vbl[cur], zh, zl, t2, t2h, t2l, t3, t3h, t3l};
+    gemv_df_kernel<<<blocks2, 256, 0, st>>>(p1);  // A v; R v, R z
+    GemvDfArgs p2{};
+    p2.n_jobs = 2;
+    p2.dp = dp;
+    p2.job[0] = GemvDfJob{R_hi, R_lo, t1h, t1l, t3h, t3l, y1, nullptr, nullptr, y3, nullptr, nullptr};
+    p2.job[1] = GemvDfJob{A_hi, A_lo, t2h, t2l, nullptr, nullptr, y2, nullptr, nullptr, nullptr, nullptr, nullptr};
+    gemv_df_kernel<<<blocks2, 256, 0, st>>>(p2);  // R A v, R R z; A R v
     diff2_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y1, y2, w, y3, z, w3, dp);  // C v, N z
-    if ((e = normalize(w, dp, vn, out, st)) != cudaSuccess) return e;       // ||C v|| (v unit)
-    if ((e = normalize(w3, dp, z, out + 1, st)) != cudaSuccess) return e;   // ||N z|| (z unit)
+    normalize_split_kernel<<<1, 1024, 0, st>>>(w, dp, vb[nxt], vbh[nxt], vbl[nxt], out);  // ||C v||
+    normalize_split_kernel<<<1, 1024, 0, st>>>(w3, dp, z, zh, zl, out + 1);               // ||N z||
   }
   // Rayleigh-Ritz on the last plane {v_prev, v_last = C v_prev / ||C v_prev||}
   // (orthonormal: v^T C v = 0 for the antisymmetric C): the entries of the
   // 2 x 2 projection of A, out[2..4] = v_prev.A v_prev, v_last.A v_prev,
   // v_last.A v_last
-  const double* v_prev = vb[(iters - 1) & 1];
-  const double* v_last = vb[iters & 1];
-  gemv2_f64_kernel<<<blocks2, 256, 0, st>>>(A, v_last, t4, nullptr, nullptr, R, v_last, t5, nullptr, nullptr, dp);
-  dot3_kernel<<<1, 1024, 0, st>>>(v_prev, t1, v_last, t1, v_last, t4, dp, out + 2);
+  const int last = iters & 1, prev = (iters - 1) & 1;
+  GemvDfArgs p3{};
+  p3.n_jobs = 1;
+  p3.dp = dp;
+  p3.job[0] = GemvDfJob{A_hi, A_lo, vbh[last], vbl[last], nullptr, nullptr, t4, nullptr, nullptr, nullptr, nullptr,
+                        nullptr};
+  gemv_df_kernel<<<(dp + 7) / 8, 256, 0, st>>>(p3);
+  dot3_kernel<<<1, 1024, 0, st>>>(vb[prev], t1, vb[last], t1, vb[last], t4, dp, out + 2);
   // out[0] = ||C v_prev|| = 2 ||G v_prev|| (G = 1/2 R C): halve it
   scale_scalar_kernel<<<1, 1, 0, st>>>(out, 0.5);
   return cudaGetLastError();

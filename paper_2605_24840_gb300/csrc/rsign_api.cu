@@ -390,16 +390,25 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   float *pv = nullptr, *pw = nullptr;
   RS_TRY(mem.alloc((void**)&pv, (size_t)dp * 4));
   RS_TRY(mem.alloc((void**)&pw, (size_t)dp * 4));
-  constexpr int kPowerIters = 24;
+  constexpr int kPowerIters = 16;
   constexpr int kCheckIters = 12;
   double* cwork = nullptr;
-  RS_TRY(mem.alloc((void**)&cwork, (size_t)13 * dp * 8));
+  float *cfwork = nullptr, *A_hi = nullptr, *A_lo = nullptr, *R_hi = nullptr, *R_lo = nullptr;
+  RS_TRY(mem.alloc((void**)&cwork, (size_t)12 * dp * 8));
+  RS_TRY(mem.alloc((void**)&cfwork, (size_t)12 * dp * 4));
+  RS_TRY(mem.alloc((void**)&A_hi, dd * 4));
+  RS_TRY(mem.alloc((void**)&A_lo, dd * 4));
+  RS_TRY(mem.alloc((void**)&R_hi, dd * 4));
+  RS_TRY(mem.alloc((void**)&R_lo, dd * 4));
+  RS_TRY(c.ok(split_f32(in.A64, dd, A_hi, A_lo, st)) ? cudaSuccess : c.err);  // operand of the checks
   double kappa = NAN;
   for (int sw = 0; sw <= in.max_sweeps; ++sw) {
     if (sw >= 1) {
       // a-posteriori check of the current R (matrix free, FP64 GEMVs):
       // err ~ 1.5 kappa alpha ||G||_2 with kappa the gain of the last tangent solve
-      if (!c.ok(commutator_gain_norm(in.A64, in.R64, dp, d, kCheckIters, cwork, red + 9, st))) return c.err;
+      if (!c.ok(commutator_gain_norm(A_hi, A_lo, in.R64, R_hi, R_lo, dp, d, kCheckIters, cwork, cfwork, red + 9,
+                                     st)))
+        return c.err;
       c.launches += 5 * kCheckIters + 6;
       RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
       RS_TRY(cudaStreamSynchronize(st));
@@ -619,13 +628,20 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   if (!c.ok(ingest(Hd, d, dp, s, A64, rowpart, &ctl->flags, st))) return fail_cuda();
   if (!c.ok(inf_norm_finish(rowpart, dp, rowsum, ctl->scal, st))) return fail_cuda();
   if (opt.alpha_mode == RSIGN_ALPHA_POWER) {
-    // alpha = 1/(1.02 rho_est) from power steps on A (overwrites the Gershgorin value)
-    double *px = nullptr, *py = nullptr;
-    if (mem.alloc((void**)&px, (size_t)dp * 8) != cudaSuccess ||
-        mem.alloc((void**)&py, (size_t)dp * 8) != cudaSuccess)
+    // alpha = 1/(1.02 rho_est) from power steps on A (overwrites the Gershgorin
+    // value); an estimate within a few percent is all it needs, so the steps
+    // run on an FP32 copy of A: half the bytes and the FP32 pipe (FP64 FMAs
+    // would bound the GEMV on this GPU)
+    float *a32 = nullptr, *pv = nullptr, *pw = nullptr;
+    if (mem.alloc((void**)&a32, dd * 4) != cudaSuccess || mem.alloc((void**)&pv, (size_t)dp * 4) != cudaSuccess ||
+        mem.alloc((void**)&pw, (size_t)dp * 4) != cudaSuccess)
       return fail_cuda();
-    if (!c.ok(power_alpha(A64, dp, px, py, std::max(1, opt.power_steps), 1.02, ctl->scal, st))) return fail_cuda();
-    c.launches += 2 * std::max(1, opt.power_steps) + 2;
+    const int ps = std::max(1, opt.power_steps);
+    if (!c.ok(split_f32(A64, dd, a32, nullptr, st)) ||
+        !c.ok(spectral_norm_f32(a32, dp, pv, pw, ps, ctl->scal + 4, st)) ||
+        !c.ok(alpha_from_rho(ctl->scal + 4, 1.02, ctl->scal, st)))
+      return fail_cuda();
+    c.launches += 2 * ps + 2;
   }
   if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -737,6 +753,9 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     double* tr_part = nullptr;
     if (mem.alloc((void**)&tr_part, (size_t)nt * 4 * 8) != cudaSuccess) return fail_cuda();
     const double tr_tol = 0.5 + 2.0 * u * std::sqrt((double)d);
+    // exact squared row norms of each iterate: the SYRK's diagonal
+    float* rowsq = nullptr;
+    if (mem.alloc((void**)&rowsq, (size_t)dp * 4) != cudaSuccess) return fail_cuda();
     int m = 0;
     bool stopped = false;
     while (m <= opt.max_steps && !stopped) {
@@ -761,6 +780,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         const double am = mm < (int)coef.size() ? coef[mm] : 1.0;
         sy.ns_c2 = (float)(am * am);
         sy.ns_c1 = (float)am;
+        sy.ns_diag = rowsq;
+        if (!c.ok(row_sumsq(xm, fmt, split ? 1 : 0, dp, d, rowsq, &ctl->done_low, st))) return fail_cuda();
         if (!c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st))) return fail_cuda();
         const bool floors = mm >= m_min;
         if (!c.ok(ns_check(partials, nt * 4, hist_low, mm, 0.0, floors ? floor_lo : -1.0, floors ? floor_hi : -1.0,
@@ -1093,6 +1114,8 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
     }
     const double u = split ? 4.0 * unit_roundoff(fmt) * unit_roundoff(fmt) : unit_roundoff(fmt);
     const int nt = tc_num_tiles(dp, 1);
+    float* rowsq = nullptr;
+    if (mem.alloc((void**)&rowsq, (size_t)dp * 4) != cudaSuccess) return fail();
     int M = max_steps;
     for (int m = 0; m <= max_steps; ++m) {
       void* xm = slot(xs, m);
@@ -1108,7 +1131,9 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
       }
       sy.split = split ? 1 : 0; sy.group_scale[0] = 1.0; sy.scale = 1.0f; sy.out = em; sy.partials = partials;
       sy.status = &ctl->status;
-      if (!c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st)) ||
+      sy.ns_diag = rowsq;
+      if (!c.ok(row_sumsq(xm, fmt, split ? 1 : 0, dp, d, rowsq, nullptr, st)) ||
+          !c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st)) ||
           !c.ok(ns_check(partials, nt * 4, hist, m, 0.0, 2.0 * u * std::sqrt((double)d), 16.0 * u * std::sqrt((double)d),
                          0.5, &ctl->done_low, &ctl->steps_low, st)))
         return fail();
@@ -1478,6 +1503,58 @@ rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, 
                           cudaStreamSynchronize(st) != cudaSuccess))
     res = RSIGN_ERR_CUDA;
   if (res == RSIGN_OK && hs != 0) res = (rsign_status)hs;
+  mem.release();
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  cudaGetLastError();
+  return res;
+}
+
+rsign_status rsign_dbg_gemv_df(const double* M, const double* x, int64_t dp, double* y, void* stream) {
+  if (!M || !x || !y || dp < 256 || dp % 256 || dp > 16384) return RSIGN_ERR_ARG;
+  int sms = 0;
+  rsign_status ds = (rsign_status)check_device(&sms);
+  if (ds != RSIGN_OK) return ds;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf mem;
+  mem.st = st;
+  const size_t dd = (size_t)dp * dp;
+  float *mh = nullptr, *ml = nullptr, *xh = nullptr, *xl = nullptr;
+  rsign_status res = RSIGN_OK;
+  if (mem.alloc((void**)&mh, dd * 4) != cudaSuccess || mem.alloc((void**)&ml, dd * 4) != cudaSuccess ||
+      mem.alloc((void**)&xh, (size_t)dp * 4) != cudaSuccess || mem.alloc((void**)&xl, (size_t)dp * 4) != cudaSuccess ||
+      split_f32(M, dd, mh, ml, st) != cudaSuccess || split_f32(x, (size_t)dp, xh, xl, st) != cudaSuccess ||
+      gemv_df(mh, ml, xh, xl, y, (int)dp, st) != cudaSuccess)
+    res = RSIGN_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  mem.release();
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  cudaGetLastError();
+  return res;
+}
+
+rsign_status rsign_dbg_commutator_check(const double* A, const double* R, int64_t dp, int64_t d, int32_t iters,
+                                        double* out, void* stream) {
+  if (!A || !R || !out || dp < 256 || dp % 256 || dp > 16384 || d < 1 || d > dp || iters < 1 || iters > 1000)
+    return RSIGN_ERR_ARG;
+  int sms = 0;
+  rsign_status ds = (rsign_status)check_device(&sms);
+  if (ds != RSIGN_OK) return ds;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf mem;
+  mem.st = st;
+  const size_t dd = (size_t)dp * dp;
+  float *ah = nullptr, *al = nullptr, *rh = nullptr, *rl = nullptr, *fw = nullptr;
+  double *w = nullptr, *o = nullptr;
+  rsign_status res = RSIGN_OK;
+  if (mem.alloc((void**)&ah, dd * 4) != cudaSuccess || mem.alloc((void**)&al, dd * 4) != cudaSuccess ||
+      mem.alloc((void**)&rh, dd * 4) != cudaSuccess || mem.alloc((void**)&rl, dd * 4) != cudaSuccess ||
+      mem.alloc((void**)&fw, (size_t)12 * dp * 4) != cudaSuccess ||
+      mem.alloc((void**)&w, (size_t)12 * dp * 8) != cudaSuccess || mem.alloc((void**)&o, 8 * 8) != cudaSuccess ||
+      split_f32(A, dd, ah, al, st) != cudaSuccess ||
+      commutator_gain_norm(ah, al, R, rh, rl, (int)dp, (int)d, iters, w, fw, o, st) != cudaSuccess ||
+      cudaMemcpyAsync(out, o, 5 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    res = RSIGN_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
   mem.release();
   if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
   cudaGetLastError();

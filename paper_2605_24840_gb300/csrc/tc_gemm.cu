@@ -299,7 +299,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
       for (int jj = 0; jj < 32; ++jj) {
         const int j = j0 + jj;
         const bool real = row_real && (j < d_real);
-        const float e = real ? ((i == j ? 1.0f : 0.0f) - (c2 == 1.0f ? v[jj] : c2 * v[jj])) : 0.0f;
+        // the diagonal from the exact row norms when given (the tensor-core
+        // sum of its K positive terms is biased low)
+        const float xx = (i == j && a.ns_diag != nullptr) ? a.ns_diag[voff + i] : v[jj];
+        const float e = real ? ((i == j ? 1.0f : 0.0f) - (c2 == 1.0f ? xx : c2 * xx)) : 0.0f;
         v[jj] = e;
         if (real && j >= i) accf = fmaf((j > i ? 2.0f : 1.0f) * e, e, accf);
       }

@@ -113,7 +113,7 @@ def test_autograd_function_matches_backward_and_daleckii_krein():
     assert np.max(np.abs(R.detach().cpu().numpy() - oracle.reflector_from_basis(spec.Q, k))) < 1e-10
 
 
-@pytest.mark.parametrize("policy,tol", [("FP32", 2e-2), ("BF16_POLISH", 2e-1), ("FP64", 1e-8)])
+@pytest.mark.parametrize("policy,tol", [("FP32", 2e-2), ("BF16_POLISH", 3e-1), ("FP64", 1e-8)])
 def test_backward_adjoint_workload_d2048(policy, tol):
     # the adjoint workload: d = 2048 controlled spectrum, k = 8, half-gap 1e-2,
     # checkpoints every 4 iterates; against the oracle's Daleckii-Krein gradient

@@ -112,3 +112,25 @@ def test_allen_cahn_d4096_refine():
     err = spec_norm_sym(R - oracle.reflector_from_basis(V, k))
     assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
     assert err <= 1e-6 and err <= info.err_bound * 1.05, (err, info.as_dict())
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_allen_cahn_polish_against_the_fp64_gpu_path(k):
+    # the Allen-Cahn workload as configured: 64 x 64 grid (d = 4096), low-precision
+    # steps (FP16 for the TF32 reading, BF16) with FP32 accumulation plus two
+    # FP64 polish steps, compared with the FP64 GPU path.  The distance to the
+    # FP64 result is the low-precision stage's floor (measured at most 6e-3
+    # for FP16 and 5e-2 for BF16 with the scaled steps; without them BF16
+    # reaches 0.8 at k = 1, 2: its rounding of H is as large as the gap)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    H, w, V = _problem(64)
+    s = oracle.midpoint(w[k - 1], w[k])
+    m = oracle.margin(s, w[k - 1], w[k])
+    R64, i64, st64 = _run(rs, torch, H, k, s, rs.Policy.FP64, 1e-12, ns_scaling=1, margin=m)
+    assert st64 == rs.Status.OK and spec_norm_sym(R64 - oracle.reflector_from_basis(V, k)) <= 1e-9
+    for policy, floor in (("FP16_POLISH", 3e-2), ("BF16_POLISH", 1e-1)):
+        R, info, st = _run(rs, torch, H, k, s, rs.Policy[policy], 1e-12, ns_scaling=1, margin=m)
+        assert st == rs.Status.OK and info.cert_ok == 1, (policy, st, info.as_dict())
+        assert info.steps_fp64 == 2, info.as_dict()
+        assert spec_norm_sym(R - R64) <= floor, (policy, spec_norm_sym(R - R64))

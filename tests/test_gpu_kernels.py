@@ -146,3 +146,65 @@ def test_fp64e_product_is_fp64_accurate(dp, d_real, sym):
     assert ((out - ref).abs() - bound).max().item() <= 0.0
     if sym:
         assert (out - out.T).abs().max().item() == 0.0
+
+
+@pytest.mark.parametrize("dp,scale_spread", [(256, 0), (768, 2), (1024, 8), (8192, 4)])
+def test_gemv_df_is_fp64_accurate(dp, scale_spread):
+    # double-float GEMV of the refinement check: per term ~2^-46 relative, so
+    # |y - y_exact| <= 2^-44 sum_j |m_ij x_j| (checked against FP64 torch,
+    # whose own error is below 2^-50 sqrt(K) sum |m x| here)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    g = torch.Generator(device="cuda").manual_seed(11 + dp)
+    M = torch.randn((dp, dp), generator=g, device="cuda", dtype=torch.float64)
+    if scale_spread:  # rows and columns over 2^(+-spread): a wide dynamic range
+        e = torch.randint(-scale_spread, scale_spread + 1, (dp,), generator=g, device="cuda").double()
+        M = M * torch.pow(2.0, e)[:, None] * torch.pow(2.0, -e)[None, :]
+    x = torch.randn(dp, generator=g, device="cuda", dtype=torch.float64)
+    y = rs.dbg_gemv_df(M, x)
+    ref = M @ x
+    scale = M.abs() @ x.abs()
+    assert float(((y - ref).abs() - 2.0 ** -44 * scale).max()) <= 0.0
+
+
+@pytest.mark.parametrize("d,dp", [(512, 512), (700, 768), (1000, 1024)])
+def test_commutator_check_matches_fp64_power_steps(d, dp):
+    # the matrix-free check against the same power steps in FP64 (torch), on a
+    # reflector perturbed by 1e-7: ||C v||/2 and ||N z|| to the cancellation's
+    # accuracy (C and N are 1e-7 of the products, so their directions, and the
+    # Rayleigh-Ritz entries taken on them, agree to ~1e-7 relative)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    g = torch.Generator(device="cuda").manual_seed(d)
+    Q, _ = torch.linalg.qr(torch.randn((d, d), generator=g, device="cuda", dtype=torch.float64))
+    lam = torch.cat([-torch.linspace(1.0, 0.05, 8, device="cuda", dtype=torch.float64),
+                     torch.linspace(0.05, 1.0, d - 8, device="cuda", dtype=torch.float64)])
+    A = (Q * lam) @ Q.T
+    R = torch.eye(d, device="cuda", dtype=torch.float64) - 2.0 * Q[:, :8] @ Q[:, :8].T
+    P = torch.randn((d, d), generator=g, device="cuda", dtype=torch.float64)
+    R = R + 1e-7 * (P + P.T)
+    Ap = torch.zeros((dp, dp), device="cuda", dtype=torch.float64)
+    Rp = torch.zeros((dp, dp), device="cuda", dtype=torch.float64)
+    Ap[:d, :d] = A
+    Rp[:d, :d] = R
+    iters = 12
+    g2, rho, (a11, a12, a22) = rs.dbg_commutator_check(Ap, Rp, d=d, iters=iters)
+    # the same steps in FP64
+    i = torch.arange(d, device="cuda", dtype=torch.float64)
+    v = 1.0 + torch.remainder(i, 7.0) * 0.125
+    v = v / v.norm()
+    z = v.clone()
+    for _ in range(iters):
+        v_prev = v
+        Av = A @ v
+        w = R @ Av - A @ (R @ v)
+        c_norm = float(w.norm())
+        v = w / w.norm()
+        w3 = R @ (R @ z) - z
+        n_norm = float(w3.norm())
+        z = w3 / w3.norm()
+    assert g2 == pytest.approx(0.5 * c_norm, rel=1e-5)
+    assert rho == pytest.approx(n_norm, rel=1e-5)
+    assert a11 == pytest.approx(float(v_prev @ (A @ v_prev)), rel=1e-6, abs=1e-9)
+    assert a12 == pytest.approx(float(v @ (A @ v_prev)), rel=1e-6, abs=1e-9)
+    assert a22 == pytest.approx(float(v @ (A @ v)), rel=1e-6, abs=1e-9)

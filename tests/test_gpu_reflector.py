@@ -365,3 +365,29 @@ def test_refine_stop_on_bound_certifies_a_controlled_spectrum():
     err = float(torch.linalg.eigvalsh(0.5 * (D + D.T)).abs().max())
     assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
     assert info.err_bound <= 1e-6 and err <= info.err_bound, (err, info.as_dict())
+
+
+def test_refine_largest_order_d16384():
+    # the largest supported order: d = 16384 (FP64-emulating digit width 5,
+    # 11 planes in the polish tables; 2 GiB per FP64 matrix)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k, delta = 16384, 16, 1e-2
+    H, lam, Q = workloads.controlled_spectrum_torch(d, k, delta, seed=93)
+    R, info, st = rs.reflector(H, k, 0.0, tol=1e-6, policy=rs.Policy.FP16_REFINE, check=False,
+                               options=rs.default_options(ns_scaling=1, margin=delta,
+                                                          alpha_mode=int(rs.AlphaMode.POWER)))
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    Qk = Q[:, :k]
+    D = R - (torch.eye(d, dtype=torch.float64, device=R.device) - 2.0 * Qk @ Qk.T)
+    del H, Q
+    # ||D||_2 by power steps on the symmetric D (converging from below), and
+    # the Frobenius norm as a loose upper bound
+    v = torch.ones(d, dtype=torch.float64, device=R.device)
+    for _ in range(60):
+        v = D @ (D @ v)
+        v = v / v.norm()
+    err = float((D @ v).norm())
+    assert err <= 1e-6, (err, info.as_dict())
+    assert float(D.norm()) <= 1e-4
+    assert abs(info.trace - (d - 2 * k)) < 1e-6
