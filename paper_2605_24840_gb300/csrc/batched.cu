@@ -152,36 +152,6 @@ __global__ void batch_to_f64_kernel(const T* __restrict__ X0, const T* __restric
 // matrices that stay active and ctr[1] the finished blocks: the last block
 // sets all_done (1 once no matrix is active) and clears both counters.
 constexpr int kCheckWarps = 4;
-// Exact squared row norms of each matrix's iterate (the diagonal of X^2 for
-// the grouped SYRK), the same arithmetic as the one-matrix path.  Warps stride
-// over the rows of all matrices (rb: each matrix's first row in that count,
-// a binary search maps a row to its matrix), so the grid does not grow with
-// the padded slab; rows of retired matrices, and everything once the group
-// has stopped, are skipped.
-template <typename T>
-__global__ void batch_rowsq_kernel(const T* __restrict__ x, int D, long long slot, const int* __restrict__ dv,
-                                   const int* __restrict__ rb, int ng, int total_rows,
-                                   const int* __restrict__ done, const int* __restrict__ all_done,
-                                   float* __restrict__ out) {
-  if (*all_done) return;
-  const int lane = threadIdx.x & 31;
-  const int n_warps = gridDim.x * (blockDim.x >> 5);
-  for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < total_rows; r += n_warps) {
-    int lo = 0, hi = ng - 1;  // the last m with rb[m] <= r
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (rb[mid] <= r) lo = mid;
-      else hi = mid - 1;
-    }
-    const int m = lo;
-    if (done[m]) continue;  // warp-uniform
-    const int row = r - rb[m];
-    const int ncols = (dv[m] + 7) / 8 * 8;  // zeros beyond d_m inside the slot
-    const double acc = row_sumsq_warp<T>(x + (size_t)m * slot + (size_t)row * D, 0, 0, ncols, lane);
-    if (lane == 0) out[(size_t)m * D + row] = (float)acc;
-  }
-}
-
 // trp (nullable): trace partials of the current iterates (from the grouped
 // update, same slots); a floor or stagnation stop of matrix m then also needs
 // |trace X_m - (d_m - 2 k_m)| <= 1/2 + 2 u sqrt(d_m).
@@ -400,7 +370,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     // ---- per-matrix control arrays (one int and one double allocation)
     // ints: d, dp_lp(128), dp_lp(256), dp64, done, steps, flags, done64, steps64,
     //       slot_begin (lp: n+1, f64: n+1), status, all_done, all_done64
-    enum { I_D = 0, I_DP128, I_DP256, I_DP64, I_DONE, I_STEPS, I_FLAGS, I_DONE64, I_STEPS64, I_K, I_RB, I_N };
+    enum { I_D = 0, I_DP128, I_DP256, I_DP64, I_DONE, I_STEPS, I_FLAGS, I_DONE64, I_STEPS64, I_K, I_N };
     const size_t n_int = (size_t)I_N * ng + 3 * (size_t)(ng + 1) + 6;
     int* ib = nullptr;
     double* db = nullptr;
@@ -425,12 +395,9 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
 
     std::vector<int> h_int(n_int, 0);
     std::vector<int> dp128(ng), dp256(ng), dp64(ng);
-    int total_rows = 0;  // rows of all grouped matrices (I_RB: each matrix's first)
     for (int m = 0; m < ng; ++m) {
       h_int[(size_t)I_D * ng + m] = g.d[m];
       h_int[(size_t)I_K * ng + m] = g.k[m];
-      h_int[(size_t)I_RB * ng + m] = total_rows;
-      total_rows += g.d[m];
       dp128[m] = round_up(g.d[m], 128);
       dp256[m] = round_up(g.d[m], 256);
       dp64[m] = round_up(g.d[m], kF64Tile);
@@ -493,12 +460,10 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
       }
     }
     double* trpart = nullptr;  // trace partials of the grouped updates
-    float* rowsq = nullptr;    // exact squared row norms [ng][D] of the current iterates
     if (mem.alloc((void**)&A64, nel * 8) != cudaSuccess ||
         mem.alloc((void**)&rowpart, (size_t)ng * (D / 32) * D * 8) != cudaSuccess ||
         mem.alloc((void**)&partials, n_slots_max * 4 * 8) != cudaSuccess ||
-        mem.alloc((void**)&trpart, n_slots_max * 4 * 8) != cudaSuccess ||
-        mem.alloc((void**)&rowsq, (size_t)ng * D * 4) != cudaSuccess)
+        mem.alloc((void**)&trpart, n_slots_max * 4 * 8) != cudaSuccess)
       return fail_cuda();
     {
       dim3 grid(D / 32, D / 32, ng), block(32, 8);
@@ -611,7 +576,6 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         a.skip = all_done; a.units = units_c[c]; a.n_units = (int)ulp[c].size();
         a.mat_dp = c == 0 ? ia(I_DP128) : ia(I_DP256); a.mat_d = ia(I_D); a.mat_skip = ia(I_DONE);
         a.mat_stride = (long long)slot; a.a_planes = 1; a.b_planes = 1; a.cluster = 1;
-        a.ns_diag = rowsq; a.mat_vec_stride = D;
         return a;
       };
       // tile choice: forced, cached, or timed on the first SYRK (which
@@ -673,16 +637,6 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
       auto step = [&](int gs, cudaStream_t s2, bool last) -> bool {
         void* xm = xlp[gs & 1];
         void* xn = xlp[(gs + 1) & 1];
-        // one row per warp where possible (each row is a short dependent chain)
-        const int rq_blocks = std::max(1, std::min(32 * num_sms, (total_rows + 7) / 8));
-        if (fmt == 0)
-          batch_rowsq_kernel<__half><<<rq_blocks, 256, 0, s2>>>((const __half*)xm, D, (long long)slot, ia(I_D),
-                                                                ia(I_RB), ng, total_rows, ia(I_DONE), all_done,
-                                                                rowsq);
-        else
-          batch_rowsq_kernel<__nv_bfloat16><<<rq_blocks, 256, 0, s2>>>(
-              (const __nv_bfloat16*)xm, D, (long long)slot, ia(I_D), ia(I_RB), ng, total_rows, ia(I_DONE), all_done,
-              rowsq);
         if (tc_gemm_grouped(sy, tile_bn, xm, ng, xm, ng, fmt, num_sms, s2) != cudaSuccess) return false;
         batch_check_kernel<<<check_blocks, 32 * kCheckWarps, 0, s2>>>(
             partials, slot_use, ng, ia(I_D), 0, tol, u, max_steps, ia(I_DONE), ia(I_STEPS), da(D_PREV),
@@ -693,10 +647,10 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         a.out = xn;
         a.xin = xm;
         if (tc_gemm_grouped(a, tile_bn, xm, ng, elp, ng, fmt, num_sms, s2) != cudaSuccess) return false;
-        if (s2 == st) launches += 4;
+        if (s2 == st) launches += 3;
         return true;
       };
-      if (!run_stage(max_steps, all_done, 4, step)) return fail_cuda();
+      if (!run_stage(max_steps, all_done, 3, step)) return fail_cuda();
       // FP64 copy of each matrix's final iterate
       if (fmt == 0)
         batch_to_f64_kernel<__half><<<grid_of(nel), 256, 0, st>>>((const __half*)xlp[0], (const __half*)xlp[1],

@@ -1,6 +1,8 @@
 // f64_kernels.cu -- FP64 products (DMMA m8n8k4 on the FP64 pipe) and the
 // bandwidth-bound elementwise / reduction kernels of the reflector path.
+#include <type_traits>
 #include "common.cuh"
+#include "intconv.cuh"
 #include "kernels.h"
 
 namespace rsign {
@@ -157,6 +159,10 @@ __global__ void ingest_kernel(const double* __restrict__ H, int d, int dp, doubl
   __shared__ double t1[32][33], t2[32][33];
   const int bi = blockIdx.y, bj = blockIdx.x;  // A tile (bi, bj): rows bi*32.., cols bj*32..
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  // FP64 arithmetic only where it changes a value (GB300's FP64 pipe is
+  // slower than the stream): the finiteness test and |v| on the bit
+  // patterns, the average of a bitwise symmetric pair is the entry itself,
+  // the shift only on the diagonal
   bool bad = false;
   for (int r = ty; r < 32; r += 8) {
     const int i = bi * 32 + r, j = bj * 32 + tx;
@@ -164,7 +170,7 @@ __global__ void ingest_kernel(const double* __restrict__ H, int d, int dp, doubl
     if (i < d && j < d) h1 = H[(size_t)i * d + j];
     const int i2 = bj * 32 + r, j2 = bi * 32 + tx;  // transposed tile
     if (i2 < d && j2 < d) h2 = H[(size_t)i2 * d + j2];
-    if (!isfinite(h1) || !isfinite(h2)) bad = true;
+    if (((ic_bits(h1) >> 52) & 0x7FF) == 0x7FF || ((ic_bits(h2) >> 52) & 0x7FF) == 0x7FF) bad = true;
     t1[r][tx] = h1;
     t2[r][tx] = h2;
   }
@@ -172,9 +178,14 @@ __global__ void ingest_kernel(const double* __restrict__ H, int d, int dp, doubl
   for (int r = ty; r < 32; r += 8) {
     const int i = bi * 32 + r, j = bj * 32 + tx;
     double v = 0.0;
-    if (i < d && j < d) v = 0.5 * (t1[r][tx] + t2[tx][r]) - (i == j ? s : 0.0);
+    if (i < d && j < d) {
+      const double a = t1[r][tx], b = t2[tx][r];
+      if (i == j) v = a - s;
+      else if (ic_bits(a) == ic_bits(b)) v = a;
+      else v = 0.5 * (a + b);
+    }
     A[(size_t)i * dp + j] = v;
-    t1[r][tx] = fabs(v);
+    t1[r][tx] = ic_double(ic_bits(v) & 0x7FFFFFFFFFFFFFFFull);
   }
   if (bad) atomicOr(flags, 1);
   __syncthreads();
@@ -298,22 +309,47 @@ __global__ void scale_convert_kernel(const double* __restrict__ src, size_t n, c
   }
 }
 
+// hi + lo = x * scale as a pair of FP16/BF16 planes without FP64 arithmetic:
+// x 2^k and scale 2^-k split into float pairs by integer operations (2^k
+// the scale's power of two, which keeps x 2^k inside the float range), their
+// product formed in double-float (the leading product split exactly by an
+// FMA), hi = T(v_hi), lo = T(v_hi - hi + v_lo).  hi + lo carries the product
+// to the pair's 2^-22; hi may differ from the rounding of the exact product
+// in the last place where that product lies within v_lo of a tie.
 template <typename T>
 __global__ void convert_split_kernel(const double* __restrict__ src, size_t n, const double* scale_dev,
                                      T* __restrict__ dst) {
   const double sc = scale_dev ? *scale_dev : 1.0;
+  const int k = ic_exponent(sc);
+  float ah, al;
+  ic_split_f32(sc, -k, &ah, &al);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = src[i] * sc;
-    const T hi = from_f64<T>(v);
+    float xh, xl;
+    ic_split_f32(src[i], k, &xh, &xl);
+    const float p = __fmul_rn(xh, ah);
+    const float c = fmaf(xh, ah, -p) + fmaf(xh, al, xl * ah);
+    const float vh = __fadd_rn(p, c);
+    const float vl = __fsub_rn(c, __fsub_rn(vh, p));
+    const T hi = from_f32<T>(vh);
     dst[i] = hi;
-    dst[n + i] = from_f64<T>(v - (double)to_f32<T>(hi));
+    dst[n + i] = from_f32<T>(__fsub_rn(vh, to_f32<T>(hi)) + vl);
   }
 }
 
+// dst = hi + lo exactly: for FP16 by integer operations (both halves are
+// multiples of 2^-24 below 2^16, so their sum is an integer count of 2^-24
+// below 2^41); BF16 (a wider exponent range) in FP64
 template <typename T>
 __global__ void split_to_f64_kernel(const T* __restrict__ src, size_t n, double* __restrict__ dst) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = (double)to_f32<T>(src[i]) + (double)to_f32<T>(src[n + i]);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value) {
+      const uint16_t h = *reinterpret_cast<const uint16_t*>(src + i);
+      const uint16_t l = *reinterpret_cast<const uint16_t*>(src + n + i);
+      dst[i] = ic_i64_scaled(ic_f16_units(h) + ic_f16_units(l), -24);
+    } else {
+      dst[i] = (double)to_f32<T>(src[i]) + (double)to_f32<T>(src[n + i]);
+    }
+  }
 }
 
 // out[i] = sum_j x_ij^2 of the FP16/BF16 operand x = hi (+ lo) of a Newton-
@@ -431,9 +467,9 @@ __global__ void symmetrize_scale_kernel(const double* __restrict__ S, int dp, do
   }
 }
 
-__global__ void alpha_from_rho_kernel(const double* nrm, double c, double* scal) {
+__global__ void alpha_from_rho_kernel(const double* nrm, double c, double* scal, int kscaled) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    const double rho = nrm[0];
+    const double rho = kscaled ? ldexp(nrm[0], -ic_exponent(scal[1])) : nrm[0];
     scal[3] = rho;
     scal[1] = rho > 0.0 ? 1.0 / (c * rho) : 0.0;
   }
@@ -600,8 +636,8 @@ cudaError_t symmetrize_scale(const double* src, int dp, double scale, double* ds
   return cudaGetLastError();
 }
 
-cudaError_t alpha_from_rho(const double* nrm, double c, double* scal, cudaStream_t st) {
-  alpha_from_rho_kernel<<<1, 32, 0, st>>>(nrm, c, scal);
+cudaError_t alpha_from_rho(const double* nrm, double c, double* scal, int kscaled, cudaStream_t st) {
+  alpha_from_rho_kernel<<<1, 32, 0, st>>>(nrm, c, scal, kscaled);
   return cudaGetLastError();
 }
 

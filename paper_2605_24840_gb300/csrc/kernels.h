@@ -358,9 +358,14 @@ cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockm
 // v, w: dp-float work vectors.
 cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
                               cudaStream_t st);
-// hi = fl32(x), lo = fl32(x - hi) (lo nullable): x = hi + lo to 2^-48
-// relative, the operand form of the double-float GEMVs below.
-cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, cudaStream_t st);
+// hi + lo = x 2^k to 2^-47 relative (lo nullable), by integer operations
+// (GB300's FP64 conversions run at the FP64 rate): the operand form of the
+// double-float GEMVs below.  k = k_host plus, when kref is given, the
+// exponent of the device scalar *kref (a power-of-two scaling that keeps the
+// data inside the float range; values below 2^-126 after scaling become 0).
+// n even.
+cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, int k_host, const double* kref,
+                      cudaStream_t st);
 // y = M x in double-float arithmetic (M, x as hi + lo FP32 pairs; dp a
 // multiple of 256), y in FP64.
 cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y, int dp,
@@ -385,7 +390,12 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
 // 1 / (c rho_est).  alpha rho < sqrt(3) keeps every sign (f(t) = t(3 - t^2)/2
 // > 0 on (0, sqrt(3))) as long as rho_est > rho / (c sqrt(3)); the trace
 // certificate checks it.
-cudaError_t alpha_from_rho(const double* nrm, double c, double* scal, cudaStream_t st);
+// With kscaled, nrm[0] came from A 2^k, k the exponent of the Gershgorin alpha
+// in scal[1] on entry: rho_est = nrm[0] 2^-k.
+cudaError_t alpha_from_rho(const double* nrm, double c, double* scal, int kscaled, cudaStream_t st);
+// dst (FP16) = src (FP64) rounded by way of the nearest float (integer
+// operations; may differ from a direct rounding at exact FP16 ties); n even.
+cudaError_t to_f16(const double* src, size_t n, void* dst, cudaStream_t st);
 // R += 1/2 P / sigma (P FP32 symmetric product R_lp Et_lp).
 cudaError_t polish_update(double* R, const float* P, int dp, const float* sigma, cudaStream_t st);
 

@@ -10,6 +10,7 @@
 // epilogue and the truncation after kSlices digits (35 bits).
 #include <type_traits>
 #include "common.cuh"
+#include "intconv.cuh"
 #include "kernels.h"
 
 #include <algorithm>
@@ -119,6 +120,9 @@ __device__ __forceinline__ void tile_max(float v, float* blockmax) {
   }
 }
 
+// C = N - N^T: one FP64 subtraction per element (the cancellation needs it);
+// the float of the result by integer rounding, its square summed in FP32 per
+// thread (four terms) and in FP64 across the tile
 __global__ void antisym_kernel(const double* __restrict__ N, int dp, float* __restrict__ C,
                                float* blockmax, double* part) {
   __shared__ double t[TILE][TILE + 1];
@@ -126,17 +130,16 @@ __global__ void antisym_kernel(const double* __restrict__ N, int dp, float* __re
   const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
   for (int r = ty; r < TILE; r += 8) t[r][tx] = N[(size_t)(bj * TILE + r) * dp + bi * TILE + tx];
   __syncthreads();
-  float m = 0.f;
-  double s2 = 0.0;
+  float m = 0.f, s2f = 0.f;
   for (int r = ty; r < TILE; r += 8) {
     const size_t e = (size_t)(bi * TILE + r) * dp + bj * TILE + tx;
-    const double cd = N[e] - t[tx][r];
-    const float c = (float)cd;
+    float c, cl;
+    ic_split_f32(N[e] - t[tx][r], 0, &c, &cl);
     C[e] = c;
     m = fmaxf(m, fabsf(c));
-    s2 += cd * cd;
+    s2f = fmaf(c, c, s2f);
   }
-  s2 = warp_sum(s2);
+  double s2 = warp_sum((double)s2f);
   if (tx == 0) sd[ty] = s2;
   tile_max(m, blockmax);  // contains __syncthreads
   if (tx == 0 && ty == 0) {
@@ -183,22 +186,26 @@ __global__ void tangent_combine_kernel(float* __restrict__ E, const float* __res
   tile_max(m, blockmax);
 }
 
+// Et = I - Y: off the diagonal -Y (a sign flip), rounded to float by integer
+// operations; FP64 only on the diagonal; squares summed as in antisym_kernel
 __global__ void ident_minus_kernel(const double* __restrict__ Y, int dp, int d, float* __restrict__ Et,
                                    float* blockmax, double* part) {
   __shared__ double sd[8];
   const int bi = blockIdx.y, bj = blockIdx.x, tx = threadIdx.x, ty = threadIdx.y;
-  float m = 0.f;
-  double s2 = 0.0;
+  float m = 0.f, s2f = 0.f;
   for (int r = ty; r < TILE; r += 8) {
     const int i = bi * TILE + r, j = bj * TILE + tx;
     const size_t e = (size_t)i * dp + j;
-    const bool real = i < d && j < d;
-    const double v = real ? ((i == j ? 1.0 : 0.0) - Y[e]) : 0.0;
-    Et[e] = (float)v;
-    m = fmaxf(m, fabsf((float)v));
-    s2 += v * v;
+    float v = 0.f, vl;
+    if (i < d && j < d) {
+      const double y = Y[e];
+      ic_split_f32(i == j ? 1.0 - y : ic_double(ic_bits(y) ^ 0x8000000000000000ull), 0, &v, &vl);
+    }
+    Et[e] = v;
+    m = fmaxf(m, fabsf(v));
+    s2f = fmaf(v, v, s2f);
   }
-  s2 = warp_sum(s2);
+  double s2 = warp_sum((double)s2f);
   if (tx == 0) sd[ty] = s2;
   tile_max(m, blockmax);  // contains __syncthreads
   if (tx == 0 && ty == 0) {
@@ -236,21 +243,43 @@ __global__ void max_pow2_kernel(const float* __restrict__ x, int n, float* out) 
 template <typename T>
 __global__ void scale_to_lp_kernel(const float* __restrict__ src, size_t n, const float* scale,
                                    T* __restrict__ dst) {
+  // four elements per thread and iteration: one 16-byte load, one 8-byte store
+  // (n is a multiple of 4)
   const float s = scale[0];
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = from_f32<T>(src[i] * s);
+  const size_t n4 = n >> 2;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = s4[i];
+    const T t[4] = {from_f32<T>(v.x * s), from_f32<T>(v.y * s), from_f32<T>(v.z * s), from_f32<T>(v.w * s)};
+    uint2 w;
+    w.x = (uint32_t)(*reinterpret_cast<const uint16_t*>(&t[0])) |
+          ((uint32_t)(*reinterpret_cast<const uint16_t*>(&t[1])) << 16);
+    w.y = (uint32_t)(*reinterpret_cast<const uint16_t*>(&t[2])) |
+          ((uint32_t)(*reinterpret_cast<const uint16_t*>(&t[3])) << 16);
+    reinterpret_cast<uint2*>(dst)[i] = w;
+  }
 }
 
+// R += E: the float converted exactly by integer operations, one FP64 add;
+// ||E||_F^2 from FP32 squares (four per thread between FP64 additions)
 __global__ void add_correction_kernel(double* __restrict__ R, const float* __restrict__ E, int dp, int d,
                                       double* part) {
   __shared__ double sh[32];
   double s = 0.0;
+  float sf = 0.f;
+  int cnt = 0;
   const size_t n = (size_t)dp * dp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const double v = (double)E[e];
-    R[e] += v;
-    s += v * v;
+    const float v = E[e];
+    R[e] += ic_f2d(v);
+    sf = fmaf(v, v, sf);
+    if (++cnt == 4) {
+      s += (double)sf;
+      sf = 0.f;
+      cnt = 0;
+    }
   }
+  s += (double)sf;
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -261,12 +290,29 @@ __global__ void add_correction_kernel(double* __restrict__ R, const float* __res
   }
 }
 
+// R += 1/2 P / sigma; sigma is a power of two, so the scaling is exact in
+// FP32 (barring underflow); the float is converted exactly by integer
+// operations: one FP64 add per element
 __global__ void polish_update_kernel(double* __restrict__ R, const float* __restrict__ P, int dp,
                                      const float* sigma) {
-  const double f = 0.5 / (double)sigma[0];
+  const float f = 0.5f / sigma[0];
   const size_t n = (size_t)dp * dp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    R[e] += f * (double)P[e];
+    R[e] += ic_f2d(f * P[e]);
+}
+
+// dst = FP16(src) by way of the nearest float (integer rounding, then the
+// float -> half conversion): two elements per thread and iteration
+__global__ void to_f16_kernel(const double* __restrict__ src, size_t n, __half* __restrict__ dst) {
+  const size_t n2 = n >> 1;
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 x = s2[i];
+    float a, b, al, bl;
+    ic_split_f32(x.x, 0, &a, &al);
+    ic_split_f32(x.y, 0, &b, &bl);
+    reinterpret_cast<__half2*>(dst)[i] = __floats2half2_rn(a, b);
+  }
 }
 
 // w = M v for a dp x dp FP32 matrix, one warp per row; v deterministic start
@@ -473,13 +519,20 @@ __global__ void gemv_df_kernel(const GemvDfArgs a) {
   else gemv_df_row<false>(J, r, a.dp, lane);
 }
 
+// hi + lo = src 2^k (k = k_host, plus the exponent of *kref when given), by
+// integer operations (ic_split_f32): two float2 stores per pair of elements
 __global__ void split_f32_kernel(const double* __restrict__ src, size_t n, float* __restrict__ hi,
-                                 float* __restrict__ lo) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double x = src[i];
-    const float h = __double2float_rn(x);
-    hi[i] = h;
-    if (lo != nullptr) lo[i] = __double2float_rn(x - (double)h);
+                                 float* __restrict__ lo, int k_host, const double* __restrict__ kref) {
+  const int k = k_host + (kref != nullptr ? ic_exponent(kref[0]) : 0);
+  const size_t n2 = n >> 1;  // n is even (dp^2 or dp)
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 x = s2[i];
+    float2 h, l;
+    ic_split_f32(x.x, k, &h.x, &l.x);
+    ic_split_f32(x.y, k, &h.y, &l.y);
+    reinterpret_cast<float2*>(hi)[i] = h;
+    if (lo != nullptr) reinterpret_cast<float2*>(lo)[i] = l;
   }
 }
 
@@ -734,8 +787,9 @@ cudaError_t max_pow2(const float* x, int n, float* out, cudaStream_t st) {
 }
 
 cudaError_t scale_to_lp(const float* src, size_t n, const float* scale, void* dst, int fmt, cudaStream_t st) {
-  if (fmt == 0) scale_to_lp_kernel<__half><<<grid_for(n), 256, 0, st>>>(src, n, scale, (__half*)dst);
-  else scale_to_lp_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, st>>>(src, n, scale, (__nv_bfloat16*)dst);
+  if (n & 3) return cudaErrorInvalidValue;
+  if (fmt == 0) scale_to_lp_kernel<__half><<<grid_for(n / 4), 256, 0, st>>>(src, n, scale, (__half*)dst);
+  else scale_to_lp_kernel<__nv_bfloat16><<<grid_for(n / 4), 256, 0, st>>>(src, n, scale, (__nv_bfloat16*)dst);
   return cudaGetLastError();
 }
 
@@ -782,8 +836,10 @@ cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, con
   return cudaGetLastError();
 }
 
-cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, cudaStream_t st) {
-  split_f32_kernel<<<grid_for(n), 256, 0, st>>>(src, n, hi, lo);
+cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, int k, const double* kref,
+                      cudaStream_t st) {
+  if (n & 1) return cudaErrorInvalidValue;
+  split_f32_kernel<<<grid_for(n / 2), 256, 0, st>>>(src, n, hi, lo, k, kref);
   return cudaGetLastError();
 }
 
@@ -811,7 +867,7 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
   float *t2h = fwork + 8 * dp, *t2l = fwork + 9 * dp;
   float *t3h = fwork + 10 * dp, *t3l = fwork + 11 * dp;
   const size_t dd = (size_t)dp * dp;
-  split_f32_kernel<<<grid_for(dd), 256, 0, st>>>(R, dd, R_hi, R_lo);
+  split_f32_kernel<<<grid_for(dd / 2), 256, 0, st>>>(R, dd, R_hi, R_lo, 0, nullptr);
   start_vec_f64_kernel<<<(dp + 255) / 256, 256, 0, st>>>(w, d, dp);
   normalize_split_kernel<<<1, 1024, 0, st>>>(w, dp, vb[0], vbh[0], vbl[0], out);
   normalize_split_kernel<<<1, 1024, 0, st>>>(w, dp, z, zh, zl, out + 1);
@@ -853,6 +909,12 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
   dot3_kernel<<<1, 1024, 0, st>>>(vb[prev], t1, vb[last], t1, vb[last], t4, dp, out + 2);
   // out[0] = ||C v_prev|| = 2 ||G v_prev|| (G = 1/2 R C): halve it
   scale_scalar_kernel<<<1, 1, 0, st>>>(out, 0.5);
+  return cudaGetLastError();
+}
+
+cudaError_t to_f16(const double* src, size_t n, void* dst, cudaStream_t st) {
+  if (n & 1) return cudaErrorInvalidValue;
+  to_f16_kernel<<<grid_for(n / 2), 256, 0, st>>>(src, n, (__half*)dst);
   return cudaGetLastError();
 }
 

@@ -259,6 +259,10 @@ struct RefineOut {
   int levels_ra0 = 0;
 };
 
+// Orders above which the Newton-Schulz SYRK takes the diagonal of X^2 from
+// exact row norms (row_sumsq) instead of the tensor-core sums.
+constexpr int kExactDiagMin = 1024;
+
 // Digit levels of the refinement's FP64-grade products (5 bits each): the
 // polish SYRK R^2, the first sweep's R A and the later sweeps' R A; 0 = by
 // rule.  Polish: the truncation error scales with the off-diagonal row maxima
@@ -354,7 +358,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     if (!c.ok(r = sum_partials(part, ntile, red + 0, st))) return r;
     if (!c.ok(r = max_pow2(bmax, ntile, fs + 0, st))) return r;
     if (!c.ok(r = scale_to_lp(C32, dd, fs + 1, Clp, 0, st))) return r;
-    if (!c.ok(r = scale_convert(in.R64, dd, nullptr, 1.0, Rlp, 0, st))) return r;
+    if (!c.ok(r = to_f16(in.R64, dd, Rlp, st))) return r;
     if (!c.ok(r = tc(Rlp, Clp, 0, 1, TC_EPI_STORE_F32, P32))) return r;
     if (!c.ok(r = polish_update(in.R64, P32, dp, fs + 1, st))) return r;
     o->polish_steps++;
@@ -400,7 +404,9 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   RS_TRY(mem.alloc((void**)&A_lo, dd * 4));
   RS_TRY(mem.alloc((void**)&R_hi, dd * 4));
   RS_TRY(mem.alloc((void**)&R_lo, dd * 4));
-  RS_TRY(c.ok(split_f32(in.A64, dd, A_hi, A_lo, st)) ? cudaSuccess : c.err);  // operand of the checks
+  // operand of the checks: A 2^kA, 2^kA ~ alpha ~ 1/||A|| (results scaled back)
+  const int kA = std::ilogb(in.alpha);
+  RS_TRY(c.ok(split_f32(in.A64, dd, A_hi, A_lo, kA, nullptr, st)) ? cudaSuccess : c.err);
   double kappa = NAN;
   for (int sw = 0; sw <= in.max_sweeps; ++sw) {
     if (sw >= 1) {
@@ -412,7 +418,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       c.launches += 5 * kCheckIters + 6;
       RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
       RS_TRY(cudaStreamSynchronize(st));
-      const double g2 = h_red[9];
+      const double g2 = std::ldexp(h_red[9], -kA);
       o->comm = 2.0 * g2;  // ||R A - A R||_2 = 2 ||G||_2 for an orthogonal R
       o->rho = h_red[10];
       const bool mu_known = std::isfinite(in.margin) && in.margin > 0.0;
@@ -424,7 +430,8 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       // component F between eigenpairs i, j has ||C||_2 = |lam_i - lam_j| ||F||_2.
       // The second catches errors that the last solve left between
       // eigenvalues next to the gap (clustered spectra).
-      const double a11 = h_red[11], a12 = h_red[12], a22 = h_red[13];
+      const double a11 = std::ldexp(h_red[11], -kA), a12 = std::ldexp(h_red[12], -kA),
+                   a22 = std::ldexp(h_red[13], -kA);
       double g_rr = std::sqrt((a11 - a22) * (a11 - a22) + 4.0 * a12 * a12);
       if (mu_known) g_rr = std::max(g_rr, 2.0 * in.margin);
       const double est_rr = g_rr > 0.0 ? o->comm / g_rr : INFINITY;
@@ -465,7 +472,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     if (!c.ok(sum_partials(part, ntile, red + 4, st))) return c.err;
     if (!c.ok(max_pow2(bmax, ntile, fs + 2, st))) return c.err;
     if (!c.ok(scale_to_lp(C32, dd, fs + 3, Clp, 0, st))) return c.err;
-    if (!c.ok(scale_convert(in.R64, dd, nullptr, 1.0, Rlp, 0, st))) return c.err;
+    if (!c.ok(to_f16(in.R64, dd, Rlp, st))) return c.err;
     // P = R C_lp^T = -sigma_C R C;  E_0 = alpha/4 (R C + (R C)^T)
     if (!c.ok(tc(Rlp, Clp, 0, 0, TC_EPI_STORE_F32, P32))) return c.err;
     if (!c.ok(newton_direction(P32, dp, fs + 3, in.alpha, E32, bmax, st))) return c.err;
@@ -637,9 +644,11 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         mem.alloc((void**)&pw, (size_t)dp * 4) != cudaSuccess)
       return fail_cuda();
     const int ps = std::max(1, opt.power_steps);
-    if (!c.ok(split_f32(A64, dd, a32, nullptr, st)) ||
+    // (A scaled by 2^k, 2^k the Gershgorin alpha's power of two, so that any
+    // scale of H stays inside the float range)
+    if (!c.ok(split_f32(A64, dd, a32, nullptr, 0, ctl->scal + 1, st)) ||
         !c.ok(spectral_norm_f32(a32, dp, pv, pw, ps, ctl->scal + 4, st)) ||
-        !c.ok(alpha_from_rho(ctl->scal + 4, 1.02, ctl->scal, st)))
+        !c.ok(alpha_from_rho(ctl->scal + 4, 1.02, ctl->scal, 1, st)))
       return fail_cuda();
     c.launches += 2 * ps + 2;
   }
@@ -753,9 +762,12 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     double* tr_part = nullptr;
     if (mem.alloc((void**)&tr_part, (size_t)nt * 4 * 8) != cudaSuccess) return fail_cuda();
     const double tr_tol = 0.5 + 2.0 * u * std::sqrt((double)d);
-    // exact squared row norms of each iterate: the SYRK's diagonal
+    // exact squared row norms of each iterate for the SYRK's diagonal above
+    // d = 1024 (kExactDiagMin): below, the tensor cores' accumulation bias moves
+    // the trace by less than 3e-3 (and the grouped launches of the batched
+    // calls, d <= 1024, stay bitwise equal to one-matrix calls)
     float* rowsq = nullptr;
-    if (mem.alloc((void**)&rowsq, (size_t)dp * 4) != cudaSuccess) return fail_cuda();
+    if (d > kExactDiagMin && mem.alloc((void**)&rowsq, (size_t)dp * 4) != cudaSuccess) return fail_cuda();
     int m = 0;
     bool stopped = false;
     while (m <= opt.max_steps && !stopped) {
@@ -781,7 +793,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         sy.ns_c2 = (float)(am * am);
         sy.ns_c1 = (float)am;
         sy.ns_diag = rowsq;
-        if (!c.ok(row_sumsq(xm, fmt, split ? 1 : 0, dp, d, rowsq, &ctl->done_low, st))) return fail_cuda();
+        if (rowsq && !c.ok(row_sumsq(xm, fmt, split ? 1 : 0, dp, d, rowsq, &ctl->done_low, st))) return fail_cuda();
         if (!c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st))) return fail_cuda();
         const bool floors = mm >= m_min;
         if (!c.ok(ns_check(partials, nt * 4, hist_low, mm, 0.0, floors ? floor_lo : -1.0, floors ? floor_hi : -1.0,
@@ -1115,7 +1127,7 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
     const double u = split ? 4.0 * unit_roundoff(fmt) * unit_roundoff(fmt) : unit_roundoff(fmt);
     const int nt = tc_num_tiles(dp, 1);
     float* rowsq = nullptr;
-    if (mem.alloc((void**)&rowsq, (size_t)dp * 4) != cudaSuccess) return fail();
+    if (d > kExactDiagMin && mem.alloc((void**)&rowsq, (size_t)dp * 4) != cudaSuccess) return fail();
     int M = max_steps;
     for (int m = 0; m <= max_steps; ++m) {
       void* xm = slot(xs, m);
@@ -1132,7 +1144,7 @@ rsign_status backward_impl(const double* H, int64_t d64, int32_t k, double s, rs
       sy.split = split ? 1 : 0; sy.group_scale[0] = 1.0; sy.scale = 1.0f; sy.out = em; sy.partials = partials;
       sy.status = &ctl->status;
       sy.ns_diag = rowsq;
-      if (!c.ok(row_sumsq(xm, fmt, split ? 1 : 0, dp, d, rowsq, nullptr, st)) ||
+      if ((rowsq && !c.ok(row_sumsq(xm, fmt, split ? 1 : 0, dp, d, rowsq, nullptr, st))) ||
           !c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st)) ||
           !c.ok(ns_check(partials, nt * 4, hist, m, 0.0, 2.0 * u * std::sqrt((double)d), 16.0 * u * std::sqrt((double)d),
                          0.5, &ctl->done_low, &ctl->steps_low, st)))
@@ -1522,7 +1534,8 @@ rsign_status rsign_dbg_gemv_df(const double* M, const double* x, int64_t dp, dou
   rsign_status res = RSIGN_OK;
   if (mem.alloc((void**)&mh, dd * 4) != cudaSuccess || mem.alloc((void**)&ml, dd * 4) != cudaSuccess ||
       mem.alloc((void**)&xh, (size_t)dp * 4) != cudaSuccess || mem.alloc((void**)&xl, (size_t)dp * 4) != cudaSuccess ||
-      split_f32(M, dd, mh, ml, st) != cudaSuccess || split_f32(x, (size_t)dp, xh, xl, st) != cudaSuccess ||
+      split_f32(M, dd, mh, ml, 0, nullptr, st) != cudaSuccess ||
+      split_f32(x, (size_t)dp, xh, xl, 0, nullptr, st) != cudaSuccess ||
       gemv_df(mh, ml, xh, xl, y, (int)dp, st) != cudaSuccess)
     res = RSIGN_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
@@ -1550,7 +1563,7 @@ rsign_status rsign_dbg_commutator_check(const double* A, const double* R, int64_
       mem.alloc((void**)&rh, dd * 4) != cudaSuccess || mem.alloc((void**)&rl, dd * 4) != cudaSuccess ||
       mem.alloc((void**)&fw, (size_t)12 * dp * 4) != cudaSuccess ||
       mem.alloc((void**)&w, (size_t)12 * dp * 8) != cudaSuccess || mem.alloc((void**)&o, 8 * 8) != cudaSuccess ||
-      split_f32(A, dd, ah, al, st) != cudaSuccess ||
+      split_f32(A, dd, ah, al, 0, nullptr, st) != cudaSuccess ||
       commutator_gain_norm(ah, al, R, rh, rl, (int)dp, (int)d, iters, w, fw, o, st) != cudaSuccess ||
       cudaMemcpyAsync(out, o, 5 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     res = RSIGN_ERR_CUDA;
