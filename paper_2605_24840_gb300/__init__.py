@@ -189,6 +189,8 @@ def load():
     lib.rsign_dbg_fp64grade_gemm.restype = ctypes.c_int
     lib.rsign_dbg_set_refine_levels.argtypes = [i32, i32, i32]
     lib.rsign_dbg_set_refine_levels.restype = i32
+    lib.rsign_dbg_set_ozaki_tile.argtypes = [i32]
+    lib.rsign_dbg_set_ozaki_tile.restype = i32
     lib.rsign_dbg_tile_order.argtypes = [i64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.rsign_dbg_tile_order.restype = i32
     lib.rsign_dbg_fp64e_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
@@ -508,6 +510,12 @@ def dbg_set_refine_levels(polish=-1, ra_first=-1, ra_later=-1):
     """Set the digit levels of the refinement's FP64-grade products (0 = by the tolerance,
     -1 keeps a setting); returns the previous settings as 100 p + 10 f + l."""
     return int(load().rsign_dbg_set_refine_levels(int(polish), int(ra_first), int(ra_later)))
+
+
+def dbg_set_ozaki_tile(bn):
+    """Tile width (128, 256, or 0 = by order) of the refinement's FP64-grade products; returns the
+    previous setting."""
+    return int(load().rsign_dbg_set_ozaki_tile(int(bn)))
 
 
 def dbg_tile_order(dp, sym=0, cluster=1):

@@ -317,8 +317,17 @@ cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
 // sym = 1 when the product is symmetric (A == B): upper tiles + mirror.
 // `levels` (<= kSlices) truncates the digit-plane product after levels
 // 0 .. levels-1 (5 bits each, relative to the off-diagonal row maxima).
+// With `tiles` the product runs on 128 x 128 tiles from that device table
+// (one matrix in the grouped mode): the int64 level sums then stay in TMEM
+// instead of a global read-modify-write per level group.
+struct OzTiles {
+  const int4* units = nullptr;  // (0, row tile, column tile, slot)
+  int n_units = 0;
+  const int* dims = nullptr;    // device {dp, d_real}
+};
 cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym,
-                       double* out, int* status, int num_sms, cudaStream_t st, int levels = kSlices);
+                       double* out, int* status, int num_sms, cudaStream_t st, int levels = kSlices,
+                       const OzTiles* tiles = nullptr);
 
 // Elementwise kernels of the refinement sweep.  `scal` is a small device
 // array of scalars: each kernel documents the slots it reads and writes.

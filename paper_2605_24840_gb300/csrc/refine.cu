@@ -717,8 +717,16 @@ cudaError_t fp64e_plan(TcGemmArgs* a, int n_planes, int beta, int levels, int k_
 }
 
 cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym, double* out,
-                       int* status, int num_sms, cudaStream_t st, int levels) {
+                       int* status, int num_sms, cudaStream_t st, int levels, const OzTiles* tiles) {
   Fp64eExtra x{};
+  if (tiles != nullptr) {  // 128 x 128 tiles, int64 level sums in TMEM (grouped mode, one matrix)
+    x.units = tiles->units;
+    x.n_units = tiles->n_units;
+    x.n_mat = 1;
+    x.bn = 128;
+    x.mat_dp = tiles->dims;
+    x.mat_d = tiles->dims + 1;
+  }
   return fp64e_gemm(A, B, dp, d_real, sym, out, x, status, num_sms, st, levels);
 }
 

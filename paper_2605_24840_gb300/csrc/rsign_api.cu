@@ -259,7 +259,32 @@ struct RefineOut {
   int levels_ra0 = 0;
 };
 
-// Orders above which the Newton-Schulz SYRK takes the diagonal of X^2 from
+// Tile width of the refinement's FP64-grade products: 128 keeps the int64
+// level sums in TMEM (grouped-mode launch over a one-matrix tile table),
+// 256 uses cluster pairs with the sums in global memory; 0 = by order.
+// Measured per call (FP16_REFINE, k = 16): d = 3072 9.85 ms with 128 against
+// 10.45 with 256 (the global read-modify-write of the sums stalls the
+// epilogue when the K loop of a level group is short); d = 8192 78.5 against
+// 76.5 (long K loops hide it, and the pairs' shared B panel halves the
+// operand traffic).
+int g_oz_tile = 0;
+int oz_tile_for(int dp) { return g_oz_tile != 0 ? g_oz_tile : (dp <= 4096 ? 128 : 256); }
+
+// Tile table of one dp x dp product on 128 x 128 tiles (upper triangle when
+// sym), visited in blocks of 16 x 16 tiles so that the CTAs in flight share
+// row and column panels in L2.
+std::vector<int4> oz_tile_table(int dp, int sym) {
+  const int nb = dp / 128, bh = 16, bw = 16;
+  std::vector<int4> u;
+  for (int cb = 0; cb < nb; cb += bw)
+    for (int rb = 0; rb < nb; rb += bh)
+      for (int r = rb; r < std::min(rb + bh, nb); ++r)
+        for (int c = cb; c < std::min(cb + bw, nb); ++c)
+          if (!sym || c >= r) u.push_back(make_int4(0, r, c, (int)u.size()));
+  return u;
+}
+
+// Order above which the Newton-Schulz SYRK takes the diagonal of X^2 from
 // exact row norms (row_sumsq) instead of the tensor-core sums.
 constexpr int kExactDiagMin = 1024;
 
@@ -336,6 +361,30 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   RS_TRY(mem.alloc((void**)&part, (size_t)std::max(ntile, 1024) * 8));
   RS_TRY(mem.alloc((void**)&fs, 16 * 4));
   RS_TRY(mem.alloc((void**)&red, 24 * 8));
+  OzTiles oz_full{}, oz_sym{};
+  const OzTiles* tz_full = nullptr;
+  const OzTiles* tz_sym = nullptr;
+  if (oz_tile_for(dp) == 128) {
+    const std::vector<int4> uf = oz_tile_table(dp, 0), us = oz_tile_table(dp, 1);
+    int4 *duf = nullptr, *dus = nullptr;
+    int* dims = nullptr;
+    const int h_dims[2] = {dp, d};
+    RS_TRY(mem.alloc((void**)&duf, uf.size() * sizeof(int4)));
+    RS_TRY(mem.alloc((void**)&dus, us.size() * sizeof(int4)));
+    RS_TRY(mem.alloc((void**)&dims, 2 * sizeof(int)));
+    RS_TRY(cudaMemcpyAsync(duf, uf.data(), uf.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    RS_TRY(cudaMemcpyAsync(dus, us.data(), us.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    RS_TRY(cudaMemcpyAsync(dims, h_dims, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    RS_TRY(cudaStreamSynchronize(st));  // the host tables go out of scope
+    oz_full.units = duf;
+    oz_full.n_units = (int)uf.size();
+    oz_full.dims = dims;
+    oz_sym.units = dus;
+    oz_sym.n_units = (int)us.size();
+    oz_sym.dims = dims;
+    tz_full = &oz_full;
+    tz_sym = &oz_sym;
+  }
   int* status = &ctl->status;
 
   auto tc = [&](const void* A, const void* B, int fmt, int sym, int epi, void* out) {
@@ -352,7 +401,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     // R^2 to ~1e-9 absolute suffices for the polish: 6 levels (30 bits of the
     // off-diagonal part, the diagonal exact)
     if (!c.ok(r = ozaki_gemm(Rs, Rs, dp, d, 1, N64, status, c.num_sms, st,
-                             levels_for(g_levels_polish, in.tol, d, in.k))))
+                             levels_for(g_levels_polish, in.tol, d, in.k), tz_sym)))
       return r;
     if (!c.ok(r = ident_minus(N64, dp, d, C32, bmax, part, st))) return r;
     if (!c.ok(r = sum_partials(part, ntile, red + 0, st))) return r;
@@ -394,6 +443,22 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   float *pv = nullptr, *pw = nullptr;
   RS_TRY(mem.alloc((void**)&pv, (size_t)dp * 4));
   RS_TRY(mem.alloc((void**)&pw, (size_t)dp * 4));
+  // side stream for the 2-norm estimates of the tangent solve; joined before
+  // every readback, and synchronised before the workspace can be released
+  struct Side {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    ~Side() {
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+      for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+  } side;
+  RS_TRY(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+  for (int q = 0; q < 3; ++q) RS_TRY(cudaEventCreateWithFlags(&side.ev[q], cudaEventDisableTiming));
   constexpr int kPowerIters = 16;
   constexpr int kCheckIters = 12;
   double* cwork = nullptr;
@@ -467,7 +532,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       }
     }
     o->levels_ra0 = sw == 0 ? lev : o->levels_ra0;
-    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st, lev))) return c.err;
+    if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st, lev, tz_full))) return c.err;
     if (!c.ok(antisym_part(N64, dp, C32, bmax, part, st))) return c.err;
     if (!c.ok(sum_partials(part, ntile, red + 4, st))) return c.err;
     if (!c.ok(max_pow2(bmax, ntile, fs + 2, st))) return c.err;
@@ -477,8 +542,14 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     if (!c.ok(tc(Rlp, Clp, 0, 0, TC_EPI_STORE_F32, P32))) return c.err;
     if (!c.ok(newton_direction(P32, dp, fs + 3, in.alpha, E32, bmax, st))) return c.err;
     if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return c.err;
-    if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 6, st))) return c.err;  // ||E_0||_2
-    c.launches += 2 * kPowerIters - 1;
+    // ||E_0||_2 on the side stream, beside the tangent products (tensor-bound,
+    // with HBM and SM slots to spare): a copy first, since the tangent steps
+    // update E in place
+    RS_TRY(cudaMemcpyAsync(Q32, E32, dd * 4, cudaMemcpyDeviceToDevice, st));
+    RS_TRY(cudaEventRecord(side.ev[0], st));
+    RS_TRY(cudaStreamWaitEvent(side.s, side.ev[0], 0));
+    if (!c.ok(spectral_norm_f32(Q32, dp, pv, pw, kPowerIters, red + 6, side.s))) return c.err;  // ||E_0||_2
+    c.launches += 2 * kPowerIters;
     // tangent recursion along the stored iterates
     for (int m = 0; m < in.M; ++m) {
       if (!c.ok(scale_to_lp(E32, dd, fs + 5, Elp, in.fmt, st))) return c.err;
@@ -494,11 +565,17 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       if (!c.ok(tc_gemm(tg, Qlp, 1, in.X[m], 1, in.fmt, c.num_sms, st))) return c.err;
       if (!c.ok(max_pow2(bmax, tc_num_tiles(dp, 1) * 4, fs + 4, st))) return c.err;
     }
-    if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 7, st))) return c.err;
-    c.launches += 2 * kPowerIters - 1;
+    // ||E||_2 on the side stream (after ||E_0||_2 there), beside the
+    // correction and the polish, which only read E
+    RS_TRY(cudaEventRecord(side.ev[1], st));
+    RS_TRY(cudaStreamWaitEvent(side.s, side.ev[1], 0));
+    if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 7, side.s))) return c.err;
+    RS_TRY(cudaEventRecord(side.ev[2], side.s));
+    c.launches += 2 * kPowerIters;
     if (!c.ok(add_correction(in.R64, E32, dp, d, part, st))) return c.err;
     if (!c.ok(sum_partials(part, 1024, red + 2, st))) return c.err;
     RS_TRY(polish());
+    RS_TRY(cudaStreamWaitEvent(st, side.ev[2], 0));  // join before E and red are reused
     RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
     RS_TRY(cudaStreamSynchronize(st));
     o->sweeps = sw + 1;
@@ -1468,6 +1545,12 @@ int32_t rsign_dbg_set_refine_levels(int32_t polish, int32_t ra_first, int32_t ra
   if (ok(polish)) g_levels_polish = polish;
   if (ok(ra_first)) g_levels_ra0 = ra_first;
   if (ok(ra_later)) g_levels_ra = ra_later;
+  return prev;
+}
+
+int32_t rsign_dbg_set_ozaki_tile(int32_t bn) {
+  const int prev = g_oz_tile;
+  if (bn == 0 || bn == 128 || bn == 256) g_oz_tile = bn;
   return prev;
 }
 

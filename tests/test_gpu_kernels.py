@@ -208,3 +208,25 @@ def test_commutator_check_matches_fp64_power_steps(d, dp):
     assert a11 == pytest.approx(float(v_prev @ (A @ v_prev)), rel=1e-6, abs=1e-9)
     assert a12 == pytest.approx(float(v @ (A @ v_prev)), rel=1e-6, abs=1e-9)
     assert a22 == pytest.approx(float(v @ (A @ v)), rel=1e-6, abs=1e-9)
+
+
+@pytest.mark.parametrize("d,k", [(1024, 16), (1280, 640)])
+def test_refinement_products_same_bits_on_both_tile_widths(d, k):
+    # the FP64-grade products are exact integer level sums converted once, so
+    # the 128-wide (int64 sums in TMEM) and 256-wide (cluster pairs, sums in
+    # global memory) launches give the same reflector bit for bit
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    import workloads
+    H, lam, Q = workloads.controlled_spectrum_torch(d, k, 1e-2, seed=d + k)
+    outs = []
+    prev = rs.dbg_set_ozaki_tile(256)
+    try:
+        for bn in (256, 128):
+            rs.dbg_set_ozaki_tile(bn)
+            R, info, st = rs.reflector(H, k, 0.0, tol=1e-6, policy=rs.Policy.FP16_REFINE, check=False)
+            assert st == rs.Status.OK
+            outs.append(R.clone())
+    finally:
+        rs.dbg_set_ozaki_tile(prev)
+    assert torch.equal(outs[0], outs[1])
