@@ -536,6 +536,48 @@ __global__ void split_f32_kernel(const double* __restrict__ src, size_t n, float
   }
 }
 
+// The step's two normalisations in one launch: block 0 takes w = a0 - b0
+// (C v), block 1 w = a1 - b1 (N z); each writes v = w / ||w|| in FP64 and as
+// hi + lo FP32 pairs and *out = ||w||.  w is formed twice (for the norm and
+// for v) instead of being stored.
+struct DiffNormJob {
+  const double* a;
+  const double* b;
+  double* v;
+  float* vhi;
+  float* vlo;
+  double* out;
+};
+__global__ void diff_normalize2_kernel(DiffNormJob j0, DiffNormJob j1, int n) {
+  const DiffNormJob& J = blockIdx.x == 0 ? j0 : j1;
+  __shared__ double sh[32];
+  __shared__ double inv_sh;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double w = J.a[i] - J.b[i];
+    s = fma(w, w, s);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += sh[q];
+    const double nw = sqrt(tot);
+    inv_sh = nw > 0.0 ? 1.0 / nw : 0.0;
+    *J.out = nw;
+  }
+  __syncthreads();
+  const double inv = inv_sh;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = (J.a[i] - J.b[i]) * inv;
+    J.v[i] = x;
+    const float h = __double2float_rn(x);
+    J.vhi[i] = h;
+    J.vlo[i] = __double2float_rn(x - (double)h);
+  }
+}
+
 // v = w / ||w|| in FP64 and as hi + lo FP32 pairs; *out = ||w|| (one block)
 __global__ void normalize_split_kernel(const double* __restrict__ w, int n, double* __restrict__ v,
                                        float* __restrict__ vhi, float* __restrict__ vlo, double* out) {
@@ -592,16 +634,6 @@ __global__ void dot3_kernel(const double* __restrict__ a, const double* __restri
     double t = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[threadIdx.x][q];
     out[threadIdx.x] = t;
-  }
-}
-
-// c = a - b and f = e - g (two differences in one pass)
-__global__ void diff2_kernel(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c,
-                             const double* __restrict__ e, const double* __restrict__ g, double* __restrict__ f,
-                             int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    c[i] = a[i] - b[i];
-    f[i] = e[i] - g[i];
   }
 }
 
@@ -899,9 +931,10 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
     p2.job[0] = GemvDfJob{R_hi, R_lo, t1h, t1l, t3h, t3l, y1, nullptr, nullptr, y3, nullptr, nullptr};
     p2.job[1] = GemvDfJob{A_hi, A_lo, t2h, t2l, nullptr, nullptr, y2, nullptr, nullptr, nullptr, nullptr, nullptr};
     gemv_df_kernel<<<blocks2, 256, 0, st>>>(p2);  // R A v, R R z; A R v
-    diff2_kernel<<<(dp + 255) / 256, 256, 0, st>>>(y1, y2, w, y3, z, w3, dp);  // C v, N z
-    normalize_split_kernel<<<1, 1024, 0, st>>>(w, dp, vb[nxt], vbh[nxt], vbl[nxt], out);  // ||C v||
-    normalize_split_kernel<<<1, 1024, 0, st>>>(w3, dp, z, zh, zl, out + 1);               // ||N z||
+    // v <- C v / ||C v|| (C v = R A v - A R v), z <- N z / ||N z|| (N z = R R z - z)
+    diff_normalize2_kernel<<<2, 1024, 0, st>>>(DiffNormJob{y1, y2, vb[nxt], vbh[nxt], vbl[nxt], out},
+                                               DiffNormJob{y3, z, w3, zh, zl, out + 1}, dp);
+    std::swap(z, w3);
   }
   // Rayleigh-Ritz on the last plane {v_prev, v_last = C v_prev / ||C v_prev||}
   // (orthonormal: v^T C v = 0 for the antisymmetric C): the entries of the
