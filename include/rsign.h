@@ -115,7 +115,8 @@ typedef struct {
   double lam_k_est;        /* Lanczos estimate of lam_k                                */
   double lam_k1_est;       /* Lanczos estimate of lam_{k+1}                            */
   double shift_eps;        /* endpoint error bound eps (largest Ritz residual bound plus a
-                              rounding allowance 16 sqrt(d) u ||T||)                    */
+                              rounding allowance 16 sqrt(d) u ||T||, u = 2^-46 the unit
+                              of the double-float products A v)                         */
   double margin_lb;        /* guaranteed margin m_hat - eps of the chosen shift        */
   int32_t lanczos_iters;   /* Lanczos steps taken                                      */
   int32_t steps_pred;      /* NS steps the scalar recurrence predicts for eps_m(gamma) <= tol,

@@ -378,49 +378,6 @@ __global__ void to_f64_kernel(const T* __restrict__ src, size_t n, double* __res
   }
 }
 
-// y = A x (FP64)
-__global__ void gemv_kernel(const double* __restrict__ A, int dp, const double* __restrict__ x,
-                            double* __restrict__ y) {
-  // one warp per row; eight 16-byte loads in flight per lane (a GEMV is
-  // latency-bound per warp), the matrix streamed past L1 (__ldcs), x cached
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= dp) return;
-  const double2* a = reinterpret_cast<const double2*>(A + (size_t)row * dp);
-  const double2* xv = reinterpret_cast<const double2*>(x);
-  double s0 = 0.0, s1 = 0.0;
-  const int n2 = dp >> 1;  // a multiple of 128: full chunks of 256, then at most one of 128
-  int j = lane;
-  for (; j + 224 < n2; j += 256) {
-    double2 av[8], bv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      av[u] = __ldcs(a + j + 32 * u);
-      bv[u] = xv[j + 32 * u];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      s0 = fma(av[u].x, bv[u].x, s0);
-      s1 = fma(av[u].y, bv[u].y, s1);
-    }
-  }
-  if (j < n2) {
-    double2 av[4], bv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      av[u] = __ldcs(a + j + 32 * u);
-      bv[u] = xv[j + 32 * u];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      s0 = fma(av[u].x, bv[u].x, s0);
-      s1 = fma(av[u].y, bv[u].y, s1);
-    }
-  }
-  double s = warp_sum(s0 + s1);
-  if (lane == 0) y[row] = s;
-}
-
 __global__ void normalize_kernel(double* y, int n, double* x, double* nrm) {
   __shared__ double sh[32];
   double s = 0.0;
@@ -612,11 +569,6 @@ cudaError_t ns_check(const double* partials, int n, double* hist, int m, double 
 
 cudaError_t trace_f64(const double* X, int dp, int d, double* out, cudaStream_t st) {
   trace_kernel<<<1, 1024, 0, st>>>(X, dp, d, out);
-  return cudaGetLastError();
-}
-
-cudaError_t gemv_f64(const double* A, int dp, const double* x, double* y, cudaStream_t st) {
-  gemv_kernel<<<(dp + 7) / 8, 256, 0, st>>>(A, dp, x, y);
   return cudaGetLastError();
 }
 

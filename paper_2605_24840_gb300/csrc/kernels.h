@@ -209,8 +209,6 @@ cudaError_t row_sumsq(const void* x, int fmt, int split, int dp, int d, float* o
                       cudaStream_t st);
 // Deterministic sum of n partials -> out[0]; out[1] = sqrt(out[0]) when sqrt_out.
 cudaError_t sum_partials(const double* partials, int n, double* out, cudaStream_t st);
-// y = A x for dp x dp FP64 A (row-major), x,y length dp.
-cudaError_t gemv_f64(const double* A, int dp, const double* x, double* y, cudaStream_t st);
 // Copy the leading d x d block of src (ld dp) into dst (ld d), and back
 // (copy_pad writes the whole dp x dp destination, zeros outside d x d).
 cudaError_t copy_unpad(const double* src, int dp, double* dst, int d, cudaStream_t st);
@@ -376,9 +374,13 @@ cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int it
 cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, int k_host, const double* kref,
                       cudaStream_t st);
 // y = M x in double-float arithmetic (M, x as hi + lo FP32 pairs; dp a
-// multiple of 256), y in FP64.
+// multiple of 256), y in FP64; with kref, M is the split of M0 2^e (e the
+// exponent of *kref) and y = M0 x (the result is scaled back by 2^-e).
 cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y, int dp,
-                    cudaStream_t st);
+                    cudaStream_t st, const double* kref = nullptr);
+// *out = 1 / max_i |x_i| (1 when that is 0 or not finite), a device scalar
+// for split_f32's kref; bits: one device word of scratch.
+cudaError_t inv_maxabs(const double* x, size_t n, unsigned long long* bits, double* out, cudaStream_t st);
 // Matrix-free estimate of ||G||_2, G = 1/2 R C, C = R A - A R: power steps on
 // the antisymmetric C, v -> R (A v) - A (R v), and in the same passes power
 // steps on N = R^2 - I.  The matrix-vector products run on the FP32 pipe in

@@ -2,8 +2,9 @@
 // lam_k, lam_{k+1} by a partial eigensolver, take the midpoint of Prop. 4.1 and
 // check admissibility with the margin test of Prop. 4.2).
 //
-// Lanczos on A = sym(H) (FP64, full reorthogonalisation by two classical
-// Gram-Schmidt passes, vectors kept on the device) from whichever end of the
+// Lanczos on A = sym(H) (FP64 vectors, full reorthogonalisation by two
+// classical Gram-Schmidt passes, vectors kept on the device; the products A v
+// in double-float arithmetic, ~2^-46 per term) from whichever end of the
 // spectrum is closer to the target index; the tridiagonal T_m is solved on
 // the host by Sturm-sequence bisection (eigenvalues) and inverse iteration
 // (the last eigenvector components, which give the residual bounds
@@ -159,8 +160,20 @@ cudaError_t lanczos_endpoints(const double* A, int dp, int d, int k, int max_ite
   double* al = c + (m_cap + 1);                   // alpha_j
   double* be = al + (m_cap + 1);                  // beta_j (norms)
   double* tmp = be + (m_cap + 1);                 // [dp]
+  // A v in double-float arithmetic on the FP32 pipe (GB300's FP64 pipe bounds
+  // an FP64 GEMV): A 2^e split once into hi + lo planes, 2^e ~ 1/max|A|,
+  // from a 256-byte boundary (the GEMV reads these rows with 16-byte loads)
+  float* a_hi = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tmp + dp) + 255) & ~(uintptr_t)255);  // [dp][dp]
+  float* a_lo = a_hi + (size_t)dp * dp;              // [dp][dp]
+  float* v_hi = a_lo + (size_t)dp * dp;              // [dp]
+  float* v_lo = v_hi + dp;                           // [dp]
+  double* kscale = reinterpret_cast<double*>(v_lo + dp);
+  unsigned long long* kbits = reinterpret_cast<unsigned long long*>(kscale + 1);
   cudaError_t e;
   int64_t nl = 0;
+  if ((e = inv_maxabs(A, (size_t)dp * dp, kbits, kscale, st)) != cudaSuccess) return e;
+  if ((e = split_f32(A, (size_t)dp * dp, a_hi, a_lo, 0, kscale, st)) != cudaSuccess) return e;
+  nl += 3;
   start_vec_kernel<<<(dp + 255) / 256, 256, 0, st>>>(tmp, d, dp);
   e = normalize(tmp, dp, V, be + m_cap, st);  // V_0
   nl += 2;
@@ -171,8 +184,9 @@ cudaError_t lanczos_endpoints(const double* A, int dp, int d, int k, int max_ite
   int next_check = std::min(m_cap, std::max(2 * (kk + 1) + 40, 60));
   for (int j = 0; j < m_cap; ++j) {
     // w = A v_j
-    if ((e = gemv_f64(A, dp, V + (size_t)j * dp, w, st)) != cudaSuccess) return e;
-    ++nl;
+    if ((e = split_f32(V + (size_t)j * dp, dp, v_hi, v_lo, 0, nullptr, st)) != cudaSuccess) return e;
+    if ((e = gemv_df(a_hi, a_lo, v_hi, v_lo, w, dp, st, kscale)) != cudaSuccess) return e;
+    nl += 2;
     // two passes of classical Gram-Schmidt against V_0..V_j; the coefficient on
     // V_j is alpha_j = v_j^T A v_j
     cudaMemsetAsync(al + j, 0, sizeof(double), st);
@@ -207,13 +221,14 @@ cudaError_t lanczos_endpoints(const double* A, int dp, int d, int k, int max_ite
         out->lam_k = th[0];
         out->lam_k1 = th[1];
         // residual bounds |beta_m s_m| (exact arithmetic) plus a rounding
-        // allowance 16 sqrt(d) u ||T||, ||T|| <= its Gershgorin bound: without it
-        // a converged Krylov space (beta_m ~ 0) would claim to resolve gaps below
-        // the FP64 resolution of the eigenvalues
+        // allowance 16 sqrt(d) u ||T||, ||T|| <= its Gershgorin bound, with u =
+        // 2^-46 the unit of the double-float products: without it a converged
+        // Krylov space (beta_m ~ 0) would claim to resolve gaps below the
+        // resolution of the eigenvalues
         double tn = 0.0;
         for (int i = 0; i < m; ++i)
           tn = std::max(tn, std::fabs(a[i]) + (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0));
-        const double floor_r = 16.0 * std::sqrt((double)d) * 1.1102230246251565e-16 * tn;
+        const double floor_r = 16.0 * std::sqrt((double)d) * std::ldexp(1.0, -46) * tn;
         out->eps_k = std::fabs(hb[m - 1] * lc[0]) + floor_r;
         out->eps_k1 = std::fabs(hb[m - 1] * lc[1]) + floor_r;
         // The pair's indices k, k+1 count the Ritz values between it and the
@@ -248,7 +263,9 @@ cudaError_t lanczos_endpoints(const double* A, int dp, int d, int k, int max_ite
 
 size_t lanczos_work_doubles(int dp, int max_iter) {
   const int m_cap = std::min(max_iter, 1024);
-  return (size_t)(m_cap + 1) * dp + dp + 3 * (size_t)(m_cap + 1) + dp + 64;
+  // V, w, c / alpha / beta, tmp; then the split A (2 dp^2 floats), the split
+  // vector (2 dp floats) and two scalars
+  return (size_t)(m_cap + 1) * dp + dp + 3 * (size_t)(m_cap + 1) + dp + (size_t)dp * dp + dp + 64;
 }
 
 }  // namespace rsign

@@ -422,6 +422,7 @@ struct GemvDfArgs {
   GemvDfJob job[2];
   int n_jobs;
   int dp;
+  const double* kref;  // nullable: outputs scaled by 2^-e, e the exponent of *kref
 };
 
 // s + c += (ah + al)(xh + xl): the product ah xh split exactly into p + e by
@@ -440,7 +441,7 @@ __device__ __forceinline__ void df_acc(float& s, float& c, float ah, float al, f
 }
 
 template <bool TWO>
-__device__ __forceinline__ void gemv_df_row(const GemvDfJob& J, int r, int dp, int lane) {
+__device__ __forceinline__ void gemv_df_row(const GemvDfJob& J, int r, int dp, int lane, int kout) {
   const float4* mh = reinterpret_cast<const float4*>(J.mhi + (size_t)r * dp);
   const float4* ml = reinterpret_cast<const float4*>(J.mlo + (size_t)r * dp);
   const float4* xh = reinterpret_cast<const float4*>(J.xhi);
@@ -489,6 +490,10 @@ __device__ __forceinline__ void gemv_df_row(const GemvDfJob& J, int r, int dp, i
   }
   t = warp_sum(t);
   if (TWO) tb = warp_sum(tb);
+  if (kout != 0) {  // exact power-of-two rescaling
+    t = ldexp(t, kout);
+    if (TWO) tb = ldexp(tb, kout);
+  }
   if (lane == 0) {
     J.y[r] = t;
     if (J.yhi != nullptr) {
@@ -515,8 +520,9 @@ __global__ void gemv_df_kernel(const GemvDfArgs a) {
   const int jb = gw >= a.dp ? 1 : 0;
   const int r = gw - jb * a.dp;
   const GemvDfJob& J = a.job[jb];
-  if (J.xbhi != nullptr) gemv_df_row<true>(J, r, a.dp, lane);
-  else gemv_df_row<false>(J, r, a.dp, lane);
+  const int kout = a.kref != nullptr ? -ic_exponent(a.kref[0]) : 0;
+  if (J.xbhi != nullptr) gemv_df_row<true>(J, r, a.dp, lane, kout);
+  else gemv_df_row<false>(J, r, a.dp, lane, kout);
 }
 
 // hi + lo = src 2^k (k = k_host, plus the exponent of *kref when given), by
@@ -575,6 +581,30 @@ __global__ void diff_normalize2_kernel(DiffNormJob j0, DiffNormJob j1, int n) {
     const float h = __double2float_rn(x);
     J.vhi[i] = h;
     J.vlo[i] = __double2float_rn(x - (double)h);
+  }
+}
+
+// *bits = max |x_i| as the bit pattern of a non-negative double (which orders
+// like an unsigned integer), by integer operations
+__global__ void maxabs_bits_kernel(const double* __restrict__ x, size_t n, unsigned long long* bits) {
+  unsigned long long m = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = ic_bits(x[i]) & 0x7FFFFFFFFFFFFFFFull;
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(bits, m);
+}
+
+// *out = 1 / max (1 when the maximum is 0 or not finite)
+__global__ void inv_of_bits_kernel(const unsigned long long* bits, double* out) {
+  if (threadIdx.x == 0) {
+    const double m = ic_double(*bits);
+    *out = (m > 0.0 && m < 1.0e300) ? 1.0 / m : 1.0;
   }
 }
 
@@ -867,12 +897,21 @@ cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int it
 }
 
 cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y, int dp,
-                    cudaStream_t st) {
+                    cudaStream_t st, const double* kref) {
   GemvDfArgs a{};
   a.n_jobs = 1;
   a.dp = dp;
+  a.kref = kref;
   a.job[0] = GemvDfJob{M_hi, M_lo, x_hi, x_lo, nullptr, nullptr, y, nullptr, nullptr, nullptr, nullptr, nullptr};
   gemv_df_kernel<<<(dp + 7) / 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t inv_maxabs(const double* x, size_t n, unsigned long long* bits, double* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  maxabs_bits_kernel<<<grid_for(n), 256, 0, st>>>(x, n, bits);
+  inv_of_bits_kernel<<<1, 32, 0, st>>>(bits, out);
   return cudaGetLastError();
 }
 
