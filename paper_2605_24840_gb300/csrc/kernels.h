@@ -113,6 +113,8 @@ struct TcGemmArgs {
   const float* tg_sigma;   // device scalar sigma
   float tg_a;              // step scaling a (1 = plain)
   float* tg_max;           // 4 per tile
+  void* tg_Elp;            // nullable: also store the new E times tg_sigma in the operand
+                           // type (both triangles), the next step's operand
   // scaled Newton-Schulz step X+ = 1/2 a X (3I - a^2 X^2): TC_EPI_NS_SYRK stores
   // E = I - ns_c2 X^2 (ns_c2 = a^2), TC_EPI_NS_UPDATE stores ns_c1 (X + 1/2 X E)
   // (ns_c1 = a); 0 means 1 (the plain step)

@@ -555,9 +555,13 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     RS_TRY(cudaStreamWaitEvent(side.s, side.ev[0], 0));
     if (!c.ok(spectral_norm_f32(Q32, dp, pv, pw, kPowerIters, red + 6, side.s))) return c.err;  // ||E_0||_2
     c.launches += 2 * kPowerIters;
-    // tangent recursion along the stored iterates
+    // tangent recursion along the stored iterates.  The operand scale sigma
+    // (fs[5], a power of two with |E_0| sigma <= 1) stays fixed along the
+    // recursion: E grows by at most ~2.6 per step, well inside the FP16 range
+    // (FP16's relative precision does not depend on the scale), so each
+    // step's epilogue writes the next step's operand directly.
+    if (!c.ok(scale_to_lp(E32, dd, fs + 5, Elp, in.fmt, st))) return c.err;
     for (int m = 0; m < in.M; ++m) {
-      if (!c.ok(scale_to_lp(E32, dd, fs + 5, Elp, in.fmt, st))) return c.err;
       if (!c.ok(tc(Elp, in.Et[m], in.fmt, 0, TC_EPI_STORE_F32, P32))) return c.err;   // E Et
       if (!c.ok(tc(in.X[m], Elp, in.fmt, 0, TC_EPI_STORE_LP, Qlp))) return c.err;     // X E
       // (X E) X with the tangent step fused into its epilogue (E updated in place)
@@ -567,8 +571,8 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       tg.group_scale[0] = 1.0; tg.scale = 1.0f; tg.status = status;
       tg.tg_E = E32; tg.tg_P = P32; tg.tg_sigma = fs + 5; tg.tg_max = bmax;
       tg.tg_a = (in.a != nullptr && m < in.n_a) ? (float)in.a[m] : 1.0f;
+      tg.tg_Elp = (m + 1 < in.M) ? Elp : nullptr;
       if (!c.ok(tc_gemm(tg, Qlp, 1, in.X[m], 1, in.fmt, c.num_sms, st))) return c.err;
-      if (!c.ok(max_pow2(bmax, tc_num_tiles(dp, 1) * 4, fs + 4, st))) return c.err;
     }
     // ||E||_2 on the side stream (after ||E_0||_2 there), beside the
     // correction and the polish, which only read E

@@ -378,10 +378,23 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
     float4* d4 = reinterpret_cast<float4*>(E + row + j0);
 #pragma unroll
     for (int q = 0; q < 8; ++q) d4[q] = make_float4(vn[4 * q], vn[4 * q + 1], vn[4 * q + 2], vn[4 * q + 3]);
+    // the next step's operand, E sigma in the operand type (nothing in this
+    // launch reads it), stored in the same order as E: rows, then mirrors
+    T* el = reinterpret_cast<T*>(a.tg_Elp);
+    const float sg = el != nullptr ? a.tg_sigma[0] : 0.0f;
+    if (el != nullptr) {
+      float vs[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) vs[jj] = vn[jj] * sg;
+      store32_lp<T>(el + row + j0, vs);
+    }
     if (!above) __syncwarp();
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj)
-      if (above || j0 + jj > i) E[(size_t)(j0 + jj) * ld + i] = vn[jj];
+      if (above || j0 + jj > i) {
+        E[(size_t)(j0 + jj) * ld + i] = vn[jj];
+        if (el != nullptr) el[(size_t)(j0 + jj) * ld + i] = from_f32<T>(vn[jj] * sg);
+      }
   } else {  // TC_EPI_OZAKI
     // The group sums are exact integers (< 2^24).  They are combined as
     // int64 fixed-point values V = sum_g acc_g 2^(group_shift[g]) (one per
