@@ -52,9 +52,10 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 Newton-Schulz comparator")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--engine", default="scaled", choices=["plain", "scaled"],
+    p.add_argument("--engine", default="scaled", choices=["plain", "scaled", "ns5"],
                    help="plain: Eq. NS steps; scaled: the stable step scalings from the margin of the "
-                        "midpoint shift (the half-gap), then plain steps")
+                        "midpoint shift (the half-gap), then plain steps; ns5: the quintic filter "
+                        "1/8 X (15I - 10X^2 + 3X^4) (not with REFINE policies)")
     p.add_argument("--workload", default="dense", choices=["dense", "batched"],
                    help="dense: the d=8192 headline; batched: 512 matrices of order 32..512 through the "
                         "grouped launches, against a per-matrix call loop")
@@ -234,8 +235,9 @@ def workload_config(args):
             "d": args.d, "k": args.k, "delta": args.delta, "theta": args.theta, "policy": args.policy,
             "tol": args.tol,
             "alpha": "1/(1.02 rho_est), 20 power steps" if args.alpha == "power" else "1/||H-sI||_inf",
-            "engine": ("scaled Newton-Schulz steps from the gap margin, then plain" if args.engine == "scaled"
-                       else "plain Newton-Schulz (Eq. NS)"),
+            "engine": {"scaled": "scaled Newton-Schulz steps from the gap margin, then plain",
+                       "plain": "plain Newton-Schulz (Eq. NS)",
+                       "ns5": "quintic Newton-Schulz filter (three products per step)"}[args.engine],
             "parallelism": "replicas",
             "l2": "inputs larger than L2 (H = 8 d^2 bytes)"}
 
@@ -262,7 +264,8 @@ def run_rsign(args):
     R = torch.empty_like(H)
     margin = float(min(s - lam_h[args.k - 1], lam_h[args.k] - s))
     opt = rs.default_options(alpha_mode=int(rs.AlphaMode.POWER if args.alpha == "power" else rs.AlphaMode.INF),
-                             ns_scaling=1 if args.engine == "scaled" else 0, margin=margin)
+                             ns_scaling=1 if args.engine == "scaled" else 0, margin=margin,
+                             engine=int(rs.Engine.NS5 if args.engine == "ns5" else rs.Engine.NS3))
     stream = torch.cuda.current_stream(dev)
 
     def call(Hin, Rout, pol=policy, tol=args.tol):
@@ -317,7 +320,7 @@ def run_rsign(args):
     # symmetric product X (I - X^2)); duration from the library's CUDA events
     pk, pk_kind = peaks()
     ms_low = statistics.mean(i.ms_low for i, _ in infos)
-    launches_low = 2 * info.steps_low + 1
+    launches_low = (3 if args.engine == "ns5" else 2) * info.steps_low + 1
     avg_launch_ms = ms_low / launches_low
     flops_per_launch = float(args.d) ** 3
     achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12

@@ -180,8 +180,22 @@ typedef struct {
                                commutator by the whole gap 2 mu, so broadband rounding
                                noise in R (large eigenvalue differences) inflates it:
                                it can stay above tol at errors far below tol           */
-  int32_t reserved_opt;
+  int32_t engine;           /* rsign_engine (default RSIGN_ENGINE_NS3)                   */
 } rsign_options;
+
+/* Polynomial sign engines (rsign_options.engine), Sec. 3.4 / Sec. 5.4 on higher-degree odd
+ * filters.  Both are fixed points of sign with X_0 = alpha (H - sI), alpha <= 1/rho. */
+typedef enum {
+  RSIGN_ENGINE_NS3 = 0,   /* Eq. NS: X <- 1/2 X (3I - X^2), two products per step (and the
+                             scaled variant of rsign_options.ns_scaling)                   */
+  RSIGN_ENGINE_NS5 = 1    /* the quintic X <- 1/8 X (15I - 10X^2 + 3X^4), in update form
+                             X + 1/2 X W with E = I - X^2, W = E + 3/4 E^2: three products
+                             per step, cubic convergence near +-1, growth 15/8 near 0.
+                             FP64, FP16, BF16, FP32 and *_POLISH policies (the polish steps
+                             stay Eq. NS; no scaled variant); REFINE policies and batched
+                             calls: RSIGN_ERR_ARG; rsign_reflector_backward differentiates
+                             the NS3 map                                                    */
+} rsign_engine;
 
 /* Stop tests of the refinement sweeps (rsign_options.refine_stop). */
 typedef enum {

@@ -17,7 +17,8 @@ passage of the paper it restates:
     margin (Prop. 4.2);
   * alpha = 1/||A||_inf (Sec. 4.3 scaling discussion);
   * the Daleckii-Krein derivative of sign (used to check the adjoint);
-  * the commutator error bound of a refined reflector (Sylvester argument).
+  * the commutator error bound of a refined reflector (Sylvester argument);
+  * the quintic Newton-Schulz filter and its iterates (Sec. 5.4 reading).
 
 Pins: every function here is checked in ``tests/test_oracle_pins.py`` against
 closed forms, library routines, brute force on tiny inputs and hand-derived
@@ -264,6 +265,32 @@ def scaled_ns_map(x, a: float):
     """The scalar scaled step g(x) = 1/2 a x (3 - a^2 x^2)."""
     x = np.asarray(x, dtype=np.float64)
     return 0.5 * a * x * (3.0 - a * a * x * x)
+
+
+def ns5_map(x):
+    """The quintic odd filter q(x) = x (15 - 10 x^2 + 3 x^4) / 8: the degree-5
+    member of the Newton-Schulz family (a higher-degree odd polynomial filter
+    of the kind Sec. 5.4 points to).  q(1) = 1, q'(x) = 15/8 (1 - x^2)^2, so
+    q is increasing on [0, 1], fixes +-1 with q'(1) = q''(1) = 0 (cubic
+    convergence), and grows small x by 15/8."""
+    x = np.asarray(x, dtype=np.float64)
+    x2 = x * x
+    return x * (15.0 - 10.0 * x2 + 3.0 * x2 * x2) / 8.0
+
+
+def ns5_iterates(X0: np.ndarray, steps: int):
+    """X_0..X_steps of X <- 1/8 X (15I - 10X^2 + 3X^4), formed as written
+    (matrix products by the oracle's plain triple loop)."""
+    X = _c(X0).copy()
+    out = [X]
+    d = X.shape[0]
+    eye = np.eye(d)
+    for _ in range(steps):
+        X2 = matmul(X, X)
+        X4 = matmul(X2, X2)
+        X = matmul(X, 15.0 * eye - 10.0 * X2 + 3.0 * X4) / 8.0
+        out.append(X)
+    return out
 
 
 def scaled_ns_iterates(X0: np.ndarray, coeffs, steps: int):

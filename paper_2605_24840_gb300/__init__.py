@@ -81,8 +81,13 @@ class Options(ctypes.Structure):
         ("low_split", ctypes.c_int32), ("lanczos_max", ctypes.c_int32),
         ("batch_graphs", ctypes.c_int32), ("batch_tile", ctypes.c_int32),
         ("ns_scaling", ctypes.c_int32), ("margin", ctypes.c_double),
-        ("refine_stop", ctypes.c_int32), ("reserved_opt", ctypes.c_int32),
+        ("refine_stop", ctypes.c_int32), ("engine", ctypes.c_int32),
     ]
+
+
+class Engine(enum.IntEnum):
+    NS3 = 0
+    NS5 = 1
 
 
 class RefineStop(enum.IntEnum):

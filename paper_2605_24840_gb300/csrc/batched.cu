@@ -303,6 +303,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
   if ((int)policy < RSIGN_FP64 || (int)policy > RSIGN_FP32) return RSIGN_ERR_ARG;
   if (opt.max_steps < 1 || opt.max_steps > 1000 || opt.polish_steps < 0) return RSIGN_ERR_ARG;
   if (opt.batch_tile != 0 && opt.batch_tile != 128 && opt.batch_tile != 256) return RSIGN_ERR_ARG;
+  if (opt.engine != RSIGN_ENGINE_NS3) return RSIGN_ERR_ARG;  // the grouped launches run Eq. NS
   if (n == 0) return RSIGN_OK;
   std::vector<rsign_status> stat(n, RSIGN_OK);
   if (infos) std::memset(infos, 0, sizeof(rsign_info) * (size_t)n);

@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(128) f64_gemm_kernel(const F64GemmArgs a) {
           v = real ? ((i == j ? 1.0 : 0.0) - v) : 0.0;
           if (real && (!a.sym || j >= i)) part += ((a.sym && j > i) ? 2.0 : 1.0) * v * v;
         } else {  // F64_EPI_NS_UPDATE
+          if (a.scale != 0.0 && a.scale != 1.0) v *= a.scale;  // X_in + 1/2 scale acc
           v = xinp[(size_t)i * ld + j] + 0.5 * v;
           if (a.ns_c1 != 0.0 && a.ns_c1 != 1.0) v *= a.ns_c1;  // X+ = a (X + 1/2 X E)
           if (i == j && i < d_real) part += v;

@@ -40,7 +40,7 @@ enum TcEpi : int {
   TC_EPI_STORE_F32 = 0,  // out_f32 = scale * acc
   TC_EPI_STORE_LP = 1,   // out_lp  = scale * acc (rounded to the operand type)
   TC_EPI_NS_SYRK = 2,    // acc = X^2: out_lp = I - acc (masked to d), residual partials
-  TC_EPI_NS_UPDATE = 3,  // acc = X E: out_lp = X_in + 1/2 acc, trace partials
+  TC_EPI_NS_UPDATE = 3,  // acc = X E: out_lp = X_in + 1/2 scale acc, trace partials
   TC_EPI_OZAKI = 4,      // out_f64 (+)= rs_i cs_j group_scale_g acc (exact integer groups)
   TC_EPI_TANGENT = 5,    // acc = sigma X E X (symmetric): the tangent step of the refinement,
                          // E <- a (1/2 E + inv (P + P^T)) - a^3 inv acc, inv = 1/(2 sigma),
@@ -155,7 +155,7 @@ void tc_build_units(int n, const int* dp, int bn, int sym, int order, std::vecto
 enum F64Epi : int {
   F64_EPI_STORE = 0,      // out = scale * acc
   F64_EPI_NS_SYRK = 1,    // acc = X^2: out = I - acc (masked to d), residual partials
-  F64_EPI_NS_UPDATE = 2,  // acc = X E: out = X_in + 1/2 acc, trace partials
+  F64_EPI_NS_UPDATE = 2,  // acc = X E: out = X_in + 1/2 scale acc (scale 0 = 1), trace partials
 };
 
 struct F64GemmArgs {

@@ -134,6 +134,7 @@ struct F64Loop {
   double* hist;
   int* done;
   int* steps;
+  double* W = nullptr;  // NS5 engine: W = E + 3/4 E^2 (nullptr: Eq. NS)
 };
 
 bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_steps, Ctl* ctl_dev,
@@ -154,9 +155,18 @@ bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_ste
       if (!c.ok(ns_check(L.partials, nt * 4, L.hist, mm, tol_abs, -1.0, -1.0, 0.0, L.done, L.steps, c.st)))
         return false;
       if (mm == max_steps) break;  // residual of the last iterate only
+      if (L.W != nullptr) {
+        // NS5: W = E + 3/4 E^2 (the update epilogue with scale 3/2 on E E),
+        // then X+ = X + 1/2 X W = 1/8 X (15I - 10X^2 + 3X^4)
+        F64GemmArgs w{};
+        w.dp = dp; w.d_real = d; w.sym = 1; w.epi = F64_EPI_NS_UPDATE; w.scale = 1.5;
+        w.A = L.E; w.B = L.E; w.xin = L.E; w.out = L.W; w.partials = L.partials; w.skip = L.done;
+        if (!c.ok(f64_gemm(w, c.st))) return false;
+      }
       F64GemmArgs up{};
       up.dp = dp; up.d_real = d; up.sym = 1; up.epi = F64_EPI_NS_UPDATE;
-      up.A = L.xb[mm & 1]; up.B = L.E; up.xin = L.xb[mm & 1]; up.out = L.xb[(mm + 1) & 1];
+      up.A = L.xb[mm & 1]; up.B = L.W != nullptr ? L.W : L.E; up.xin = L.xb[mm & 1];
+      up.out = L.xb[(mm + 1) & 1];
       up.partials = L.partials; up.skip = L.done;
       up.ns_c1 = am;
       if (!c.ok(f64_gemm(up, c.st))) return false;
@@ -614,6 +624,9 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   const bool auto_shift = std::isnan(s);
   const bool refine = policy == RSIGN_FP16_REFINE || policy == RSIGN_BF16_REFINE;
   if (opt.refine_stop != RSIGN_STOP_ESTIMATE && opt.refine_stop != RSIGN_STOP_BOUND) return RSIGN_ERR_ARG;
+  if (opt.engine != RSIGN_ENGINE_NS3 && opt.engine != RSIGN_ENGINE_NS5) return RSIGN_ERR_ARG;
+  const bool ns5 = opt.engine == RSIGN_ENGINE_NS5;
+  if (ns5 && refine) return RSIGN_ERR_ARG;  // the tangent recursion differentiates Eq. NS
   if (refine && opt.refine_stop == RSIGN_STOP_BOUND && !auto_shift && std::isnan(opt.margin)) return RSIGN_ERR_ARG;
 
   Ctx c;
@@ -769,7 +782,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   std::vector<double> coef;
   {
     const double mk = auto_shift ? margin_lb : opt.margin;
-    if (opt.ns_scaling && std::isfinite(mk) && mk > 0.0) {
+    if (opt.ns_scaling && !ns5 && std::isfinite(mk) && mk > 0.0) {
       const double u0 = opt.alpha_mode == RSIGN_ALPHA_POWER ? 1.04 : 1.0;
       double l = std::min(1.0, alpha * mk) / u0;
       for (int m = 0; m < 200; ++m) {
@@ -784,7 +797,9 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   double* Rfinal = nullptr;  // dp x dp FP64 result
   double* xb64[2] = {nullptr, nullptr};
   double* E64 = nullptr;
+  double* W64 = nullptr;  // NS5 engine, FP64 policy
   const bool need64 = policy == RSIGN_FP64 || policy == RSIGN_FP16_POLISH || policy == RSIGN_BF16_POLISH;
+  if (ns5 && policy == RSIGN_FP64 && mem.alloc((void**)&W64, dd * 8) != cudaSuccess) return fail_cuda();
   if (mem.alloc((void**)&xb64[0], dd * 8) != cudaSuccess) return fail_cuda();
   if (need64 && (mem.alloc((void**)&xb64[1], dd * 8) != cudaSuccess ||
                  mem.alloc((void**)&E64, dd * 8) != cudaSuccess))
@@ -848,6 +863,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     double* tr_part = nullptr;
     if (mem.alloc((void**)&tr_part, (size_t)nt * 4 * 8) != cudaSuccess) return fail_cuda();
     const double tr_tol = 0.5 + 2.0 * u * std::sqrt((double)d);
+    void* wlp = nullptr;  // NS5 engine: W = E + 3/4 E^2
+    if (ns5 && mem.alloc(&wlp, dd * 2 * planes) != cudaSuccess) return fail_cuda();
     // exact squared row norms of each iterate for the SYRK's diagonal above
     // d = 1024 (kExactDiagMin): below, the tensor cores' accumulation bias moves
     // the trace by less than 3e-3 (and the grouped launches of the batched
@@ -887,9 +904,18 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
                            (double)(d - 2 * k), tr_tol)))
           return fail_cuda();
         if (mm == opt.max_steps) break;
+        void* bm = em;
+        if (ns5) {
+          // W = E + 3/4 E^2 (update epilogue, scale 3/2 on E E), then X+ = X + 1/2 X W
+          TcGemmArgs w = sy;
+          w.epi = TC_EPI_NS_UPDATE; w.out = wlp; w.xin = em; w.partials = partials; w.scale = 1.5f;
+          w.ns_c1 = 0.0f; w.ns_diag = nullptr;
+          if (!c.ok(tc_gemm(w, em, planes, em, planes, fmt, c.num_sms, st))) return fail_cuda();
+          bm = wlp;
+        }
         TcGemmArgs up = sy;
         up.epi = TC_EPI_NS_UPDATE; up.out = xn; up.xin = xm; up.partials = tr_part;
-        if (!c.ok(tc_gemm(up, xm, planes, em, planes, fmt, c.num_sms, st))) return fail_cuda();
+        if (!c.ok(tc_gemm(up, xm, planes, bm, planes, fmt, c.num_sms, st))) return fail_cuda();
       }
       if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess)
@@ -944,7 +970,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
 
   if (need64 && ctl_h.status == 0) {
     // ------------------------------------------------------------- FP64 stage
-    F64Loop L{{xb64[0], xb64[1]}, E64, partials, hist64, &ctl->done64, &ctl->steps64};
+    F64Loop L{{xb64[0], xb64[1]}, E64, partials, hist64, &ctl->done64, &ctl->steps64, W64};
     int m_ret = 0;
     const bool polish = policy != RSIGN_FP64;
     if (polish) {
@@ -1018,7 +1044,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       cudaEventElapsedTime(&t, ev[2], ev[3]); info->ms_fp64 = t;
     }
     const double dd3 = (double)d * d * d;
-    info->flops_low = is_low(policy) ? dd3 * (2.0 * steps_low + 1.0) : 0.0;
+    info->flops_low = is_low(policy) ? dd3 * ((ns5 ? 3.0 : 2.0) * steps_low + 1.0) : 0.0;
     info->launches = c.launches;
     info->workspace_bytes = mem.bytes;
   }
@@ -1380,7 +1406,7 @@ void rsign_options_default(rsign_options* opt) {
   opt->ns_scaling = 0;
   opt->margin = NAN;
   opt->refine_stop = RSIGN_STOP_ESTIMATE;
-  opt->reserved_opt = 0;
+  opt->engine = RSIGN_ENGINE_NS3;
 }
 
 rsign_status rsign_reflector_ex(const double* H, int64_t d, int32_t k, double s, double tol,

@@ -318,6 +318,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
         for (int jj = 0; jj < 32; ++jj) x[jj] += xl[jj];
       }
       const float c1 = a.ns_c1 != 0.0f ? a.ns_c1 : 1.0f;  // X+ = a (X + 1/2 X E) (scaled step)
+      if (a.scale != 1.0f && a.scale != 0.0f) {  // X_in + 1/2 scale acc
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) v[jj] *= a.scale;
+      }
       if (c1 == 1.0f) {
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) v[jj] = x[jj] + 0.5f * v[jj];

@@ -531,3 +531,49 @@ def test_commutator_bound_residual_term_is_tight_for_commuting_errors(oracle_mod
         b = oracle_mod.commutator_error_bound(0.0, mu, rho)
         assert eta * (1 - 1e-6) <= b <= eta * (1 + 4 * eta) + 1e-15
     assert oracle_mod.commutator_error_bound(1.0, 1.0, 0.0) == math.inf
+
+
+# ---------------------------------------------------------------------------
+# quintic Newton-Schulz filter (the higher-degree engine)
+# ---------------------------------------------------------------------------
+def test_ns5_map_closed_forms(oracle_mod):
+    x = np.linspace(-1.2, 1.2, 2401)
+    q = oracle_mod.ns5_map(x)
+    # odd, fixes 0 and +-1, derivative 15/8 (1 - x^2)^2 by central differences
+    assert np.allclose(q, -oracle_mod.ns5_map(-x), atol=1e-15)
+    assert oracle_mod.ns5_map(1.0) == 1.0 and oracle_mod.ns5_map(-1.0) == -1.0 and oracle_mod.ns5_map(0.0) == 0.0
+    h = 1e-6
+    dq = (oracle_mod.ns5_map(x + h) - oracle_mod.ns5_map(x - h)) / (2 * h)
+    assert np.allclose(dq, 15.0 / 8.0 * (1 - x * x) ** 2, atol=1e-8)
+    # cubic convergence at 1: 1 - q(1 - e) = 5/2 e^3 + O(e^4)
+    for e in (1e-2, 1e-3):
+        assert (1.0 - oracle_mod.ns5_map(1.0 - e)) / e ** 3 == pytest.approx(2.5, rel=10 * e)
+    # the update form X + 1/2 X W, W = E + 3/4 E^2, E = 1 - x^2 (the GPU's form)
+    E = 1.0 - x * x
+    assert np.allclose(x + 0.5 * x * (E + 0.75 * E * E), q, atol=1e-14)
+
+
+def test_ns5_iterates_on_a_diagonal_are_the_scalar_map(oracle_mod):
+    d = np.array([-0.9, -0.3, -0.02, 0.05, 0.4, 1.0])
+    it = oracle_mod.ns5_iterates(np.diag(d), 4)
+    y = d.copy()
+    for m in range(1, 5):
+        y = oracle_mod.ns5_map(y)
+        assert np.allclose(np.diag(it[m]), y, atol=1e-15)
+        assert np.allclose(it[m] - np.diag(np.diag(it[m])), 0.0)
+
+
+def test_ns5_iterates_reach_the_reflector_brute_force(oracle_mod):
+    rng = np.random.default_rng(21)
+    for d, k in ((6, 2), (9, 4)):
+        Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+        lam = np.concatenate([-rng.uniform(0.05, 1.0, k), rng.uniform(0.05, 1.0, d - k)])
+        H = (Q * lam) @ Q.T
+        X0 = H / np.abs(lam).max()
+        it = oracle_mod.ns5_iterates(X0, 14)
+        R = np.eye(d) - 2 * Q[:, :k] @ Q[:, :k].T
+        assert np.abs(it[-1] - R).max() < 1e-12
+        # fewer steps than Eq. NS from the same start
+        m3 = next(m for m, X in enumerate(oracle_mod.ns_iterates(X0, 40)) if np.abs(X - R).max() < 1e-10)
+        m5 = next(m for m, X in enumerate(it) if np.abs(X - R).max() < 1e-10)
+        assert m5 < m3
