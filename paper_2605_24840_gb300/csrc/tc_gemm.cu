@@ -422,19 +422,72 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
     const double* a_full = with_diag ? a.a_full + moff : nullptr;
     const double* b_full = with_diag ? a.b_full + moff : nullptr;
     float accf = 0.0f;
-#pragma unroll 4
-    for (int jj = 0; jj < 32; ++jj) {
+    // The int64 partial sums move in halves of 16 elements: all loads of a
+    // half are issued before any use (16-byte loads where the whole chunk is
+    // direct, i.e. not in the diagonal block of a symmetric product; there
+    // only the upper elements are touched), so their latency overlaps.
+    const bool full_chunk = !a.sym || above;
+#pragma unroll
+    for (int hh = 0; hh < 32; hh += 16) {
+      long long pv[16], pk[16];
+      if (!first) {
+        if (full_chunk) {
+          const longlong2* p2 = reinterpret_cast<const longlong2*>(accp + row + j0 + hh);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const longlong2 t = p2[q];
+            pv[2 * q] = t.x;
+            pv[2 * q + 1] = t.y;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) pv[q] = (j0 + hh + q >= i) ? accp[row + j0 + hh + q] : 0ll;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) pv[q] = 0ll;
+      }
+      if (last && two) {
+        const long long* pp = a.acc64 + moff + row + j0 + hh;
+        if (full_chunk) {
+          const longlong2* p2 = reinterpret_cast<const longlong2*>(pp);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const longlong2 t = p2[q];
+            pk[2 * q] = t.x;
+            pk[2 * q + 1] = t.y;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) pk[q] = (j0 + hh + q >= i) ? pp[q] : 0ll;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) pk[q] = 0ll;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) pv[q] += (long long)__float2int_rn(v[hh + q]) * (1ll << shift);
+      if (!last) {
+        if (full_chunk) {
+          longlong2* p2 = reinterpret_cast<longlong2*>(accp + row + j0 + hh);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) p2[q] = make_longlong2(pv[2 * q], pv[2 * q + 1]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (j0 + hh + q >= i) accp[row + j0 + hh + q] = pv[q];
+        }
+        continue;
+      }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int jj = hh + q;
       const int j = j0 + jj;
       const bool mirror = a.sym && j > i;
       if (a.sym && j < i) continue;
       const size_t e = row + j;
-      long long vv = (long long)__float2int_rn(v[jj]) * (1ll << shift);
-      if (!first) vv += accp[e];
-      if (!last) {
-        accp[e] = vv;
-        continue;
-      }
-      double x = oz_value(a, vv, two ? a.acc64[moff + e] : 0ll, ei + pow2_exp(cs[j]));
+      const long long vv = pv[q];
+      double x = oz_value(a, vv, pk[q], ei + pow2_exp(cs[j]));
       if (with_diag) {
         // exact diagonal terms: d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
         const double dbj = a.b_diag[voff + j];
@@ -449,6 +502,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
       }
       out[e] = x;
       if (mirror) out[(size_t)j * ld + i] = x;
+    }
     }
     acc1 += (double)accf;
   }
