@@ -72,9 +72,10 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
 int32_t rsign_dbg_set_refine_levels(int32_t polish, int32_t ra_first, int32_t ra_later);
 
 /*
- * Tile width of the refinement's FP64-grade products: 128 (the int64 level
+ * Tile width of the digit-plane products of one-matrix calls (refinement and
+ * FP64 polish): 128 (the int64 level
  * sums stay in TMEM), 256 (cluster pairs, sums in global memory) or 0 (the
- * default: 128 up to order 4096, else 256).  Other values leave it unchanged.
+ * default: 128 up to order 3072, else 256).  Other values leave it unchanged.
  * Process-wide; returns the previous setting.
  */
 int32_t rsign_dbg_set_ozaki_tile(int32_t bn);

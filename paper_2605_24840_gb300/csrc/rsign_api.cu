@@ -183,6 +183,52 @@ bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_ste
   return true;
 }
 
+// Tile width of the digit-plane products of one-matrix calls (the
+// refinement's FP64-grade products and the FP64-emulating polish): 128 keeps
+// the int64 level sums in TMEM (grouped-mode launch over a one-matrix tile
+// table), 256 uses cluster pairs with the sums in global memory; 0 = by order.
+// Measured per call (k = 16): FP16_REFINE d = 3072 8.95 ms with 128 against
+// 9.03 with 256, d = 8192 74.2 against 71.0; FP16_POLISH d = 2048 4.3 against
+// 6.0, d = 4096 21.9 against 18.2.  Short K loops favour the TMEM sums (a
+// level group's MMAs do not hide the read-modify-write of its sums), long
+// ones the cluster pairs (their shared B panel halves the operand traffic).
+int g_oz_tile = 0;
+int oz_tile_for(int dp) { return g_oz_tile != 0 ? g_oz_tile : (dp <= 3072 ? 128 : 256); }
+
+// Tile table of one dp x dp product on 128 x 128 tiles (upper triangle when
+// sym), visited in blocks of 16 x 16 tiles so that the CTAs in flight share
+// row and column panels in L2.
+std::vector<int4> oz_tile_table(int dp, int sym) {
+  const int nb = dp / 128, bh = 16, bw = 16;
+  std::vector<int4> u;
+  for (int cb = 0; cb < nb; cb += bw)
+    for (int rb = 0; rb < nb; rb += bh)
+      for (int r = rb; r < std::min(rb + bh, nb); ++r)
+        for (int c = cb; c < std::min(cb + bw, nb); ++c)
+          if (!sym || c >= r) u.push_back(make_int4(0, r, c, (int)u.size()));
+  return u;
+}
+
+// Device tile table (and {dp, d}) of one product on 128 x 128 tiles, from the
+// call's workspace.
+cudaError_t make_oz_tiles(DevBuf& mem, int dp, int d, int sym, cudaStream_t st, OzTiles* out) {
+  const std::vector<int4> u = oz_tile_table(dp, sym);
+  int4* du = nullptr;
+  int* dims = nullptr;
+  const int h_dims[2] = {dp, d};
+  cudaError_t e;
+  if ((e = mem.alloc((void**)&du, u.size() * sizeof(int4))) != cudaSuccess) return e;
+  if ((e = mem.alloc((void**)&dims, 2 * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(du, u.data(), u.size() * sizeof(int4), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(dims, h_dims, 2 * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;  // the host table goes out of scope
+  out->units = du;
+  out->n_units = (int)u.size();
+  out->dims = dims;
+  return cudaSuccess;
+}
+
 // FP64 polish steps X+ = X + 1/2 X (I - X^2) (Eq. NS, update form) on the
 // tensor cores: both products are FP64-emulating digit-plane products
 // (fp64e: >= 54-bit digits, FP32-exact group sums, int64 fixed point), the
@@ -209,7 +255,25 @@ cudaError_t fp64e_polish(Ctx& c, DevBuf& mem, double* xb[2], double* E, int dp, 
   if ((e = mem.alloc((void**)&Es.sigma, (size_t)dp * 8)) != cudaSuccess) return e;
   if ((e = mem.alloc((void**)&Es.diag, (size_t)dp * 8)) != cudaSuccess) return e;
   if ((e = mem.alloc((void**)&acc64, dd * 8)) != cudaSuccess) return e;
-  const int nt = tc_num_tiles(dp, 1);
+  // up to order 4096 the products run on 128 x 128 tiles with the int64 sums
+  // in TMEM (as the refinement's products); the residual partials then come
+  // per tile of that table
+  OzTiles tz{};
+  int nt = tc_num_tiles(dp, 1);
+  const bool t128 = oz_tile_for(dp) == 128;
+  if (t128) {
+    if ((e = make_oz_tiles(mem, dp, d, 1, c.st, &tz)) != cudaSuccess) return e;
+    nt = tz.n_units;
+  }
+  auto tiles = [&](Fp64eExtra& x) {
+    if (!t128) return;
+    x.units = tz.units;
+    x.n_units = tz.n_units;
+    x.n_mat = 1;
+    x.bn = 128;
+    x.mat_dp = tz.dims;
+    x.mat_d = tz.dims + 1;
+  };
   for (int m = 0; m <= steps; ++m) {
     double* X = xb[m & 1];
     Xs.full = X;
@@ -218,6 +282,7 @@ cudaError_t fp64e_polish(Ctx& c, DevBuf& mem, double* xb[2], double* E, int dp, 
     sq.acc64 = acc64;
     sq.ident = 1;
     sq.partials = partials;
+    tiles(sq);
     if (!c.ok(fp64e_gemm(Xs, Xs, dp, d, 1, E, sq, &ctl->status, c.num_sms, c.st, P))) return c.err;
     if (!c.ok(ns_check(partials, nt * 4, hist, m, -1.0, -1.0, -1.0, 0.0, &ctl->done64, &ctl->steps64, c.st)))
       return c.err;
@@ -228,6 +293,7 @@ cudaError_t fp64e_polish(Ctx& c, DevBuf& mem, double* xb[2], double* E, int dp, 
     up.acc64 = acc64;
     up.xin64 = X;
     up.xin_mult = 0.5;
+    tiles(up);
     if (!c.ok(fp64e_gemm(Xs, Es, dp, d, 1, xb[(m + 1) & 1], up, &ctl->status, c.num_sms, c.st, P)))
       return c.err;
   }
@@ -268,31 +334,6 @@ struct RefineOut {
   double resid = NAN, corr = NAN, comm = NAN, err_est = NAN, err_bound = NAN, rho = NAN;
   int levels_ra0 = 0;
 };
-
-// Tile width of the refinement's FP64-grade products: 128 keeps the int64
-// level sums in TMEM (grouped-mode launch over a one-matrix tile table),
-// 256 uses cluster pairs with the sums in global memory; 0 = by order.
-// Measured per call (FP16_REFINE, k = 16): d = 3072 9.85 ms with 128 against
-// 10.45 with 256 (the global read-modify-write of the sums stalls the
-// epilogue when the K loop of a level group is short); d = 8192 78.5 against
-// 76.5 (long K loops hide it, and the pairs' shared B panel halves the
-// operand traffic).
-int g_oz_tile = 0;
-int oz_tile_for(int dp) { return g_oz_tile != 0 ? g_oz_tile : (dp <= 4096 ? 128 : 256); }
-
-// Tile table of one dp x dp product on 128 x 128 tiles (upper triangle when
-// sym), visited in blocks of 16 x 16 tiles so that the CTAs in flight share
-// row and column panels in L2.
-std::vector<int4> oz_tile_table(int dp, int sym) {
-  const int nb = dp / 128, bh = 16, bw = 16;
-  std::vector<int4> u;
-  for (int cb = 0; cb < nb; cb += bw)
-    for (int rb = 0; rb < nb; rb += bh)
-      for (int r = rb; r < std::min(rb + bh, nb); ++r)
-        for (int c = cb; c < std::min(cb + bw, nb); ++c)
-          if (!sym || c >= r) u.push_back(make_int4(0, r, c, (int)u.size()));
-  return u;
-}
 
 // Order above which the Newton-Schulz SYRK takes the diagonal of X^2 from
 // exact row norms (row_sumsq) instead of the tensor-core sums.
@@ -375,23 +416,8 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   const OzTiles* tz_full = nullptr;
   const OzTiles* tz_sym = nullptr;
   if (oz_tile_for(dp) == 128) {
-    const std::vector<int4> uf = oz_tile_table(dp, 0), us = oz_tile_table(dp, 1);
-    int4 *duf = nullptr, *dus = nullptr;
-    int* dims = nullptr;
-    const int h_dims[2] = {dp, d};
-    RS_TRY(mem.alloc((void**)&duf, uf.size() * sizeof(int4)));
-    RS_TRY(mem.alloc((void**)&dus, us.size() * sizeof(int4)));
-    RS_TRY(mem.alloc((void**)&dims, 2 * sizeof(int)));
-    RS_TRY(cudaMemcpyAsync(duf, uf.data(), uf.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-    RS_TRY(cudaMemcpyAsync(dus, us.data(), us.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-    RS_TRY(cudaMemcpyAsync(dims, h_dims, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
-    RS_TRY(cudaStreamSynchronize(st));  // the host tables go out of scope
-    oz_full.units = duf;
-    oz_full.n_units = (int)uf.size();
-    oz_full.dims = dims;
-    oz_sym.units = dus;
-    oz_sym.n_units = (int)us.size();
-    oz_sym.dims = dims;
+    RS_TRY(make_oz_tiles(mem, dp, d, 0, st, &oz_full));
+    RS_TRY(make_oz_tiles(mem, dp, d, 1, st, &oz_sym));
     tz_full = &oz_full;
     tz_sym = &oz_sym;
   }

@@ -230,3 +230,24 @@ def test_refinement_products_same_bits_on_both_tile_widths(d, k):
     finally:
         rs.dbg_set_ozaki_tile(prev)
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("d", [768, 2048])
+def test_polish_products_same_bits_on_both_tile_widths(d):
+    # the FP64-emulating polish products are exact integer level sums as
+    # well: 128-wide (TMEM sums) and 256-wide launches give the same bits
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    import workloads
+    H, lam, Q = workloads.controlled_spectrum_torch(d, 8, 5e-2, seed=d + 3)
+    outs = []
+    prev = rs.dbg_set_ozaki_tile(256)
+    try:
+        for bn in (256, 128):
+            rs.dbg_set_ozaki_tile(bn)
+            R, info, st = rs.reflector(H, 8, 0.0, tol=1e-12, policy=rs.Policy.FP16_POLISH, check=False)
+            assert st == rs.Status.OK and info.steps_fp64 == 2
+            outs.append(R.clone())
+    finally:
+        rs.dbg_set_ozaki_tile(prev)
+    assert torch.equal(outs[0], outs[1])
