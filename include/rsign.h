@@ -95,8 +95,9 @@ typedef struct {
   double trace;            /* trace(R)                                                 */
   double correction_fro;   /* ||last refinement correction||_F (REFINE policies)       */
   double commutator_norm;  /* estimate of ||R A - A R||_2, A = H - sI, at the last
-                              a-posteriori check (REFINE): 2 ||G||_2 from FP64 power
-                              steps on v -> 1/2 R (R A v - A R v); NaN otherwise       */
+                              a-posteriori check (REFINE): 8 power steps on the
+                              antisymmetric C, v -> R A v - A R v, with FP64-class
+                              (double-float, ~2^-46 per term) products; NaN otherwise  */
   double err_est;          /* a-posteriori estimate of ||R - sign(H - sI)||_2 (REFINE):
                               max(1.5 kappa alpha ||G||_2, ||C||_2 / g): G = 1/2 R C,
                               C = R A - A R, kappa the gain of the last tangent solve,
@@ -139,9 +140,9 @@ typedef struct {
                               c = ||R A - A R||_2 / (2 mu) + ||R^2 - I||_2 / 2 (inf if
                               2c >= 1); with rsign_options.refine_stop = RSIGN_STOP_BOUND
                               the refinement stops on err_bound <= tol instead of err_est
-                              <= tol.  Both 2-norms are FP64 power-step
-                              estimates (commutator_norm and the check's power steps on
-                              R^2 - I).  NaN otherwise                                  */
+                              <= tol.  Both 2-norms are power-step estimates
+                              (commutator_norm and the check's power steps on R^2 - I,
+                              which converge from below).  NaN otherwise                */
 } rsign_info;
 
 /* Optional knobs; rsign_options_default() fills the defaults. */
