@@ -758,6 +758,32 @@ cudaError_t fp64e_plan(TcGemmArgs* a, int n_planes, int beta, int levels, int k_
     a->n_sg = 0;
     for (int g = 0; g < ng; ++g) a->group_shift[g] = beta * (L - 1 - group_level[g]);
     a->final_scale = std::ldexp(1.0, -beta * (L - 1 + 2));
+    // One exact int64 sum: any group order gives the same bits.  The groups
+    // run from the top level down, so that the heaviest epilogue (the last
+    // group's conversion to FP64) overlaps the next tile's longest group
+    // (the most pair products) instead of its shortest.
+    int pa[kTcMaxPairs], pb[kTcMaxPairs], gs[kTcMaxGroups + 1], sh[kTcMaxGroups];
+    double sc[kTcMaxGroups];
+    int q = 0;
+    for (int g = ng - 1, h = 0; g >= 0; --g, ++h) {
+      gs[h] = q;
+      sc[h] = a->group_scale[g];
+      sh[h] = a->group_shift[g];
+      for (int r = a->group_start[g]; r < a->group_start[g + 1]; ++r, ++q) {
+        pa[q] = a->pair_a[r];
+        pb[q] = a->pair_b[r];
+      }
+    }
+    gs[ng] = q;
+    for (int g = 0; g <= ng; ++g) a->group_start[g] = gs[g];
+    for (int g = 0; g < ng; ++g) {
+      a->group_scale[g] = sc[g];
+      a->group_shift[g] = sh[g];
+    }
+    for (int r = 0; r < q; ++r) {
+      a->pair_a[r] = pa[r];
+      a->pair_b[r] = pb[r];
+    }
     return cudaSuccess;
   }
   int split = L - 1;  // super-group 1 = levels split .. L-1, as long as it fits
