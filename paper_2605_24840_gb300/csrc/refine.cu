@@ -801,6 +801,40 @@ cudaError_t fp64e_plan(TcGemmArgs* a, int n_planes, int beta, int levels, int k_
   a->sg_weight[0] = std::ldexp(1.0, -beta * (split - 1 + 2));
   a->sg_weight[1] = std::ldexp(1.0, -beta * (L - 1 + 2));
   a->oz_sh01 = beta * (L - 1 - (split - 1));
+  // Within each super-group the sum is exact in any order: the groups run
+  // from the top level down (super-group 0 first, as the parking of its sum
+  // needs), so that the last group's conversion overlaps the next tile's
+  // group with the most pair products.
+  {
+    int pa[kTcMaxPairs], pb[kTcMaxPairs], gs[kTcMaxGroups + 1], sh[kTcMaxGroups], sgv[kTcMaxGroups];
+    double sc[kTcMaxGroups];
+    int q = 0, h = 0;
+    for (int s = 0; s < 2; ++s)
+      for (int g = ng - 1; g >= 0; --g) {
+        if (a->group_sg[g] != s) continue;
+        gs[h] = q;
+        sc[h] = a->group_scale[g];
+        sh[h] = a->group_shift[g];
+        sgv[h] = s;
+        for (int r = a->group_start[g]; r < a->group_start[g + 1]; ++r, ++q) {
+          pa[q] = a->pair_a[r];
+          pb[q] = a->pair_b[r];
+        }
+        ++h;
+      }
+    gs[ng] = q;
+    for (int g = 0; g <= ng; ++g) a->group_start[g] = gs[g];
+    for (int g = 0; g < ng; ++g) {
+      a->group_scale[g] = sc[g];
+      a->group_shift[g] = sh[g];
+      a->group_sg[g] = sgv[g];
+      a->group_first[g] = (g == 0 || sgv[g - 1] != sgv[g]) ? 1 : 0;
+    }
+    for (int r = 0; r < q; ++r) {
+      a->pair_a[r] = pa[r];
+      a->pair_b[r] = pb[r];
+    }
+  }
   return cudaSuccess;
 }
 
