@@ -80,7 +80,7 @@ def dist_env():
 # profiles/refine_fp16_d8192_launch_list.md (same kernel source and workload).
 # Algorithmic bytes of one launch: read X (hi + lo, 4 d^2) and write the result
 # (hi + lo, 4 d^2) = 8 d^2 = 0.54 GB at d = 8192.
-MEASURED_TRAFFIC = {(8192, "FP16_REFINE", 1): 2.261e9}
+MEASURED_TRAFFIC = {(8192, "FP16_REFINE", 1): 2.255e9}
 
 
 def peaks():
