@@ -167,3 +167,21 @@ def test_full_batched_workload_certifies_and_samples_match():
         err = np.linalg.norm(Rb[j] - _exact(sp), 2)
         # FP16 floor: a few u_fp16 over the scaled margin
         assert err <= 2e-3 / (lam[0] / np.max(np.abs(sp.lam - items[j][1]))) + 1e-6, (j, err)
+
+
+def test_sharded_batch_on_one_rank_equals_the_batched_call():
+    # the multi-GPU batched path at world size 1: its share is the whole batch
+    # and its outputs are those of one batched call, bit for bit
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    from paper_2605_24840_gb300 import shard
+    items = _batch(6, (64, 128, 256), (2e-2, 1e-1), seed=31)
+    Hs = [torch.from_numpy(sp.H).cuda() for sp, _ in items]
+    ks = [sp.k for sp, _ in items]
+    ss = [s for _, s in items]
+    mine, outs, reports = shard.reflectors_sharded(Hs, ks, ss, 1e-12, rs.Policy.FP16_POLISH, 0, 1)
+    ref, infos, st = rs.reflector_batched(Hs, ks, ss, tol=1e-12, policy=rs.Policy.FP16_POLISH)
+    assert st == rs.Status.OK and mine == list(range(6))
+    for a, b in zip(outs, ref):
+        assert torch.equal(a, b)
+    assert [r["cert_ok"] for r in reports] == [1] * 6
