@@ -244,7 +244,9 @@ rsign_status rsign_apply(const double* R, int64_t d, const double* V, int64_t nv
  * (the batched regime of Sec. 4.5).  Arrays H, d, k, s, R, infos have n
  * entries; H[i] and R[i] are d[i] x d[i] (device or host memory, each on its
  * own).  Returns the first non-OK status in index order (all are attempted);
- * infos[i] holds each matrix's own status-relevant report.
+ * infos[i] holds each matrix's own status-relevant report.  n = 0 returns
+ * RSIGN_OK at once (no device work; the pointers may be NULL); n < 0 is
+ * RSIGN_ERR_ARG.
  *   Grouped path: every matrix with d[i] <= 1024, a finite s[i] and a
  *   policy among FP64, FP16, BF16, FP16_POLISH, BF16_POLISH is placed in a
  *   Dmax x Dmax slot of one slab and the whole group advances together: each

@@ -94,6 +94,18 @@ def test_argument_errors_need_no_gpu(rs):
     assert st == rs.Status.ERR_ARG
 
 
+def test_empty_batch_is_a_no_op(rs):
+    # n = 0 is valid and returns before any device work (no GPU needed)
+    lib = rs.load()
+    st = lib.rsign_reflector_batched_ex(0, None, None, None, None, 1e-12, 0, None, None, None, None)
+    assert st == rs.Status.OK
+    outs, infos, st = rs.reflector_batched([], [], [])
+    assert st == rs.Status.OK and outs == [] and infos == []
+    # a negative count is an argument error
+    assert lib.rsign_reflector_batched_ex(-1, None, None, None, None, 1e-12, 0, None, None, None, None) \
+        == rs.Status.ERR_ARG
+
+
 @pytest.mark.parametrize("m,seed", [(1, 0), (2, 1), (7, 2), (60, 3), (200, 4)])
 def test_tridiagonal_ritz_solver_matches_scipy(rs, m, seed):
     # host part of the automatic shift: eigenvalues (Sturm bisection) and the last

@@ -391,3 +391,65 @@ def test_refine_largest_order_d16384():
     assert err <= 1e-6, (err, info.as_dict())
     assert float(D.norm()) <= 1e-4
     assert abs(info.trace - (d - 2 * k)) < 1e-6
+
+
+@pytest.mark.parametrize("policy,tol,bound", [("FP64", 1e-12, 1e-12), ("FP16_POLISH", 1e-12, 2e-2),
+                                              ("FP16_REFINE", 1e-6, 1e-6)])
+@pytest.mark.parametrize("d,k", [(2, 1), (3, 1), (3, 2)])
+def test_smallest_orders(policy, tol, bound, d, k):
+    # the degenerate orders: one 256-wide padded tile holding a 2 x 2 or 3 x 3
+    # problem (eigenvalues -delta, +delta pinned, the rest spread)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    spec = workloads.controlled_spectrum(d, k, 0.05, seed=700 + d + k)
+    R, info, st = _run(rs, torch, spec.H, k, 0.0, rs.Policy[policy], tol=tol)
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, k)) <= bound
+    assert abs(info.trace - (d - 2 * k)) < 1e-6
+
+
+def test_timed_workload_sampled_entries_match_the_oracle():
+    # the timed workload at full size and in its launch configuration: d = 8192,
+    # k = 16, half-gap 1e-2, shift at the middle of the gap, FP16_REFINE to
+    # 1e-6, power-step alpha, scaled steps from the margin.  The whole diagonal,
+    # the last row and 4096 seeded entries against the oracle's entries of
+    # I - 2 Q_k Q_k^T (|entry error| <= ||R - R_exact||_2 <= 1e-6).
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k, delta = 8192, 16, 1e-2
+    H, lam, Q = workloads.controlled_spectrum_torch(d, k, delta, workloads.controlled_seed(d, 1, 1))
+    lam_h = lam.cpu().numpy()
+    s = float(lam_h[k - 1] + 0.5 * (lam_h[k] - lam_h[k - 1]))
+    margin = float(min(s - lam_h[k - 1], lam_h[k] - s))
+    opt = rs.default_options(alpha_mode=int(rs.AlphaMode.POWER), ns_scaling=1, margin=margin)
+    R, info, st = rs.reflector(H, k, s, tol=1e-6, policy=rs.Policy.FP16_REFINE, options=opt, check=False)
+    torch.cuda.synchronize()
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert abs(info.trace - (d - 2 * k)) < 1e-6
+    Qk = Q[:, :k].cpu().numpy()
+    del H, Q
+    rng = np.random.default_rng(8192)
+    rows = np.concatenate([np.arange(d), np.full(d, d - 1), rng.integers(0, d, 4096)])
+    cols = np.concatenate([np.arange(d), np.arange(d), rng.integers(0, d, 4096)])
+    got = R[torch.from_numpy(rows).to(R.device), torch.from_numpy(cols).to(R.device)].cpu().numpy()
+    want = np.array([oracle.reflector_entry(Qk, k, int(i), int(j)) for i, j in zip(rows, cols)])
+    assert np.max(np.abs(got - want)) <= 1e-6
+    # symmetric to the bit on the sampled entries
+    assert np.array_equal(got, R[torch.from_numpy(cols).to(R.device), torch.from_numpy(rows).to(R.device)].cpu().numpy())
+
+
+@pytest.mark.parametrize("policy,tol,bound", [("FP64", 1e-12, 1e-11), ("FP16_REFINE", 1e-6, 1e-6)])
+def test_nonsymmetric_input_uses_the_symmetric_part(policy, tol, bound):
+    # only 1/2 (H + H^T) enters (the boundary's contract): an antisymmetric
+    # part of size 1 added to H leaves the reflector of the symmetric part
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 640, 9
+    spec = workloads.controlled_spectrum(d, k, 5e-2, seed=801)
+    K = np.random.default_rng(802).standard_normal((d, d))
+    H = spec.H + (K - K.T) / np.linalg.norm(K - K.T, 2)
+    assert not np.array_equal(H, H.T)
+    R, info, st = _run(rs, torch, H, k, 0.0, rs.Policy[policy], tol=tol)
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, k)) <= bound
+    assert np.array_equal(R, R.T)
