@@ -331,9 +331,10 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
 
 // Elementwise kernels of the refinement sweep.  `scal` is a small device
 // array of scalars: each kernel documents the slots it reads and writes.
-// C = N - N^T (FP32), block maxima of |C| -> blockmax and FP64 sums of C^2
-// -> part (one each per 32x32 tile).
-cudaError_t antisym_part(const double* N, int dp, float* C, float* blockmax, double* part,
+// C = (N - N^T) 2^k (FP32; the power of two keeps C inside the float range
+// whatever the scale of N), block maxima of |C| -> blockmax and FP64 sums of
+// C^2 -> part (one each per 32x32 tile).
+cudaError_t antisym_part(const double* N, int dp, int k, float* C, float* blockmax, double* part,
                          cudaStream_t st);
 // Per-32x32-tile maxima of |M| for an FP32 dp x dp matrix.
 cudaError_t absmax_tiles(const float* M, int dp, float* blockmax, cudaStream_t st);
@@ -346,7 +347,8 @@ cudaError_t scale_to_lp(const float* src, size_t n, const float* scale, void* ds
                         cudaStream_t st);
 // Direction of the Newton correction from the commutator product:
 // P = R C_lp^T (= -sigmaC R C); E0 = alpha * 1/4 (RC + (RC)^T) = -alpha/4 (P + P^T)/sigmaC,
-// written as FP32 with per-tile maxima.
+// written as FP32 with per-tile maxima (alpha pairs with the C given: alpha 2^-k
+// for a C scaled by 2^k).
 cudaError_t newton_direction(const float* P, int dp, const float* sigmaC, double alpha, float* E,
                              float* blockmax, cudaStream_t st);
 // Tangent Newton-Schulz step (Frechet derivative of X + 1/2 X (I - X^2)):

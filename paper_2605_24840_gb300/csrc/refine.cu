@@ -123,7 +123,7 @@ __device__ __forceinline__ void tile_max(float v, float* blockmax) {
 // C = N - N^T: one FP64 subtraction per element (the cancellation needs it);
 // the float of the result by integer rounding, its square summed in FP32 per
 // thread (four terms) and in FP64 across the tile
-__global__ void antisym_kernel(const double* __restrict__ N, int dp, float* __restrict__ C,
+__global__ void antisym_kernel(const double* __restrict__ N, int dp, int k, float* __restrict__ C,
                                float* blockmax, double* part) {
   __shared__ double t[TILE][TILE + 1];
   __shared__ double sd[8];
@@ -134,7 +134,7 @@ __global__ void antisym_kernel(const double* __restrict__ N, int dp, float* __re
   for (int r = ty; r < TILE; r += 8) {
     const size_t e = (size_t)(bi * TILE + r) * dp + bj * TILE + tx;
     float c, cl;
-    ic_split_f32(N[e] - t[tx][r], 0, &c, &cl);
+    ic_split_f32(N[e] - t[tx][r], k, &c, &cl);
     C[e] = c;
     m = fmaxf(m, fabsf(c));
     s2f = fmaf(c, c, s2f);
@@ -900,9 +900,9 @@ cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
   return tc_gemm_grouped(a, x.bn, A.planes, x.n_mat * A.n_planes, B.planes, x.n_mat * B.n_planes, 0, num_sms, st);
 }
 
-cudaError_t antisym_part(const double* N, int dp, float* C, float* blockmax, double* part,
+cudaError_t antisym_part(const double* N, int dp, int k, float* C, float* blockmax, double* part,
                          cudaStream_t st) {
-  antisym_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(N, dp, C, blockmax, part);
+  antisym_kernel<<<tiles_of(dp), dim3(32, 8), 0, st>>>(N, dp, k, C, blockmax, part);
   return cudaGetLastError();
 }
 

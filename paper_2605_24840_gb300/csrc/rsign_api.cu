@@ -574,14 +574,16 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     }
     o->levels_ra0 = sw == 0 ? lev : o->levels_ra0;
     if (!c.ok(ozaki_gemm(Rs, As, dp, d, 0, N64, status, c.num_sms, st, lev, tz_full))) return c.err;
-    if (!c.ok(antisym_part(N64, dp, C32, bmax, part, st))) return c.err;
+    // C in the units of alpha A (2^kA ~ alpha, exact): the FP32 copy and the
+    // direction's factor alpha 2^-kA in [1, 2) stay in range for any scale of H
+    if (!c.ok(antisym_part(N64, dp, kA, C32, bmax, part, st))) return c.err;
     if (!c.ok(sum_partials(part, ntile, red + 4, st))) return c.err;
     if (!c.ok(max_pow2(bmax, ntile, fs + 2, st))) return c.err;
     if (!c.ok(scale_to_lp(C32, dd, fs + 3, Clp, 0, st))) return c.err;
     if (!c.ok(to_f16(in.R64, dd, Rlp, st))) return c.err;
     // P = R C_lp^T = -sigma_C R C;  E_0 = alpha/4 (R C + (R C)^T)
     if (!c.ok(tc(Rlp, Clp, 0, 0, TC_EPI_STORE_F32, P32))) return c.err;
-    if (!c.ok(newton_direction(P32, dp, fs + 3, in.alpha, E32, bmax, st))) return c.err;
+    if (!c.ok(newton_direction(P32, dp, fs + 3, std::ldexp(in.alpha, -kA), E32, bmax, st))) return c.err;
     if (!c.ok(max_pow2(bmax, ntile, fs + 4, st))) return c.err;
     // ||E_0||_2 on the side stream, beside the tangent products (tensor-bound,
     // with HBM and SM slots to spare): a copy first, since the tangent steps

@@ -453,3 +453,58 @@ def test_nonsymmetric_input_uses_the_symmetric_part(policy, tol, bound):
     assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
     assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, k)) <= bound
     assert np.array_equal(R, R.T)
+
+
+@pytest.mark.parametrize("policy", ["FP64", "FP16_POLISH", "FP16_REFINE"])
+@pytest.mark.parametrize("e", [-300, 300])
+def test_power_of_two_scaling_gives_the_same_bits(policy, e):
+    # sign(c (H - sI)) = sign(H - sI) for c > 0.  With c = 2^e every FP64
+    # operation before the normalisation by alpha scales exactly, alpha
+    # scales by 1/c, and X_0 = alpha A is the same bits, so are the steps and,
+    # for FP64 and *_POLISH, the result.  REFINE handles the commutator of
+    # the unnormalised A and must stay in range at both ends (the margin
+    # option is in the units of H and scales with it).
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 700, 11
+    spec = workloads.controlled_spectrum(d, k, 5e-2, seed=901)
+    s = workloads.shift_in_gap(spec, 0.3)
+    mu = oracle.margin(s, *spec.gap)
+    refine = policy.endswith("REFINE")
+    tol = 1e-6 if refine else 1e-12
+    c = 2.0 ** e
+
+    def opts(scale):
+        if not refine:
+            return {}
+        return dict(alpha_mode=int(rs.AlphaMode.POWER), ns_scaling=1, margin=mu * scale)
+
+    R0, i0, st0 = _run(rs, torch, spec.H, k, s, rs.Policy[policy], tol=tol, **opts(1.0))
+    R1, i1, st1 = _run(rs, torch, spec.H * c, k, s * c, rs.Policy[policy], tol=tol, **opts(c))
+    assert st0 == rs.Status.OK and st1 == rs.Status.OK, (st0, st1, i1.as_dict())
+    assert (i1.steps_low, i1.steps_fp64, i1.sweeps_refine) == (i0.steps_low, i0.steps_fp64, i0.sweeps_refine)
+    assert i1.alpha == i0.alpha / c
+    if refine:
+        # the refined reflector at either scale is within the tolerance of the
+        # exact one (the bits agree at 2^-300 but not at 2^300)
+        R_ex = oracle.reflector_from_basis(spec.Q, k)
+        assert spec_norm_sym(R0 - R_ex) <= tol and spec_norm_sym(R1 - R_ex) <= tol
+    else:
+        assert np.array_equal(R0, R1)
+
+
+def test_apply_full_size_sampled_rows():
+    # out = R V at d = 8192, nv = 16 (device buffers): 64 seeded rows against numpy
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, nv = 8192, 16
+    g = torch.Generator(device="cuda").manual_seed(8193)
+    Rm = torch.randn((d, d), generator=g, device="cuda", dtype=torch.float64)
+    V = torch.randn((d, nv), generator=g, device="cuda", dtype=torch.float64)
+    out = rs.apply(Rm, V)
+    torch.cuda.synchronize()
+    rows = np.random.default_rng(8193).choice(d, 64, replace=False)
+    Rh = Rm[torch.from_numpy(rows).cuda()].cpu().numpy()
+    Vh = V.cpu().numpy()
+    got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.max(np.abs(got - Rh @ Vh)) < 1e-10
