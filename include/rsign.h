@@ -40,8 +40,8 @@ extern "C" {
 
 typedef enum {
   RSIGN_OK = 0,
-  RSIGN_ERR_ARG = 1,         /* invalid argument: d < 1, k outside [1, d-1], NULL, tol <= 0,
-                                non-finite entry in H, bad policy                        */
+  RSIGN_ERR_ARG = 1,         /* invalid argument: d < 2, k outside [1, d-1], NULL, tol <= 0,
+                                non-finite entry in H, bad policy or option              */
   RSIGN_ERR_NOCONV = 2,      /* step budget exhausted before the tolerance was met        */
   RSIGN_ERR_CERT = 3,        /* trace certificate failed: |trace R - (d - 2k)| >= 1/2,
                                 i.e. the shift is not in (lam_k, lam_{k+1}) or alpha*rho
@@ -49,7 +49,8 @@ typedef enum {
   RSIGN_ERR_GAP = 4,         /* automatic shift: target gap not resolved                  */
   RSIGN_ERR_CUDA = 5,        /* a CUDA runtime call failed                                */
   RSIGN_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up                        */
-  RSIGN_ERR_UNSUPPORTED = 7  /* device is not sm_103 or the size exceeds a limit          */
+  RSIGN_ERR_UNSUPPORTED = 7  /* device is not sm_103 or the size exceeds a limit
+                                (d > 16384; d > 512 for rsign_reflector_noalloc)          */
 } rsign_status;
 
 /* Precision policy of the Newton-Schulz steps. */
@@ -61,7 +62,8 @@ typedef enum {
   RSIGN_FP16_POLISH = 3,  /* FP16 steps followed by `polish_steps` FP64 NS steps          */
   RSIGN_BF16_POLISH = 4,  /* BF16 steps followed by `polish_steps` FP64 NS steps          */
   RSIGN_FP16_REFINE = 5,  /* FP16 steps, then commutator refinement sweeps with
-                             FP64-grade products until the correction falls below tol   */
+                             FP64-grade products until the error estimate (with
+                             refine_stop = RSIGN_STOP_BOUND: the bound) is <= tol       */
   RSIGN_BF16_REFINE = 6,  /* BF16 steps, then the same refinement                        */
   RSIGN_FP32 = 7          /* FP32-class steps: iterates carried as FP16 hi/lo pairs (22-bit
                              significands, the fused pair products hi*hi + hi*lo + lo*hi
@@ -215,7 +217,9 @@ void rsign_options_default(rsign_options* opt);
  *          recommended choice.  NaN requests an automatic midpoint shift from
  *          Lanczos estimates of lam_k, lam_{k+1} (Sec. 4.3, Prop. 4.2).
  *   tol    target: FP64 policy stops when ||X^2 - I||_F < max(tol, 16 d u_64);
- *          REFINE policies stop when the refinement correction is below tol.
+ *          REFINE policies stop when the a-posteriori error estimate err_est
+ *          (or, with refine_stop = RSIGN_STOP_BOUND, the bound err_bound) of
+ *          ||R - sign(H - sI)||_2 is at most tol.
  *   policy rsign_policy.
  *   R      d x d output (device or host), fully written on RSIGN_OK and
  *          RSIGN_ERR_CERT / RSIGN_ERR_NOCONV (last iterate).
