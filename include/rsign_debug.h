@@ -47,6 +47,25 @@ rsign_status rsign_dbg_tridiag_ritz(const double* alpha, const double* beta, int
                                     double* theta, double* last);
 
 /*
+ * Host routine of the scaled steps (runs on the CPU, no GPU needed): the step
+ * scalings a_0, a_1, ... that rsign_reflector_ex uses with ns_scaling = 1 for
+ * alpha_margin = alpha * margin (clipped to 1) and u0 the bound on the largest
+ * |eigenvalue| of X_0 (1 for the Gershgorin alpha, 1.04 for the power-step
+ * alpha).  For l = alpha_margin / u0, a = sqrt(3 / (1 + l + l^2)) and
+ * l <- 1/2 a l (3 - a^2 l^2), until a = 1 to 1e-15; a_0 is divided by u0.
+ * *n receives the count; the first min(cap, *n) are written to out.
+ */
+rsign_status rsign_dbg_scaled_coeffs(double alpha_margin, double u0, int32_t cap, double* out, int32_t* n);
+
+/*
+ * Host routine of the refinement (CPU, no GPU needed): the lower bound of the
+ * scaled margin gamma that a plain low-precision trajectory stopping after m
+ * steps implies, the root of p_m(gamma) = 0.9 (Eq. pm; p_m increases on
+ * [0, 1]) by bisection.
+ */
+rsign_status rsign_dbg_gamma_from_steps(int32_t m, double* gamma);
+
+/*
  * FP64 product on the FP64 pipe: out = A * B, all dp x dp row-major FP64,
  * dp a multiple of 64; sym = 1 as above.
  */

@@ -208,6 +208,10 @@ def load():
     lib.rsign_dbg_set_tc_cluster.restype = i32
     lib.rsign_dbg_tridiag_ritz.argtypes = [dp, dp, i32, i32, dp, dp]
     lib.rsign_dbg_tridiag_ritz.restype = ctypes.c_int
+    lib.rsign_dbg_scaled_coeffs.argtypes = [dbl, dbl, i32, dp, ctypes.POINTER(i32)]
+    lib.rsign_dbg_scaled_coeffs.restype = ctypes.c_int
+    lib.rsign_dbg_gamma_from_steps.argtypes = [i32, dp]
+    lib.rsign_dbg_gamma_from_steps.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -490,6 +494,26 @@ def dbg_tridiag_ritz(alpha, beta, j):
     if st != Status.OK:
         raise RsignError(st)
     return th.value, la.value
+
+
+def dbg_scaled_coeffs(alpha_margin, u0=1.0):
+    """Step scalings of the scaled steps for l0 = alpha * margin (host routine, no GPU)."""
+    lib = load()
+    n = ctypes.c_int32()
+    buf = (ctypes.c_double * 256)()
+    st = Status(lib.rsign_dbg_scaled_coeffs(float(alpha_margin), float(u0), 256, buf, ctypes.byref(n)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return [buf[i] for i in range(min(n.value, 256))]
+
+
+def dbg_gamma_from_steps(m: int) -> float:
+    """Margin lower bound implied by a plain trajectory stopping after m steps (host routine, no GPU)."""
+    g = ctypes.c_double()
+    st = Status(load().rsign_dbg_gamma_from_steps(int(m), ctypes.byref(g)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return g.value
 
 
 def dbg_set_tc_cluster(cluster: int) -> int:

@@ -369,6 +369,23 @@ int levels_ra0(double tol, double sA, double sR, int d, double mu) {
 // Lower bound of the scaled margin from a plain trajectory that stopped
 // after m steps: an eigenvalue x_0 = gamma reaches p_m(gamma) >= 0.9 only for
 // gamma above the root of p_m(gamma) = 0.9 (the map is increasing on [0, 1]).
+// Step scalings of the scaled iteration for a spectrum of X_0 in
+// [-u0, -l0] U [l0, u0] with l0 = min(1, alpha margin) (Sec. 3.5, the stable
+// scalings of the cited GPU sign iteration): with l = l0 / u0, each step's
+// a = sqrt(3 / (1 + l + l^2)) and l <- 1/2 a l (3 - a^2 l^2), until a is 1
+// to 1e-15; the first factor absorbs 1/u0.  Host only.
+std::vector<double> scaled_ns_coeffs(double alpha_margin, double u0) {
+  std::vector<double> coef;
+  double l = std::min(1.0, alpha_margin) / u0;
+  for (int m = 0; m < 200; ++m) {
+    const double a = std::sqrt(3.0 / (1.0 + l + l * l));
+    if (std::fabs(a - 1.0) <= 1e-15) break;
+    coef.push_back(m == 0 ? a / u0 : a);
+    l = 0.5 * a * l * (3.0 - a * a * l * l);
+  }
+  return coef;
+}
+
 double gamma_from_steps(int m) {
   double lo = 0.0, hi = 1.0;
   for (int it = 0; it < 200; ++it) {
@@ -810,16 +827,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   std::vector<double> coef;
   {
     const double mk = auto_shift ? margin_lb : opt.margin;
-    if (opt.ns_scaling && !ns5 && std::isfinite(mk) && mk > 0.0) {
-      const double u0 = opt.alpha_mode == RSIGN_ALPHA_POWER ? 1.04 : 1.0;
-      double l = std::min(1.0, alpha * mk) / u0;
-      for (int m = 0; m < 200; ++m) {
-        const double a = std::sqrt(3.0 / (1.0 + l + l * l));
-        if (std::fabs(a - 1.0) <= 1e-15) break;
-        coef.push_back(m == 0 ? a / u0 : a);
-        l = 0.5 * a * l * (3.0 - a * a * l * l);
-      }
-    }
+    if (opt.ns_scaling && !ns5 && std::isfinite(mk) && mk > 0.0)
+      coef = scaled_ns_coeffs(alpha * mk, opt.alpha_mode == RSIGN_ALPHA_POWER ? 1.04 : 1.0);
   }
 
   double* Rfinal = nullptr;  // dp x dp FP64 result
@@ -1545,6 +1554,20 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
 }
 
 int32_t rsign_dbg_set_tc_cluster(int32_t cluster) { return tc_set_default_cluster(cluster); }
+
+rsign_status rsign_dbg_scaled_coeffs(double alpha_margin, double u0, int32_t cap, double* out, int32_t* n) {
+  if (!out || !n || cap < 0 || !(alpha_margin > 0.0) || !(u0 >= 1.0) || !std::isfinite(u0)) return RSIGN_ERR_ARG;
+  const std::vector<double> coef = scaled_ns_coeffs(alpha_margin, u0);
+  *n = (int32_t)coef.size();
+  for (int32_t i = 0; i < cap && i < *n; ++i) out[i] = coef[i];
+  return RSIGN_OK;
+}
+
+rsign_status rsign_dbg_gamma_from_steps(int32_t m, double* gamma) {
+  if (!gamma || m < 0 || m > 1000) return RSIGN_ERR_ARG;
+  *gamma = gamma_from_steps(m);
+  return RSIGN_OK;
+}
 
 rsign_status rsign_dbg_tridiag_ritz(const double* alpha, const double* beta, int32_t m, int32_t j, double* theta,
                                     double* last) {

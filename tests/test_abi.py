@@ -158,3 +158,37 @@ def test_tile_order_is_a_permutation_of_the_needed_tiles(rs, dp, sym, cluster):
     # blocked: the first ~150 units touch few distinct row and column panels
     head = got[: min(len(got), 152)]
     assert len({c for _, c in head}) <= 16 and len({r for r, _ in head}) <= 40
+
+
+@pytest.mark.parametrize("l0,u0", [(1e-4, 1.0), (3e-3, 1.0), (1e-2, 1.04), (0.3, 1.0), (0.9, 1.04), (2.0, 1.0),
+                                   (2.0, 1.04)])
+def test_scaled_step_coefficients_match_the_oracle(rs, oracle_mod, l0, u0):
+    # the host routine behind rsign_options.ns_scaling against the oracle's
+    # step scalings (Sec. 3.5 reading), same interval and stop rule
+    got = rs.dbg_scaled_coeffs(l0, u0)
+    want = oracle_mod.scaled_ns_coeffs(min(1.0, l0), u0)
+    assert len(got) == len(want)
+    np.testing.assert_allclose(got, want, rtol=1e-15, atol=0)
+    if l0 >= 1.0 and u0 == 1.0:
+        assert got == []  # an involution needs no scaled step
+
+
+@pytest.mark.parametrize("m", [0, 1, 5, 12, 30])
+def test_margin_bound_from_steps_is_the_root_of_p_m(rs, oracle_mod, m):
+    # gamma with p_m(gamma) = 0.9 (Eq. pm), from the oracle's polynomial
+    g = rs.dbg_gamma_from_steps(m)
+    assert 0.0 < g <= 0.9
+    assert float(oracle_mod.p_m(g, m)) >= 0.9 - 1e-12
+    assert float(oracle_mod.p_m(g * (1.0 - 1e-9), m)) < 0.9
+    if m == 0:
+        assert g == pytest.approx(0.9, abs=1e-15)
+
+
+def test_host_routines_reject_bad_arguments(rs):
+    lib = rs.load()
+    n = ctypes.c_int32()
+    buf = (ctypes.c_double * 4)()
+    assert lib.rsign_dbg_scaled_coeffs(0.0, 1.0, 4, buf, ctypes.byref(n)) == rs.Status.ERR_ARG
+    assert lib.rsign_dbg_scaled_coeffs(0.1, 0.5, 4, buf, ctypes.byref(n)) == rs.Status.ERR_ARG
+    g = ctypes.c_double()
+    assert lib.rsign_dbg_gamma_from_steps(-1, ctypes.byref(g)) == rs.Status.ERR_ARG
