@@ -66,6 +66,29 @@ rsign_status rsign_dbg_scaled_coeffs(double alpha_margin, double u0, int32_t cap
 rsign_status rsign_dbg_gamma_from_steps(int32_t m, double* gamma);
 
 /*
+ * Host routines of the FP64-grade products (CPU, no GPU needed).
+ * rsign_dbg_fp64e_beta: the digit width (bits) that the FP64-emulating
+ * products use for an inner extent k_extent (the widest with one pair product
+ * exact in the FP32 accumulator and the plan within the kernel's limits);
+ * 0 when none fits.
+ * rsign_dbg_fp64e_plan: the accumulation plan of a product of two operands
+ * split into n_planes digit planes of beta bits, truncated after `levels`
+ * digit levels (level t = p + q for the pair of planes p, q), over k_extent
+ * terms.  meta[0..4] = number of groups G, number of pair products, number of
+ * int64 super-group sums (0 = one sum, 2 = two), log2 of the weight of one
+ * unit of the (last) sum, log2 of super-group 0's unit over super-group 1's.
+ * group_start[0..G] (pairs of group g: group_start[g] .. group_start[g+1]-1),
+ * pair_a / pair_b (plane of each operand, up to 72), group_shift[G] (log2 of
+ * the group's weight in its int64 sum), group_sg[G] (super-group of each
+ * group, 0 with one sum).  Groups appear in the kernel's execution order.
+ * RSIGN_ERR_ARG when the plan does not fit the kernel's limits.
+ */
+int32_t rsign_dbg_fp64e_beta(int64_t k_extent);
+rsign_status rsign_dbg_fp64e_plan(int32_t n_planes, int32_t beta, int32_t levels, int64_t k_extent, int32_t* meta,
+                                  int32_t* group_start, int32_t* pair_a, int32_t* pair_b, int32_t* group_shift,
+                                  int32_t* group_sg);
+
+/*
  * FP64 product on the FP64 pipe: out = A * B, all dp x dp row-major FP64,
  * dp a multiple of 64; sym = 1 as above.
  */

@@ -212,6 +212,11 @@ def load():
     lib.rsign_dbg_scaled_coeffs.restype = ctypes.c_int
     lib.rsign_dbg_gamma_from_steps.argtypes = [i32, dp]
     lib.rsign_dbg_gamma_from_steps.restype = ctypes.c_int
+    lib.rsign_dbg_fp64e_beta.argtypes = [i64]
+    lib.rsign_dbg_fp64e_beta.restype = i32
+    ip = ctypes.POINTER(i32)
+    lib.rsign_dbg_fp64e_plan.argtypes = [i32, i32, i32, i64, ip, ip, ip, ip, ip, ip]
+    lib.rsign_dbg_fp64e_plan.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -514,6 +519,29 @@ def dbg_gamma_from_steps(m: int) -> float:
     if st != Status.OK:
         raise RsignError(st)
     return g.value
+
+
+def dbg_fp64e_beta(k_extent: int) -> int:
+    """Digit width of the FP64-emulating products for an inner extent (host routine, no GPU)."""
+    return int(load().rsign_dbg_fp64e_beta(int(k_extent)))
+
+
+def dbg_fp64e_plan(n_planes, beta, levels, k_extent):
+    """Accumulation plan of an FP64-grade product (host routine, no GPU): a dict
+    with the groups (list of (pair list, shift, super-group)), the number of
+    int64 sums and the unit exponents."""
+    lib = load()
+    i32 = ctypes.c_int32
+    meta = (i32 * 5)()
+    gs, pa, pb = (i32 * 33)(), (i32 * 72)(), (i32 * 72)()
+    sh, sg = (i32 * 32)(), (i32 * 32)()
+    st = Status(lib.rsign_dbg_fp64e_plan(int(n_planes), int(beta), int(levels), int(k_extent), meta, gs, pa, pb,
+                                         sh, sg))
+    if st != Status.OK:
+        raise RsignError(st)
+    G = meta[0]
+    groups = [([(pa[r], pb[r]) for r in range(gs[g], gs[g + 1])], sh[g], sg[g]) for g in range(G)]
+    return {"groups": groups, "n_pairs": meta[1], "n_sg": meta[2], "unit_exp": meta[3], "sh01": meta[4]}
 
 
 def dbg_set_tc_cluster(cluster: int) -> int:

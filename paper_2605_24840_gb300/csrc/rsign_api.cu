@@ -1640,6 +1640,36 @@ int32_t rsign_dbg_set_ozaki_tile(int32_t bn) {
   return prev;
 }
 
+int32_t rsign_dbg_fp64e_beta(int64_t k_extent) {
+  if (k_extent < 1 || k_extent > 16384) return 0;
+  return fp64e_beta((int)k_extent);
+}
+
+rsign_status rsign_dbg_fp64e_plan(int32_t n_planes, int32_t beta, int32_t levels, int64_t k_extent, int32_t* meta,
+                                  int32_t* group_start, int32_t* pair_a, int32_t* pair_b, int32_t* group_shift,
+                                  int32_t* group_sg) {
+  if (!meta || !group_start || !pair_a || !pair_b || !group_shift || !group_sg || n_planes < 1 || beta < 2 ||
+      beta > 11 || n_planes * beta > 77 || levels < 1 || k_extent < 1 || k_extent > 16384)
+    return RSIGN_ERR_ARG;
+  TcGemmArgs a{};
+  if (fp64e_plan(&a, n_planes, beta, levels, (int)k_extent) != cudaSuccess) return RSIGN_ERR_ARG;
+  meta[0] = a.n_groups;
+  meta[1] = a.group_start[a.n_groups];
+  meta[2] = a.n_sg;
+  meta[3] = a.oz_unit_exp;
+  meta[4] = a.oz_sh01;
+  for (int g = 0; g <= a.n_groups; ++g) group_start[g] = a.group_start[g];
+  for (int r = 0; r < a.group_start[a.n_groups]; ++r) {
+    pair_a[r] = a.pair_a[r];
+    pair_b[r] = a.pair_b[r];
+  }
+  for (int g = 0; g < a.n_groups; ++g) {
+    group_shift[g] = a.group_shift[g];
+    group_sg[g] = a.n_sg == 2 ? a.group_sg[g] : 0;
+  }
+  return RSIGN_OK;
+}
+
 int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t cluster, int32_t* bm, int32_t* bn) {
   if (dp < 256 || dp % 256 || dp > 16384) return -1;
   const int n = tc_num_tiles((int)dp, sym ? 1 : 0) * 2;  // upper bound of the entries

@@ -192,3 +192,69 @@ def test_host_routines_reject_bad_arguments(rs):
     assert lib.rsign_dbg_scaled_coeffs(0.1, 0.5, 4, buf, ctypes.byref(n)) == rs.Status.ERR_ARG
     g = ctypes.c_double()
     assert lib.rsign_dbg_gamma_from_steps(-1, ctypes.byref(g)) == rs.Status.ERR_ARG
+
+
+_K_EXTENTS = [1, 255, 256, 700, 1024, 3072, 4096, 8191, 8192, 12288, 16384]
+
+
+def _check_fp64e_plan(plan, n_planes, beta, levels, k_extent):
+    L = min(levels, n_planes)
+    groups = plan["groups"]
+    # every pair of planes (p, q) with p + q < L appears exactly once
+    pairs = [pq for g in groups for pq in g[0]]
+    want = sorted((p, t - p) for t in range(L) for p in range(t + 1) if p < n_planes and t - p < n_planes)
+    assert sorted(pairs) == want and plan["n_pairs"] == len(pairs)
+    two = plan["n_sg"] == 2
+    assert plan["n_sg"] in (0, 2)
+    for g, (gp, shift, sg) in enumerate(groups):
+        levels_g = {p + q for p, q in gp}
+        assert len(levels_g) == 1  # one digit level per group
+        t = levels_g.pop()
+        # FP32 exactness: |digit| <= 2^(beta - 1), so a group sums to at most
+        # n 2^(2 beta - 2) K, which must stay within 2^24
+        assert len(gp) * 2 ** (2 * beta - 2) * k_extent <= 2 ** 24
+        # the group's weight reproduces the digit expansion: pair (p, q) of
+        # M_ik = sigma_i sum_p d_p 2^(-beta (p + 1)) weighs 2^(-beta (t + 2))
+        w = shift + plan["unit_exp"] + (plan["sh01"] if (two and sg == 0) else 0)
+        assert w == -beta * (t + 2), (g, t, shift, sg)
+        assert shift >= 0
+    # the int64 sums cannot overflow: 2^24 per group at its shift, per sum
+    for s in ((0, 1) if two else (0,)):
+        assert sum(2 ** (24 + sh) for gp, sh, sg in groups if sg == s) < 2 ** 62
+    # execution order: super-group 0 before 1, top level first within each
+    key = [(sg, -(gp[0][0] + gp[0][1])) for gp, sh, sg in groups]
+    assert key == sorted(key)
+    if two:
+        top0 = max(p + q for gp, sh, sg in groups if sg == 0 for p, q in gp)
+        low1 = min(p + q for gp, sh, sg in groups if sg == 1 for p, q in gp)
+        assert top0 < low1
+
+
+@pytest.mark.parametrize("k_extent", _K_EXTENTS)
+@pytest.mark.parametrize("levels", [1, 3, 5, 6, 7])
+def test_refinement_product_plans_are_exact(rs, k_extent, levels):
+    # the refinement's products: 7 planes of 5-bit digits, 5..7 levels
+    plan = rs.dbg_fp64e_plan(7, 5, levels, k_extent)
+    _check_fp64e_plan(plan, 7, 5, levels, k_extent)
+
+
+@pytest.mark.parametrize("k_extent", _K_EXTENTS)
+def test_fp64_emulating_plans_are_exact(rs, k_extent):
+    # the polish products: the widest digit with one exact pair product, all
+    # levels of ceil(54 / beta) planes (at least 54 bits)
+    beta = rs.dbg_fp64e_beta(k_extent)
+    assert beta in (5, 6, 7)
+    assert 2 ** (2 * beta - 2) * k_extent <= 2 ** 24
+    if beta < 7:  # a wider digit would not fit (exactness or the kernel's limits)
+        wider = 2 ** (2 * beta) * k_extent > 2 ** 24
+        assert wider or rs.dbg_fp64e_beta(max(1, k_extent // 4)) > beta
+    P = -(-54 // beta)
+    assert P * beta >= 54
+    plan = rs.dbg_fp64e_plan(P, beta, P, k_extent)
+    _check_fp64e_plan(plan, P, beta, P, k_extent)
+
+
+def test_fp64e_digit_width_shrinks_with_the_extent(rs):
+    widths = [rs.dbg_fp64e_beta(k) for k in _K_EXTENTS]
+    assert widths == sorted(widths, reverse=True)
+    assert rs.dbg_fp64e_beta(0) == 0 and rs.dbg_fp64e_beta(16385) == 0
