@@ -84,6 +84,18 @@ rsign_status rsign_dbg_gamma_from_steps(int32_t m, double* gamma);
  * RSIGN_ERR_ARG when the plan does not fit the kernel's limits.
  */
 int32_t rsign_dbg_fp64e_beta(int64_t k_extent);
+
+/*
+ * Host routine of the grouped batched launches (CPU, no GPU needed): the tile
+ * table of a batch of n matrices with padded orders dp[0..n) (multiples of
+ * bn, bn = 128 or 256), 128-row tiles of width bn, upper-triangle tiles only
+ * when sym; order 0 = largest matrices first, 1 = matrix order.  Entry i is
+ * units[4i .. 4i+3] = (matrix, tile row, tile column, partial slot); the first
+ * min(cap, count) entries are written, slot_begin (n + 1 entries, may be NULL)
+ * gets each matrix's first slot.  Returns the count, -1 for bad arguments.
+ */
+int32_t rsign_dbg_batch_units(int32_t n, const int32_t* dp, int32_t bn, int32_t sym, int32_t order, int32_t cap,
+                              int32_t* units, int32_t* slot_begin);
 rsign_status rsign_dbg_fp64e_plan(int32_t n_planes, int32_t beta, int32_t levels, int64_t k_extent, int32_t* meta,
                                   int32_t* group_start, int32_t* pair_a, int32_t* pair_b, int32_t* group_shift,
                                   int32_t* group_sg);

@@ -212,6 +212,9 @@ def load():
     lib.rsign_dbg_scaled_coeffs.restype = ctypes.c_int
     lib.rsign_dbg_gamma_from_steps.argtypes = [i32, dp]
     lib.rsign_dbg_gamma_from_steps.restype = ctypes.c_int
+    lib.rsign_dbg_batch_units.argtypes = [i32, ctypes.POINTER(i32), i32, i32, i32, i32, ctypes.POINTER(i32),
+                                          ctypes.POINTER(i32)]
+    lib.rsign_dbg_batch_units.restype = i32
     lib.rsign_dbg_fp64e_beta.argtypes = [i64]
     lib.rsign_dbg_fp64e_beta.restype = i32
     ip = ctypes.POINTER(i32)
@@ -519,6 +522,22 @@ def dbg_gamma_from_steps(m: int) -> float:
     if st != Status.OK:
         raise RsignError(st)
     return g.value
+
+
+def dbg_batch_units(dps, bn, sym=1, order=0):
+    """Tile table of the grouped batched launches (host routine, no GPU):
+    (list of (matrix, tile row, tile column, slot), slot_begin)."""
+    lib = load()
+    i32 = ctypes.c_int32
+    n = len(dps)
+    d = (i32 * max(n, 1))(*[int(x) for x in dps])
+    cnt = lib.rsign_dbg_batch_units(n, d, int(bn), int(sym), int(order), 0, None, None)
+    if cnt < 0:
+        raise RsignError(Status.ERR_ARG)
+    u = (i32 * (4 * max(cnt, 1)))()
+    sb = (i32 * (n + 1))()
+    lib.rsign_dbg_batch_units(n, d, int(bn), int(sym), int(order), cnt, u, sb)
+    return [tuple(u[4 * i:4 * i + 4]) for i in range(cnt)], list(sb)
 
 
 def dbg_fp64e_beta(k_extent: int) -> int:

@@ -1640,6 +1640,26 @@ int32_t rsign_dbg_set_ozaki_tile(int32_t bn) {
   return prev;
 }
 
+int32_t rsign_dbg_batch_units(int32_t n, const int32_t* dp, int32_t bn, int32_t sym, int32_t order, int32_t cap,
+                              int32_t* units, int32_t* slot_begin) {
+  if (n < 0 || (n > 0 && !dp) || (bn != 128 && bn != 256) || cap < 0 || (cap > 0 && !units)) return -1;
+  std::vector<int> d(dp, dp + n);
+  for (int m = 0; m < n; ++m)
+    if (d[m] < bn || d[m] % bn || d[m] > 16384) return -1;
+  std::vector<int4> u;
+  std::vector<int> sb;
+  tc_build_units(n, d.data(), bn, sym ? 1 : 0, order ? 1 : 0, &u, &sb);
+  for (int i = 0; i < (int)u.size() && i < cap; ++i) {
+    units[4 * i] = u[i].x;
+    units[4 * i + 1] = u[i].y;
+    units[4 * i + 2] = u[i].z;
+    units[4 * i + 3] = u[i].w;
+  }
+  if (slot_begin)
+    for (int m = 0; m <= n; ++m) slot_begin[m] = sb[m];
+  return (int32_t)u.size();
+}
+
 int32_t rsign_dbg_fp64e_beta(int64_t k_extent) {
   if (k_extent < 1 || k_extent > 16384) return 0;
   return fp64e_beta((int)k_extent);

@@ -258,3 +258,38 @@ def test_fp64e_digit_width_shrinks_with_the_extent(rs):
     widths = [rs.dbg_fp64e_beta(k) for k in _K_EXTENTS]
     assert widths == sorted(widths, reverse=True)
     assert rs.dbg_fp64e_beta(0) == 0 and rs.dbg_fp64e_beta(16385) == 0
+
+
+@pytest.mark.parametrize("bn", [128, 256])
+@pytest.mark.parametrize("sym", [0, 1])
+@pytest.mark.parametrize("order", [0, 1])
+def test_batch_tile_tables_cover_every_tile_once(rs, bn, sym, order):
+    # ragged padded orders (multiples of bn); each needed tile of each matrix
+    # appears once, its slot inside the matrix's own slot range
+    rng = np.random.default_rng(bn + 2 * sym + order)
+    dps = [bn * int(x) for x in rng.integers(1, 1024 // bn + 1, 37)]
+    units, sb = rs.dbg_batch_units(dps, bn, sym, order)
+    want = set()
+    for m, dp in enumerate(dps):
+        for r in range(dp // 128):
+            for c in range(dp // bn):
+                if not sym or (c + 1) * bn > r * 128:  # the tile meets the upper triangle
+                    want.add((m, r, c))
+    got = [(m, r, c) for m, r, c, _ in units]
+    assert len(got) == len(set(got)) and set(got) == want
+    assert sb[0] == 0 and sb[-1] == len(units) and all(a <= b for a, b in zip(sb, sb[1:]))
+    slots = sorted(s for *_, s in units)
+    assert slots == list(range(len(units)))
+    for m, r, c, s in units:
+        assert sb[m] <= s < sb[m + 1]
+    if order == 0:  # largest matrices first
+        sizes = [dps[m] for m, *_ in units]
+        assert sizes == sorted(sizes, reverse=True)
+    else:
+        assert [m for m, *_ in units] == sorted(m for m, *_ in units)
+
+
+def test_batch_tile_table_rejects_bad_orders(rs):
+    with pytest.raises(rs.RsignError):
+        rs.dbg_batch_units([256, 300], 128)
+    assert rs.dbg_batch_units([], 128) == ([], [0])
