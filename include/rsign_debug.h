@@ -86,6 +86,16 @@ rsign_status rsign_dbg_gamma_from_steps(int32_t m, double* gamma);
 int32_t rsign_dbg_fp64e_beta(int64_t k_extent);
 
 /*
+ * Host routine of the refinement (CPU, no GPU needed): the digit levels the
+ * refinement chooses by rule.  Low 16 bits: levels L of the first sweep's
+ * R A product, the smallest L in 5..7 with 2^(-5L) s_a s_r sqrt(d) <= tol mu / 2
+ * (7 when none), s_a and s_r the largest row scales of the digit splits of A
+ * and R, mu the margin.  High bits: levels of the polish product R^2 (5 when
+ * tol >= 1e-6 and 32 min(k, d - k) <= d, else 6).  -1 for bad arguments.
+ */
+int32_t rsign_dbg_refine_levels(double tol, double s_a, double s_r, int64_t d, double mu, int32_t k);
+
+/*
  * Host routine of the grouped batched launches (CPU, no GPU needed): the tile
  * table of a batch of n matrices with padded orders dp[0..n) (multiples of
  * bn, bn = 128 or 256), 128-row tiles of width bn, upper-triangle tiles only

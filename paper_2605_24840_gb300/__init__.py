@@ -215,6 +215,8 @@ def load():
     lib.rsign_dbg_batch_units.argtypes = [i32, ctypes.POINTER(i32), i32, i32, i32, i32, ctypes.POINTER(i32),
                                           ctypes.POINTER(i32)]
     lib.rsign_dbg_batch_units.restype = i32
+    lib.rsign_dbg_refine_levels.argtypes = [dbl, dbl, dbl, i64, dbl, i32]
+    lib.rsign_dbg_refine_levels.restype = i32
     lib.rsign_dbg_fp64e_beta.argtypes = [i64]
     lib.rsign_dbg_fp64e_beta.restype = i32
     ip = ctypes.POINTER(i32)
@@ -538,6 +540,14 @@ def dbg_batch_units(dps, bn, sym=1, order=0):
     sb = (i32 * (n + 1))()
     lib.rsign_dbg_batch_units(n, d, int(bn), int(sym), int(order), cnt, u, sb)
     return [tuple(u[4 * i:4 * i + 4]) for i in range(cnt)], list(sb)
+
+
+def dbg_refine_levels(tol, s_a, s_r, d, mu, k):
+    """(first sweep's R A levels, polish levels) chosen by rule (host routine, no GPU)."""
+    v = int(load().rsign_dbg_refine_levels(float(tol), float(s_a), float(s_r), int(d), float(mu), int(k)))
+    if v < 0:
+        raise RsignError(Status.ERR_ARG)
+    return v & 0xFFFF, v >> 16
 
 
 def dbg_fp64e_beta(k_extent: int) -> int:

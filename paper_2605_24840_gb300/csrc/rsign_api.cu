@@ -1660,6 +1660,13 @@ int32_t rsign_dbg_batch_units(int32_t n, const int32_t* dp, int32_t bn, int32_t 
   return (int32_t)u.size();
 }
 
+int32_t rsign_dbg_refine_levels(double tol, double s_a, double s_r, int64_t d, double mu, int32_t k) {
+  if (!(tol > 0.0) || !(s_a > 0.0) || !(s_r > 0.0) || d < 2 || d > 16384 || !(mu > 0.0) || k < 1 || k >= d)
+    return -1;
+  // low 16 bits: the first sweep's R A levels; high bits: the polish levels
+  return levels_ra0(tol, s_a, s_r, (int)d, mu) | (levels_for(0, tol, (int)d, k) << 16);
+}
+
 int32_t rsign_dbg_fp64e_beta(int64_t k_extent) {
   if (k_extent < 1 || k_extent > 16384) return 0;
   return fp64e_beta((int)k_extent);

@@ -1,6 +1,7 @@
 """CPU-side checks of the C ABI: the library builds, loads and exports every
 function that include/*.h declares; host logic of the binding.  No GPU calls."""
 import ctypes
+import math
 import os
 import re
 import subprocess
@@ -293,3 +294,23 @@ def test_batch_tile_table_rejects_bad_orders(rs):
     with pytest.raises(rs.RsignError):
         rs.dbg_batch_units([256, 300], 128)
     assert rs.dbg_batch_units([], 128) == ([], [0])
+
+
+def test_refinement_level_rule(rs):
+    # the first sweep's levels: the smallest L in 5..6 whose truncation model
+    # 2^(-5L) s_A s_R sqrt(d) stays within tol mu / 2, else 7
+    for tol in (1e-4, 1e-6, 1e-8, 1e-10):
+        for mu in (1e-1, 1e-2, 1e-3, 1e-4):
+            for d in (256, 4096, 16384):
+                L, _ = rs.dbg_refine_levels(tol, 2.0, 4.0, d, mu, 16)
+                model = [2.0 ** (-5 * l) * 8.0 * math.sqrt(d) <= 0.5 * tol * mu for l in (5, 6)]
+                assert L == (5 if model[0] else 6 if model[1] else 7)
+    # monotone: a smaller margin or a tighter tolerance never takes fewer levels
+    Ls = [rs.dbg_refine_levels(1e-6, 1.0, 1.0, 8192, mu, 16)[0] for mu in (1.0, 1e-1, 1e-2, 1e-3, 1e-4, 1e-5)]
+    assert Ls == sorted(Ls)
+    # polish: five levels for a small index at tol >= 1e-6, else six
+    assert rs.dbg_refine_levels(1e-6, 1, 1, 8192, 1e-2, 16)[1] == 5
+    assert rs.dbg_refine_levels(1e-6, 1, 1, 768, 1e-2, 384)[1] == 6
+    assert rs.dbg_refine_levels(1e-8, 1, 1, 8192, 1e-2, 16)[1] == 6
+    with pytest.raises(rs.RsignError):
+        rs.dbg_refine_levels(0.0, 1, 1, 8192, 1e-2, 16)
