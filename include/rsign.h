@@ -20,8 +20,17 @@
  *   - only the symmetric part 1/2 (H + H^T) of H is used; H is read-only;
  *   - workspace is allocated inside the call (stream-ordered, from a
  *     library-owned pool) and released before it returns; the pool keeps the
- *     memory mapped for later calls until rsign_trim_workspace(); no other
- *     state survives a call;
+ *     memory mapped for later calls until rsign_trim_workspace();
+ *   - state that outlives a call, shared by every host thread of the
+ *     process: that pool (one per device, created under a lock); the tile
+ *     width the batched call's autotuner chose per batch shape (a map under
+ *     a lock: the first call of a shape times both widths, later calls reuse
+ *     the choice); one-time kernel attributes and the tensor-map encoder
+ *     entry point; the static array of rsign_reflector_noalloc; and the
+ *     process-wide settings of the rsign_dbg_* entry points (not
+ *     thread-safe, for tests).  Nothing else is kept between calls, and
+ *     calls on different streams share no buffers except the pool's
+ *     allocator (rsign_reflector_noalloc excepted, see there);
  *   - calls are blocking: they return once `info` (if given) is filled, since
  *     the certificate is part of the result;
  *   - errors are reported through the return value only: the library never
@@ -112,7 +121,8 @@ typedef struct {
   double ms_fp64;          /* device time of the FP64 / FP64-grade stages, ms          */
   double flops_low;        /* algorithmic flops of the low-precision stage (2 d^3 per
                               NS step: SYRK X^2 plus the symmetric product)           */
-  int64_t launches;        /* kernels this call launched                               */
+  int64_t launches;        /* kernel launches this call issued, counting the ones
+                              enqueued after the device-side stop (they return at once) */
   int64_t workspace_bytes; /* device workspace the call allocated                      */
   /* automatic shift (s = NaN), Sec. 4.3 / Prop. 4.1-4.2; NaN / 0 otherwise:          */
   double lam_k_est;        /* Lanczos estimate of lam_k                                */
@@ -382,8 +392,9 @@ rsign_status rsign_shift_update(const double* H_new, const double* H_old, int64_
  *   - All calls share the static array: calls that overlap on the GPU (on
  *     several streams or from several host threads) race and must be
  *     serialised by the caller.  Each call clears the part it needs zeroed.
- *   - The first call on each device looks up the array's device address; make
- *     that first call before capturing the stream into a CUDA graph.
+ *   - Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress, with that device current).  That first
+ *     call should come before any stream capture begins.
  *   - Blocking like rsign_reflector; info->workspace_bytes is 0.
  */
 rsign_status rsign_reflector_noalloc(const double* H, int64_t d, int32_t k, double s, double tol,

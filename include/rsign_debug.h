@@ -29,14 +29,6 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
                                float* out, int* status, void* stream);
 
 /*
- * Process-wide choice of the tensor-core GEMM variant used by every later
- * call: 2 (default) = CTA pairs of a thread-block cluster sharing each
- * 256-row B panel through TMA multicast; 1 = independent CTAs.  Returns the
- * previous setting.  Not thread-safe; meant for tests and measurements.
- */
-int32_t rsign_dbg_set_tc_cluster(int32_t cluster);
-
-/*
  * Host routine of the automatic shift (runs on the CPU, no GPU needed): the
  * j-th smallest eigenvalue (0-based) of the m x m symmetric tridiagonal with
  * diagonal alpha[0..m-1] and off-diagonal beta[0..m-2] (Sturm bisection), and
@@ -127,6 +119,29 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
                                       int32_t sym, double* out, void* stream);
 
 /*
+ * Storage of the 5-bit digit planes of the FP64-grade products (the
+ * refinement's R A and R^2, and rsign_dbg_fp64grade_gemm): 1 = FP8 E4M3
+ * bytes multiplied on the kind::f8f6f4 tensor cores, 0 = FP16 on kind::f16.
+ * The digits (|d| <= 16) are exact in both formats and every level sum is
+ * the same integer, so the two settings give the same bits.  Other values
+ * leave the setting unchanged.  Process-wide; returns the previous setting.
+ */
+int32_t rsign_dbg_set_digit_fp8(int32_t on);
+
+/*
+ * Failure path of the bounded pipeline waits (the mbarrier waits of every
+ * tcgen05 kernel, which give up after a wall-clock limit instead of hanging):
+ * one kernel initialises an mbarrier for one arrival and waits for its first
+ * phase with the limit limit_ns (1 ns .. 2 s).  With arrive = 1 it arrives
+ * first and the wait succeeds; with arrive = 0 nothing completes the phase,
+ * the wait gives up after limit_ns and writes RSIGN_ERR_TIMEOUT into the
+ * device int *status (which the caller initialises to 0), and the kernel
+ * returns normally: the context stays usable.  Blocks until the kernel ends;
+ * returns RSIGN_ERR_ARG for a bad limit or a non-device status pointer.
+ */
+rsign_status rsign_dbg_bounded_wait(int32_t arrive, int64_t limit_ns, int* status, void* stream);
+
+/*
  * Digit levels (5 bits each, at most 7) of the refinement's FP64-grade
  * products: the polish SYRK R^2, the first sweep's R A and the later sweeps'
  * R A (defaults 0, 0, 7; 0 = chosen by the tolerance: 5 levels for tol >= 1e-6,
@@ -138,7 +153,7 @@ int32_t rsign_dbg_set_refine_levels(int32_t polish, int32_t ra_first, int32_t ra
 /*
  * Tile width of the digit-plane products of one-matrix calls (refinement and
  * FP64 polish): 128 (the int64 level
- * sums stay in TMEM), 256 (cluster pairs, sums in global memory) or 0 (the
+ * sums stay in TMEM), 256 (sums in global memory) or 0 (the
  * default: 128 up to order 3072, else 256).  Other values leave it unchanged.
  * Process-wide; returns the previous setting.
  */
@@ -146,12 +161,12 @@ int32_t rsign_dbg_set_ozaki_tile(int32_t bn);
 
 /*
  * The order in which the persistent tcgen05 GEMM visits the 128 x 256 tiles of
- * one dp x dp product (host computation, no GPU): entry t * cluster + r is
- * the (bm, bn) of schedule unit t for cluster rank r; sym selects the upper
- * triangle.  With bm == NULL returns an upper bound of the entry count;
- * otherwise fills bm/bn and returns the count; -1 for a bad dp.
+ * one dp x dp product (host computation, no GPU): entry t is the (bm, bn) of
+ * schedule unit t; sym selects the upper triangle.  With bm == NULL returns
+ * the entry count; otherwise fills bm/bn and returns the count; -1 for a bad
+ * dp.
  */
-int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t cluster, int32_t* bm, int32_t* bn);
+int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t* bm, int32_t* bn);
 
 /*
  * FP64-emulating product on the FP16 tensor cores (the products of the FP64

@@ -196,7 +196,11 @@ def load():
     lib.rsign_dbg_set_refine_levels.restype = i32
     lib.rsign_dbg_set_ozaki_tile.argtypes = [i32]
     lib.rsign_dbg_set_ozaki_tile.restype = i32
-    lib.rsign_dbg_tile_order.argtypes = [i64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.rsign_dbg_set_digit_fp8.argtypes = [i32]
+    lib.rsign_dbg_set_digit_fp8.restype = i32
+    lib.rsign_dbg_bounded_wait.argtypes = [i32, i64, vp, vp]
+    lib.rsign_dbg_bounded_wait.restype = ctypes.c_int
+    lib.rsign_dbg_tile_order.argtypes = [i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.rsign_dbg_tile_order.restype = i32
     lib.rsign_dbg_fp64e_gemm.argtypes = [vp, vp, i64, i64, i32, vp, vp]
     lib.rsign_dbg_fp64e_gemm.restype = ctypes.c_int
@@ -204,8 +208,6 @@ def load():
     lib.rsign_dbg_gemv_df.restype = ctypes.c_int
     lib.rsign_dbg_commutator_check.argtypes = [vp, vp, i64, i64, i32, vp, vp]
     lib.rsign_dbg_commutator_check.restype = ctypes.c_int
-    lib.rsign_dbg_set_tc_cluster.argtypes = [i32]
-    lib.rsign_dbg_set_tc_cluster.restype = i32
     lib.rsign_dbg_tridiag_ritz.argtypes = [dp, dp, i32, i32, dp, dp]
     lib.rsign_dbg_tridiag_ritz.restype = ctypes.c_int
     lib.rsign_dbg_scaled_coeffs.argtypes = [dbl, dbl, i32, dp, ctypes.POINTER(i32)]
@@ -573,9 +575,6 @@ def dbg_fp64e_plan(n_planes, beta, levels, k_extent):
     return {"groups": groups, "n_pairs": meta[1], "n_sg": meta[2], "unit_exp": meta[3], "sh01": meta[4]}
 
 
-def dbg_set_tc_cluster(cluster: int) -> int:
-    """Select the tensor-core GEMM variant (2: cluster pairs, 1: single CTAs); returns the previous one."""
-    return int(load().rsign_dbg_set_tc_cluster(int(cluster)))
 
 
 def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
@@ -592,6 +591,11 @@ def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
     return out
 
 
+def dbg_set_digit_fp8(on):
+    """Digit planes of the FP64-grade products as FP8 E4M3 (1) or FP16 (0); returns the previous setting."""
+    return int(load().rsign_dbg_set_digit_fp8(int(on)))
+
+
 def dbg_set_refine_levels(polish=-1, ra_first=-1, ra_later=-1):
     """Set the digit levels of the refinement's FP64-grade products (0 = by the tolerance,
     -1 keeps a setting); returns the previous settings as 100 p + 10 f + l."""
@@ -604,15 +608,22 @@ def dbg_set_ozaki_tile(bn):
     return int(load().rsign_dbg_set_ozaki_tile(int(bn)))
 
 
-def dbg_tile_order(dp, sym=0, cluster=1):
+def dbg_bounded_wait(arrive, limit_ns, status, stream=None):
+    """One bounded mbarrier wait (limit in ns); without the arrival it gives up and sets
+    *status (a device int32 tensor) to ERR_TIMEOUT.  Returns the call's status."""
+    lib = load()
+    return Status(lib.rsign_dbg_bounded_wait(int(arrive), int(limit_ns), status.data_ptr(), _stream_ptr(stream, True)))
+
+
+def dbg_tile_order(dp, sym=0):
     """(bm, bn) arrays of the persistent GEMM's tile visiting order (host only)."""
     lib = load()
-    n = lib.rsign_dbg_tile_order(int(dp), int(sym), int(cluster), None, None)
+    n = lib.rsign_dbg_tile_order(int(dp), int(sym), None, None)
     if n < 0:
         raise RsignError(Status.ERR_ARG)
     bm = (ctypes.c_int32 * n)()
     bn = (ctypes.c_int32 * n)()
-    m = lib.rsign_dbg_tile_order(int(dp), int(sym), int(cluster), bm, bn)
+    m = lib.rsign_dbg_tile_order(int(dp), int(sym), bm, bn)
     return np.array(bm[:m]), np.array(bn[:m])
 
 

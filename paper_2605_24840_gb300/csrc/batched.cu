@@ -576,7 +576,7 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
         a.group_scale[0] = 1.0; a.scale = 1.0f; a.out = elp; a.partials = partials; a.status = status;
         a.skip = all_done; a.units = units_c[c]; a.n_units = (int)ulp[c].size();
         a.mat_dp = c == 0 ? ia(I_DP128) : ia(I_DP256); a.mat_d = ia(I_D); a.mat_skip = ia(I_DONE);
-        a.mat_stride = (long long)slot; a.a_planes = 1; a.b_planes = 1; a.cluster = 1;
+        a.mat_stride = (long long)slot; a.a_planes = 1; a.b_planes = 1;
         return a;
       };
       // tile choice: forced, cached, or timed on the first SYRK (which

@@ -62,21 +62,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait on phase `parity` of the mbarrier at `bar`.  Returns false if
-// the call was already aborted by another role or the wall-clock limit ran
-// out (the latter records the timeout in *status).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* status) {
+// the call was already aborted by another role or the wall-clock limit
+// (limit_ns) ran out; the latter records the timeout in *status.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, volatile int* status,
+                                              unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_timer_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63u) == 0) {
       if (*status != kStatusOk) return false;
-      if (global_timer_ns() - t0 > kWaitLimitNs) {
+      if (global_timer_ns() - t0 > limit_ns) {
         atomicCAS(const_cast<int*>(status), kStatusOk, kStatusTimeout);
         return false;
       }
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* status) {
+  return mbar_wait_for(bar, parity, status, kWaitLimitNs);
 }
 
 // Bounded wait used while shutting a CTA down: ignores the abort flag and
@@ -99,26 +103,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm,
       " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
       "l"(tm), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
-}
-// Same load, multicast: the tile lands at the same shared-memory offset in
-// every CTA of the cluster named in `mask`, and each destination CTA's
-// mbarrier at offset `bar` receives the completed bytes.
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* tm, uint32_t bar,
-                                               int x, int y, int z, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(dst),
-      "l"(tm), "r"(bar), "r"(x), "r"(y), "r"(z), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// All threads of every CTA of the cluster (also a CTA-wide barrier).
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* tm) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(tm) : "memory");
@@ -153,19 +137,22 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::f8f6f4 with both operands
+// E4M3 (the instruction descriptor's format fields 0), FP32 accumulator,
+// K = 32 elements (32 bytes) per instruction.
+__device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrive once on `bar` when all previously issued tcgen05 ops of this thread completed.
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-// Arrive once on the mbarrier at offset `bar` of every CTA in `mask` when all
-// previously issued tcgen05 ops of this thread completed.
-__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(bar),
-      "h"(mask)
       : "memory");
 }
 // 32 lanes x 32 consecutive 32-bit columns: thread t of the warp gets lane
@@ -233,8 +220,8 @@ __device__ __forceinline__ uint64_t smem_desc_k128(uint32_t saddr) {
   return desc;
 }
 
-// Instruction descriptor, kind::f16, FP32 accumulator, both operands K-major.
-// ab_fmt: 0 = FP16, 1 = BF16.
+// Instruction descriptor, FP32 accumulator, both operands K-major.
+// kind::f16: ab_fmt 0 = FP16, 1 = BF16; kind::f8f6f4: ab_fmt 0 = E4M3.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt, uint32_t M, uint32_t N) {
   return (1u << 4)                 // D format: F32
          | (ab_fmt << 7)           // A format

@@ -154,12 +154,18 @@ __global__ void __launch_bounds__(128) f64_gemm_kernel(const F64GemmArgs a) {
 
 // ------------------------------------------------------------------ ingest
 // A = 1/2 (H + H^T) - s I (zero padded to dp), row partial sums of |A| per
-// 32-column block, non-finite detection.
+// 32-column block, non-finite detection.  One block per pair of mirror tiles
+// {(bi, bj), (bj, bi)}, bi <= bj: both tiles of H are read once and both
+// tiles of A written from them, so every entry of H crosses the bus once
+// (H may be host memory mapped for the device).  Blocks below the diagonal
+// return at once.
 __global__ void ingest_kernel(const double* __restrict__ H, int d, int dp, double s,
                               double* __restrict__ A, double* __restrict__ rowpart, int* flags) {
-  __shared__ double t1[32][33], t2[32][33];
+  __shared__ double t1[32][33], t2[32][33], tv[32][33];
   const int bi = blockIdx.y, bj = blockIdx.x;  // A tile (bi, bj): rows bi*32.., cols bj*32..
+  if (bi > bj) return;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const bool mirror = bi != bj;
   // FP64 arithmetic only where it changes a value (GB300's FP64 pipe is
   // slower than the stream): the finiteness test and |v| on the bit
   // patterns, the average of a bitwise symmetric pair is the entry itself,
@@ -169,13 +175,14 @@ __global__ void ingest_kernel(const double* __restrict__ H, int d, int dp, doubl
     const int i = bi * 32 + r, j = bj * 32 + tx;
     double h1 = 0.0, h2 = 0.0;
     if (i < d && j < d) h1 = H[(size_t)i * d + j];
-    const int i2 = bj * 32 + r, j2 = bi * 32 + tx;  // transposed tile
-    if (i2 < d && j2 < d) h2 = H[(size_t)i2 * d + j2];
+    const int i2 = bj * 32 + r, j2 = bi * 32 + tx;  // the mirror tile
+    if (mirror && i2 < d && j2 < d) h2 = H[(size_t)i2 * d + j2];
     if (((ic_bits(h1) >> 52) & 0x7FF) == 0x7FF || ((ic_bits(h2) >> 52) & 0x7FF) == 0x7FF) bad = true;
     t1[r][tx] = h1;
-    t2[r][tx] = h2;
+    t2[r][tx] = mirror ? h2 : h1;  // the diagonal tile holds both triangles itself
   }
   __syncthreads();
+  // A(bi, bj)[r][c] from H_ij = t1[r][c] and H_ji = t2[c][r]
   for (int r = ty; r < 32; r += 8) {
     const int i = bi * 32 + r, j = bj * 32 + tx;
     double v = 0.0;
@@ -186,15 +193,22 @@ __global__ void ingest_kernel(const double* __restrict__ H, int d, int dp, doubl
       else v = 0.5 * (a + b);
     }
     A[(size_t)i * dp + j] = v;
-    t1[r][tx] = ic_double(ic_bits(v) & 0x7FFFFFFFFFFFFFFFull);
+    tv[r][tx] = v;
   }
   if (bad) atomicOr(flags, 1);
   __syncthreads();
-  // row partial sums over the 32 columns of this tile
+  // A(bj, bi) = A(bi, bj)^T, the same bits: row bj*32 + r of it is column r of tv
+  if (mirror)
+    for (int r = ty; r < 32; r += 8) A[(size_t)(bj * 32 + r) * dp + bi * 32 + tx] = tv[tx][r];
+  // row partial sums of |A| over the 32 columns of each tile, in column order
   if (ty == 0) {
     double sum = 0.0;
-    for (int c = 0; c < 32; ++c) sum += t1[tx][c];
+    for (int c = 0; c < 32; ++c) sum += ic_double(ic_bits(tv[tx][c]) & 0x7FFFFFFFFFFFFFFFull);
     rowpart[(size_t)bj * dp + bi * 32 + tx] = sum;
+  } else if (ty == 1 && mirror) {
+    double sum = 0.0;
+    for (int r = 0; r < 32; ++r) sum += ic_double(ic_bits(tv[r][tx]) & 0x7FFFFFFFFFFFFFFFull);
+    rowpart[(size_t)bi * dp + bj * 32 + tx] = sum;
   }
 }
 

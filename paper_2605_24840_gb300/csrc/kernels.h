@@ -61,7 +61,6 @@ struct TcGemmArgs {
   int pair_a[kTcMaxPairs];
   int pair_b[kTcMaxPairs];
   double group_scale[kTcMaxGroups];
-  int cluster;                    // 1: single-CTA tiles; 0 or 2: cluster pairs sharing B (default)
   int group_shift[kTcMaxGroups];  // TC_EPI_OZAKI: group weight 2^shift in its int64 sum
   double final_scale;             // TC_EPI_OZAKI (n_sg == 0): weight of one unit of that sum
   // TC_EPI_OZAKI with two super-groups of levels (n_sg == 2, for products of
@@ -126,19 +125,16 @@ struct TcGemmArgs {
 
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
 int tc_num_tiles(int dp, int sym);
-// Host copy of the single-matrix tile order (128 x 256 tiles, cluster size
-// cl): (bm, bn) of schedule unit t and cluster rank r at index t cl + r;
-// returns the number of entries.
-int tc_tile_order(int dp, int sym, int cl, int* bm, int* bn);
-// Process-wide default for TcGemmArgs::cluster == 0 (2 unless set to 1);
-// returns the previous value.
-int tc_set_default_cluster(int cl);
+// Host copy of the single-matrix tile order (128 x 256 tiles): (bm, bn) of
+// schedule unit t at index t; returns the number of entries.
+int tc_tile_order(int dp, int sym, int* bm, int* bn);
 
 // Launch.  A/B point to [a_slices][dp][dp] / [b_slices][dp][dp] arrays of
-// the operand type; lp_fmt 0 = FP16, 1 = BF16.  dp must be a multiple of 256.
+// the operand type; lp_fmt 0 = FP16, 1 = BF16, 2 = FP8 E4M3 (digit-plane
+// products only: TC_EPI_OZAKI).  dp must be a multiple of 256.
 cudaError_t tc_gemm(const TcGemmArgs& args, const void* A, int a_slices, const void* B,
                     int b_slices, int lp_fmt, int num_sms, cudaStream_t st);
-// Grouped launch over args.units (tile width bn = 128 or 256, no clusters);
+// Grouped launch over args.units (tile width bn = 128 or 256);
 // a_slices / b_slices count all slices of the slab (matrices x planes).
 // The digit-plane epilogue has no grouped form.
 cudaError_t tc_gemm_grouped(const TcGemmArgs& args, int bn, const void* A, int a_slices, const void* B,
@@ -273,7 +269,7 @@ constexpr int kSlices = 7;      // digit planes per operand (35 bits)
 // off-diagonal maximum, which is far below the diagonal for the reflector
 // and for diagonally heavy Hessians) and re-enters exactly in the epilogue.
 struct SplitMat {
-  void* planes;        // [n_planes][dp][dp] FP16 digits of M - diag(M)
+  void* planes;        // [n_planes][dp][dp] FP16 (or FP8) digits of M - diag(M)
                        // (grouped: [n_mat][n_planes][dp][dp], dp = slot order)
   double* sigma;       // [dp] row scales (powers of two)
   double* diag;        // [dp] diag(M)
@@ -281,6 +277,8 @@ struct SplitMat {
   int n_planes = kSlices;   // digit planes (n_planes * beta <= 56)
   int beta = kSliceBeta;    // bits per digit
   int keep_diag = 0;        // 1: the diagonal is in the digits (no exact diagonal terms)
+  int fp8 = 0;              // 1: digits stored as FP8 E4M3 bytes (beta <= 5: |digit| <= 16,
+                            // exact in E4M3), multiplied on the kind::f8f6f4 tensor cores
 };
 // Split the FP64 matrix M (dp x dp, symmetric) into digit planes; out.full = M.
 cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st);

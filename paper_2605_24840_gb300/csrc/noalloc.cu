@@ -25,8 +25,8 @@
 //
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress while that device is current (host code may not
-// use the symbol itself: in host code it is only a stand-in).  Make that
-// first call before capturing the stream into a CUDA graph.
+// use the symbol itself: in host code it is only a stand-in).  That first
+// call should come before any stream capture begins.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -197,6 +197,9 @@ extern "C" rsign_status rsign_reflector_noalloc(const double* H, int64_t d64, in
     info->err_est = NAN;
     info->err_bound = NAN;
     info->tol_fro = tol_fro;
+    // kernels issued: ingest, the two of the inf-norm reduction, the FP64
+    // copy of X_0, three per step of every 8-step chunk enqueued (the ones
+    // after the device-side stop return at once), trace and output copy
     info->launches = 6 + 3 * (int64_t)m;
     info->workspace_bytes = 0;
   }

@@ -30,6 +30,24 @@ __device__ __forceinline__ void f64_parts(long long bits, unsigned long long& ma
   e2 = E ? E - 1075 : -1074;
 }
 
+// E4M3 byte of a small integer |n| <= 16 (exact: at most four significant
+// bits; exponent bias 7, three stored significand bits), by integer steps.
+__device__ __forceinline__ uint32_t e4m3_of_int(int n) {
+  const uint32_t a = (uint32_t)(n < 0 ? -n : n);
+  if (a == 0) return 0u;
+  const int e = 31 - __clz((int)a);  // 2^e <= a < 2^(e+1), e <= 4
+  const uint32_t mant = (e <= 3 ? (a << (3 - e)) : (a >> (e - 3))) & 7u;
+  return (n < 0 ? 0x80u : 0u) | ((uint32_t)(e + 7) << 3) | mant;
+}
+
+// Two digits of one plane at columns k, k + 1 as FP16 (half2) or FP8 (two bytes)
+__device__ __forceinline__ void store_digit_pair(__half* planes, size_t idx, int d0, int d1) {
+  *reinterpret_cast<__half2*>(planes + idx) = __halves2half2(__int2half_rn(d0), __int2half_rn(d1));
+}
+__device__ __forceinline__ void store_digit_pair(uint8_t* planes, size_t idx, int d0, int d1) {
+  *reinterpret_cast<uint16_t*>(planes + idx) = (uint16_t)(e4m3_of_int(d0) | (e4m3_of_int(d1) << 8));
+}
+
 // Digit planes of one row per warp (8 rows per block; grid.y = matrix).
 // Everything is integer arithmetic on the FP64 bit patterns: the row scale
 // sigma_i = 2^ex comes from the largest off-diagonal magnitude (compared as
@@ -37,8 +55,10 @@ __device__ __forceinline__ void f64_parts(long long bits, unsigned long long& ma
 // fixed-point integer n = round(M_ik 2^(62 - ex)), |n| < 2^61, by a shift of
 // its significand, and the balanced base-2^beta digits are peeled off with
 // shifts; the FP64 pipe of this GPU is far slower than its integer pipe.
-// Lane l handles the column pairs 2 l + 64 t, 2 l + 64 t + 1 (half2 stores).
-__global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrows, __half* __restrict__ planes,
+// Lane l handles the column pairs 2 l + 64 t, 2 l + 64 t + 1 (half2 or
+// two-byte stores).
+template <typename D>
+__global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrows, D* __restrict__ planes,
                                   double* __restrict__ sigma, double* __restrict__ diag, int n_planes,
                                   int beta, const int* __restrict__ mat_dp, int keep_diag) {
   const int lane = threadIdx.x & 31;
@@ -71,8 +91,7 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrow
     sigma[(size_t)m * ld + i] = __longlong_as_double((long long)(ex + 1023) << 52);
     diag[(size_t)m * ld + i] = __longlong_as_double(row[i]);
   }
-  __half2* pl = reinterpret_cast<__half2*>(planes + (size_t)m * n_planes * slot + (size_t)i * ld);
-  const size_t pslot = slot / 2;
+  D* pl = planes + (size_t)m * n_planes * slot + (size_t)i * ld;
   for (int k = 2 * lane; k < ncols; k += 64) {
     long long n[2];
 #pragma unroll
@@ -100,7 +119,7 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrow
         dg[h] = (n[h] + (1ll << (sh - 1))) >> sh;  // nearest, |dg| <= 2^(beta-1)
         n[h] -= dg[h] * (1ll << sh);               // |n| <= 2^(sh-1)
       }
-      pl[p * pslot + (k >> 1)] = __halves2half2(__int2half_rn((int)dg[0]), __int2half_rn((int)dg[1]));
+      store_digit_pair(pl, (size_t)p * slot + k, (int)dg[0], (int)dg[1]);
     }
   }
 }
@@ -681,18 +700,32 @@ int grid_for(size_t n) {
 
 }  // namespace
 
+static bool split_ok(const SplitMat& o) {
+  return o.n_planes >= 1 && o.n_planes * o.beta <= 56 && o.beta >= 2 && o.beta <= 11 && (!o.fp8 || o.beta <= 5);
+}
+
 cudaError_t split_rows(const double* M, int dp, SplitMat out, cudaStream_t st) {
-  if (out.n_planes < 1 || out.n_planes * out.beta > 56 || out.beta < 2 || out.beta > 11) return cudaErrorInvalidValue;
-  split_rows_kernel<<<dim3((dp + 7) / 8, 1), 256, 0, st>>>(M, dp, dp, (__half*)out.planes, out.sigma, out.diag,
-                                                           out.n_planes, out.beta, nullptr, out.keep_diag);
+  if (!split_ok(out)) return cudaErrorInvalidValue;
+  const dim3 grid((dp + 7) / 8, 1);
+  if (out.fp8)
+    split_rows_kernel<uint8_t><<<grid, 256, 0, st>>>(M, dp, dp, (uint8_t*)out.planes, out.sigma, out.diag,
+                                                     out.n_planes, out.beta, nullptr, out.keep_diag);
+  else
+    split_rows_kernel<__half><<<grid, 256, 0, st>>>(M, dp, dp, (__half*)out.planes, out.sigma, out.diag,
+                                                    out.n_planes, out.beta, nullptr, out.keep_diag);
   return cudaGetLastError();
 }
 
 cudaError_t split_rows_grouped(const double* M, int D, int n_mat, const int* mat_dp, SplitMat out,
                                cudaStream_t st) {
-  if (out.n_planes < 1 || out.n_planes * out.beta > 56 || out.beta < 2 || out.beta > 11) return cudaErrorInvalidValue;
-  split_rows_kernel<<<dim3((D + 7) / 8, n_mat), 256, 0, st>>>(M, D, D, (__half*)out.planes, out.sigma, out.diag,
-                                                              out.n_planes, out.beta, mat_dp, out.keep_diag);
+  if (!split_ok(out)) return cudaErrorInvalidValue;
+  const dim3 grid((D + 7) / 8, n_mat);
+  if (out.fp8)
+    split_rows_kernel<uint8_t><<<grid, 256, 0, st>>>(M, D, D, (uint8_t*)out.planes, out.sigma, out.diag,
+                                                     out.n_planes, out.beta, mat_dp, out.keep_diag);
+  else
+    split_rows_kernel<__half><<<grid, 256, 0, st>>>(M, D, D, (__half*)out.planes, out.sigma, out.diag,
+                                                    out.n_planes, out.beta, mat_dp, out.keep_diag);
   return cudaGetLastError();
 }
 
@@ -854,7 +887,9 @@ cudaError_t ozaki_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
 
 cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real, int sym, double* out,
                        const Fp64eExtra& x, int* status, int num_sms, cudaStream_t st, int levels) {
-  if (A.beta != B.beta || A.n_planes != B.n_planes || A.keep_diag != B.keep_diag) return cudaErrorInvalidValue;
+  if (A.beta != B.beta || A.n_planes != B.n_planes || A.keep_diag != B.keep_diag || A.fp8 != B.fp8)
+    return cudaErrorInvalidValue;
+  const int fmt = A.fp8 ? 2 : 0;
   TcGemmArgs a{};
   a.dp = dp;
   a.d_real = d_real;
@@ -886,7 +921,7 @@ cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
   cudaError_t e = fp64e_plan(&a, A.n_planes, A.beta, levels, kext);
   if (e != cudaSuccess) return e;
   if (a.n_sg == 2 && a.acc64 == nullptr) return cudaErrorInvalidValue;
-  if (x.units == nullptr) return tc_gemm(a, A.planes, A.n_planes, B.planes, B.n_planes, 0, num_sms, st);
+  if (x.units == nullptr) return tc_gemm(a, A.planes, A.n_planes, B.planes, B.n_planes, fmt, num_sms, st);
   a.units = x.units;
   a.n_units = x.n_units;
   a.mat_dp = x.mat_dp;
@@ -896,8 +931,9 @@ cudaError_t fp64e_gemm(const SplitMat& A, const SplitMat& B, int dp, int d_real,
   a.mat_vec_stride = dp;
   a.a_planes = A.n_planes;
   a.b_planes = B.n_planes;
-  a.cluster = 1;
-  return tc_gemm_grouped(a, x.bn, A.planes, x.n_mat * A.n_planes, B.planes, x.n_mat * B.n_planes, 0, num_sms, st);
+ 
+  return tc_gemm_grouped(a, x.bn, A.planes, x.n_mat * A.n_planes, B.planes, x.n_mat * B.n_planes, fmt, num_sms,
+                         st);
 }
 
 cudaError_t antisym_part(const double* N, int dp, int k, float* C, float* blockmax, double* part,

@@ -80,6 +80,19 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory (cudaHostAlloc / cudaHostRegister:
+// mapped into the device's address space), or nullptr for any other pointer.
+// Kernels read and write such memory directly over the CPU-GPU link, with
+// no staging copy (on GB300 the NVLink-C2C link to the Grace CPU).
+const void* mapped_host_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int check_device(int* num_sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return RSIGN_ERR_CUDA; }
@@ -186,12 +199,10 @@ bool f64_ns(Ctx& c, const F64Loop& L, int dp, int d, double tol_abs, int max_ste
 // Tile width of the digit-plane products of one-matrix calls (the
 // refinement's FP64-grade products and the FP64-emulating polish): 128 keeps
 // the int64 level sums in TMEM (grouped-mode launch over a one-matrix tile
-// table), 256 uses cluster pairs with the sums in global memory; 0 = by order.
-// Measured per call (k = 16): FP16_REFINE d = 3072 8.95 ms with 128 against
-// 9.03 with 256, d = 8192 74.2 against 71.0; FP16_POLISH d = 2048 4.3 against
-// 6.0, d = 4096 21.9 against 18.2.  Short K loops favour the TMEM sums (a
-// level group's MMAs do not hide the read-modify-write of its sums), long
-// ones the cluster pairs (their shared B panel halves the operand traffic).
+// table), 256 keeps them in global memory between level groups; 0 = by order.
+// Short K loops favour the TMEM sums (a level group's MMAs do not hide the
+// read-modify-write of its sums), long ones the 256-wide tiles (each A panel
+// load serves twice the columns, so less operand traffic per product).
 int g_oz_tile = 0;
 int oz_tile_for(int dp) { return g_oz_tile != 0 ? g_oz_tile : (dp <= 3072 ? 128 : 256); }
 
@@ -345,6 +356,11 @@ constexpr int kExactDiagMin = 1024;
 // of R = I - 2 P_k, which grow like sqrt(min(k, d - k))/d; five levels when
 // the index is small against d (measured at d = 8192, k = 16), else six.
 int g_levels_polish = 0, g_levels_ra0 = 0, g_levels_ra = kSlices;
+// Digit planes of the refinement's FP64-grade products as FP8 E4M3 bytes on
+// the kind::f8f6f4 tensor cores (1) or as FP16 (0).  The 5-bit balanced
+// digits (|digit| <= 16) are exact in E4M3, the level sums are the same
+// integers either way, so both give the same bits.
+int g_digit_fp8 = 0;
 int levels_for(int set, double tol, int d, int k) {
   if (set > 0) return set;
   const bool few = 32 * std::min(k, d - k) <= d;
@@ -408,10 +424,12 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   void *Clp = nullptr, *Rlp = nullptr, *Elp = nullptr, *Qlp = nullptr;
   cudaError_t e;
 #define RS_TRY(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
-  RS_TRY(mem.alloc(&As.planes, dd * 2 * kSlices));
+  As.fp8 = Rs.fp8 = g_digit_fp8;
+  const size_t digit_bytes = g_digit_fp8 ? 1 : 2;
+  RS_TRY(mem.alloc(&As.planes, dd * digit_bytes * kSlices));
   RS_TRY(mem.alloc((void**)&As.sigma, (size_t)dp * 8));
   RS_TRY(mem.alloc((void**)&As.diag, (size_t)dp * 8));
-  RS_TRY(mem.alloc(&Rs.planes, dd * 2 * kSlices));
+  RS_TRY(mem.alloc(&Rs.planes, dd * digit_bytes * kSlices));
   RS_TRY(mem.alloc((void**)&Rs.sigma, (size_t)dp * 8));
   RS_TRY(mem.alloc((void**)&Rs.diag, (size_t)dp * 8));
   As.full = in.A64;
@@ -725,12 +743,21 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       mem.alloc((void**)&partials, (size_t)n_part * 8) != cudaSuccess ||
       mem.alloc((void**)&hist, (size_t)hist_len * 8) != cudaSuccess)
     return fail_cuda();
+  // page-locked host buffers are read and written in place by the ingest and
+  // output kernels; other host memory goes through staging copies
+  const double* h_map = h_dev ? nullptr : static_cast<const double*>(mapped_host_ptr(H));
+  double* r_map = r_dev ? nullptr : const_cast<double*>(static_cast<const double*>(mapped_host_ptr(R)));
   if (!h_dev) {
-    if (mem.alloc((void**)&Hd, (size_t)d * d * 8) != cudaSuccess) return fail_cuda();
-    if (cudaMemcpyAsync(Hd, H, (size_t)d * d * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return fail_cuda();
+    if (h_map) {
+      Hd = const_cast<double*>(h_map);
+    } else {
+      if (mem.alloc((void**)&Hd, (size_t)d * d * 8) != cudaSuccess) return fail_cuda();
+      if (cudaMemcpyAsync(Hd, H, (size_t)d * d * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail_cuda();
+    }
   }
-  if (!r_dev && mem.alloc((void**)&Rd, (size_t)d * d * 8) != cudaSuccess) return fail_cuda();
+  if (r_map) Rd = r_map;
+  else if (!r_dev && mem.alloc((void**)&Rd, (size_t)d * d * 8) != cudaSuccess) return fail_cuda();
   if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), st) != cudaSuccess) return fail_cuda();
   double* hist_low = hist;
   double* hist64 = hist + opt.max_steps + 2;
@@ -778,6 +805,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   // ---- ingest and scaling (Sec. 4.3: alpha = 1/||H - sI||_inf)
   if (!c.ok(ingest(Hd, d, dp, s, A64, rowpart, &ctl->flags, st))) return fail_cuda();
   if (!c.ok(inf_norm_finish(rowpart, dp, rowsum, ctl->scal, st))) return fail_cuda();
+  ++c.launches;  // inf_norm_finish issues two kernels
   if (opt.alpha_mode == RSIGN_ALPHA_POWER) {
     // alpha = 1/(1.02 rho_est) from power steps on A (overwrites the Gershgorin
     // value); an estimate within a few percent is all it needs, so the steps
@@ -1032,7 +1060,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   // ---- certificate and output
   if (!c.ok(trace_f64(Rfinal, dp, d, ctl->scal + 2, st))) return fail_cuda();
   if (!c.ok(copy_unpad(Rfinal, dp, Rd, d, st))) return fail_cuda();
-  if (!r_dev && cudaMemcpyAsync(R, Rd, (size_t)d * d * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (!r_dev && !r_map && cudaMemcpyAsync(R, Rd, (size_t)d * d * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return fail_cuda();
   if (opt.timing) cudaEventRecord(ev[3], st);
   if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1421,6 +1449,25 @@ __global__ void apply_kernel(const double* __restrict__ R, int64_t d, const doub
   }
 }
 
+// One bounded mbarrier wait with a caller-chosen limit: thread 0 initialises a
+// barrier for one arrival and waits for its first phase, arriving itself first
+// when `arrive` is set.  Without the arrival nothing completes the phase, so
+// the wait gives up after limit_ns and records RSIGN_ERR_TIMEOUT in *status:
+// the failure path of every pipeline wait in the library, exercised without a
+// broken pipeline.
+__global__ void bounded_wait_kernel(int* status, unsigned long long limit_ns, int arrive) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) mbar_arrive(smem_u32(&bar));
+    mbar_wait_for(smem_u32(&bar), 0, status, limit_ns);
+  }
+}
+
 }  // namespace
 }  // namespace rsign
 
@@ -1553,8 +1600,6 @@ rsign_status rsign_dbg_tc_gemm(const void* A, const void* B, int64_t dp, int32_t
   return tc_gemm(a, A, 1, B, 1, fmt, sms, (cudaStream_t)stream) == cudaSuccess ? RSIGN_OK : RSIGN_ERR_CUDA;
 }
 
-int32_t rsign_dbg_set_tc_cluster(int32_t cluster) { return tc_set_default_cluster(cluster); }
-
 rsign_status rsign_dbg_scaled_coeffs(double alpha_margin, double u0, int32_t cap, double* out, int32_t* n) {
   if (!out || !n || cap < 0 || !(alpha_margin > 0.0) || !(u0 >= 1.0) || !std::isfinite(u0)) return RSIGN_ERR_ARG;
   const std::vector<double> coef = scaled_ns_coeffs(alpha_margin, u0);
@@ -1604,10 +1649,12 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
   rsign_status res = RSIGN_OK;
   sa.full = A;
   sb.full = B;
-  if (mem.alloc(&sa.planes, dd * 2 * kSlices) != cudaSuccess ||
+  sa.fp8 = sb.fp8 = g_digit_fp8;
+  const size_t digit_bytes = g_digit_fp8 ? 1 : 2;
+  if (mem.alloc(&sa.planes, dd * digit_bytes * kSlices) != cudaSuccess ||
       mem.alloc((void**)&sa.sigma, (size_t)dp * 8) != cudaSuccess ||
       mem.alloc((void**)&sa.diag, (size_t)dp * 8) != cudaSuccess ||
-      mem.alloc(&sb.planes, dd * 2 * kSlices) != cudaSuccess ||
+      mem.alloc(&sb.planes, dd * digit_bytes * kSlices) != cudaSuccess ||
       mem.alloc((void**)&sb.sigma, (size_t)dp * 8) != cudaSuccess ||
       mem.alloc((void**)&sb.diag, (size_t)dp * 8) != cudaSuccess ||
       mem.alloc((void**)&status, 4) != cudaSuccess || cudaMemsetAsync(status, 0, 4, st) != cudaSuccess ||
@@ -1623,6 +1670,26 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
   if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
   cudaGetLastError();
   return res;
+}
+
+int32_t rsign_dbg_set_digit_fp8(int32_t on) {
+  const int prev = g_digit_fp8;
+  if (on == 0 || on == 1) g_digit_fp8 = on;
+  return prev;
+}
+
+rsign_status rsign_dbg_bounded_wait(int32_t arrive, int64_t limit_ns, int* status, void* stream) {
+  if (!status || limit_ns < 1 || limit_ns > (int64_t)kWaitLimitNs || !is_device_ptr(status)) return RSIGN_ERR_ARG;
+  int sms = 0;
+  rsign_status ds = (rsign_status)check_device(&sms);
+  if (ds != RSIGN_OK) return ds;
+  cudaStream_t st = (cudaStream_t)stream;
+  bounded_wait_kernel<<<1, 32, 0, st>>>(status, (unsigned long long)limit_ns, arrive ? 1 : 0);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return RSIGN_ERR_CUDA;
+  }
+  return RSIGN_OK;
 }
 
 int32_t rsign_dbg_set_refine_levels(int32_t polish, int32_t ra_first, int32_t ra_later) {
@@ -1697,11 +1764,11 @@ rsign_status rsign_dbg_fp64e_plan(int32_t n_planes, int32_t beta, int32_t levels
   return RSIGN_OK;
 }
 
-int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t cluster, int32_t* bm, int32_t* bn) {
+int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t* bm, int32_t* bn) {
   if (dp < 256 || dp % 256 || dp > 16384) return -1;
-  const int n = tc_num_tiles((int)dp, sym ? 1 : 0) * 2;  // upper bound of the entries
+  const int n = tc_num_tiles((int)dp, sym ? 1 : 0);
   if (!bm || !bn) return n;
-  return tc_tile_order((int)dp, sym ? 1 : 0, cluster == 2 ? 2 : 1, bm, bn);
+  return tc_tile_order((int)dp, sym ? 1 : 0, bm, bn);
 }
 
 rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, int64_t d_real, int32_t sym,

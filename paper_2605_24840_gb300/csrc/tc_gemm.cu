@@ -14,9 +14,9 @@
 // of X^2 (SYRK) and of the symmetric product X (I - X^2) of a Newton-Schulz
 // step (Eq. NS).
 //
-// Tile widths: BN = 256 (one matrix, optionally cluster pairs sharing the B
-// panel) and BN = 128 (grouped batches of small matrices, where a 256-wide
-// tile would be mostly padding).  Grouped mode (args.units != nullptr) takes
+// Tile widths: BN = 256 (one matrix) and BN = 128 (grouped batches of small
+// matrices, where a 256-wide tile would be mostly padding).  Every CTA loads
+// its own A and B tiles: no shared-memory exchange between CTAs.  Grouped mode (args.units != nullptr) takes
 // its tiles from a device table of (matrix, bm, bn, slot) entries built on
 // the host: every matrix of a batch lives in its own Dmax x Dmax slot of one
 // slab, each tile runs its K loop over its own matrix's padded size only, and
@@ -24,6 +24,8 @@
 // all three roles alike.
 #include "common.cuh"
 #include "kernels.h"
+
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <mutex>
@@ -33,7 +35,9 @@
 namespace rsign {
 namespace {
 
-constexpr int BM = 128, BK = 64;
+// One pipeline stage holds 128 bytes of K per operand row (one 128-byte
+// swizzle row): BK = 64 FP16/BF16 elements, or 128 FP8 elements (kBK8).
+constexpr int BM = 128, BK = 64, kBK8 = 128;
 constexpr int NUM_THREADS = 192;
 
 template <int BN>
@@ -46,42 +50,35 @@ struct Cfg {
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
-// Tile schedule of one matrix over 128 x BN output tiles (bm, bn).  With
-// cluster pairs (cl = 2) the unit is a 256-row super-tile (a, bn) covering
-// bm = 2a and bm = 2a + 1: both tiles need the same BN-row panel of B, which
-// the pair loads once (each CTA half of it, multicast to both).  In the
-// triangular schedule schedule-row r (rows r cl BM .. ) needs the columns
-// bn >= floor(r cl BM / BN); for BN = 256 both members of a pair are always
-// needed together.
+// Tile schedule of one matrix over 128 x BN output tiles (bm, bn).  In the
+// triangular schedule tile row r needs the columns bn >= floor(r BM / BN).
 //
-// Order: blocks of 2048 rows (16 tile rows, or 8 super-rows of a pair) x
-// kBW = 8 columns (2048 columns), block-rows top to bottom, column blocks
-// left to right, row-major inside a block.  The ~150 tiles in flight then
-// cover about one block, whose row and column panels (2 x 2048 rows of K)
-// stay in L2 across all the pair products of the tiles, instead of one row
-// of units streaming every column panel.
+// Order: blocks of 2048 rows (16 tile rows) x kBW = 8 columns (2048
+// columns), block-rows top to bottom, column blocks left to right, row-major
+// inside a block.  The ~150 tiles in flight then cover about one block, whose
+// row and column panels (2 x 2048 rows of K) stay in L2 across all the pair
+// products of the tiles, instead of one row of tiles streaming every column
+// panel.
 constexpr int kBW = 8;
+constexpr int kBH = 16;  // tile rows per block (2048 matrix rows)
 
 template <int BN>
 struct TileSched {
-  int nbm, nbn, sym, cl, n;
-  __device__ __host__ TileSched(int dp, int s, int c) : nbm(dp / BM), nbn(dp / BN), sym(s), cl(c) {
-    const int rows = nbm / cl;  // schedule rows: tiles (cl == 1) or super-tiles (cl == 2)
+  int nbm, nbn, sym, n;
+  __device__ __host__ TileSched(int dp, int s) : nbm(dp / BM), nbn(dp / BN), sym(s) {
     if (!s) {
-      n = rows * nbn;
+      n = nbm * nbn;
     } else {
       n = 0;
-      for (int r = 0; r < rows; ++r) n += nbn - first(r);
+      for (int r = 0; r < nbm; ++r) n += nbn - first(r);
     }
   }
-  __device__ __host__ int first(int r) const { return sym ? (r * cl * BM) / BN : 0; }
-  // unit t -> (bm, bn) for cluster rank `rank`
-  __device__ __host__ void decode(int t, int rank, int& bm, int& bn) const {
-    const int rows = nbm / cl;
-    const int bh = 16 / cl;  // schedule rows per block (2048 matrix rows)
+  __device__ __host__ int first(int r) const { return sym ? (r * BM) / BN : 0; }
+  // unit t -> (bm, bn)
+  __device__ __host__ void decode(int t, int& bm, int& bn) const {
     int r = 0, c = 0;
-    for (int r0 = 0; r0 < rows; r0 += bh) {
-      const int r1 = r0 + bh < rows ? r0 + bh : rows;
+    for (int r0 = 0; r0 < nbm; r0 += kBH) {
+      const int r1 = r0 + kBH < nbm ? r0 + kBH : nbm;
       int cnt = 0;
       for (int q = r0; q < r1; ++q) cnt += nbn - first(q);
       if (t >= cnt) {
@@ -114,7 +111,7 @@ struct TileSched {
       }
       break;
     }
-    bm = cl == 1 ? r : 2 * r + rank;
+    bm = r;
     bn = c;
   }
 };
@@ -125,8 +122,8 @@ struct Unit {
   bool skip;
 };
 
-template <int BN, int CL>
-__device__ __forceinline__ Unit unit_at(const TcGemmArgs& a, const TileSched<BN>& s, int t, int rank) {
+template <int BN, int BKE>
+__device__ __forceinline__ Unit unit_at(const TcGemmArgs& a, const TileSched<BN>& s, int t) {
   Unit u;
   if (a.units != nullptr) {
     const int4 q = a.units[t];
@@ -134,13 +131,13 @@ __device__ __forceinline__ Unit unit_at(const TcGemmArgs& a, const TileSched<BN>
     u.bm = q.y;
     u.bn = q.z;
     u.slot = q.w;
-    u.n_kb = a.mat_dp[q.x] / BK;
+    u.n_kb = a.mat_dp[q.x] / BKE;
     u.skip = a.mat_skip != nullptr && a.mat_skip[q.x] != 0;
   } else {
-    s.decode(t, rank, u.bm, u.bn);
+    s.decode(t, u.bm, u.bn);
     u.mat = 0;
-    u.slot = t * CL + rank;
-    u.n_kb = a.dp / BK;
+    u.slot = t;
+    u.n_kb = a.dp / BKE;
     u.skip = false;
   }
   return u;
@@ -592,16 +589,21 @@ __device__ __forceinline__ void epilogue_oz_tmem(const TcGemmArgs& a, int i, int
   acc1 += (double)accf;
 }
 
-template <int EPI, typename T, int CL, int BN>
+template <int EPI, typename T, int BN>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ TcGemmArgs args, const uint32_t idesc) {
   using C = Cfg<BN>;
   constexpr int STAGES = C::STAGES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
+  // FP8 (E4M3) digit planes: the same 128-byte rows per stage hold 128
+  // elements of K, four kind::f8f6f4 MMAs of K = 32 each
+  constexpr bool F8 = sizeof(T) == 1;
+  constexpr int BKE = F8 ? kBK8 : BK;
+  static_assert(!F8 || EPI == TC_EPI_OZAKI, "FP8 operands only for the digit-plane products");
   // 128-column digit-plane products keep their int64 sums in TMEM columns 256..511
   constexpr bool OZ_TMEM = (EPI == TC_EPI_OZAKI && BN == 128);
   constexpr uint32_t TMEM_ALLOC = OZ_TMEM ? 512u : C::TMEM_COLS;
-  if (args.skip != nullptr && *args.skip != 0) return;  // uniform across the grid (and cluster)
+  if (args.skip != nullptr && *args.skip != 0) return;  // uniform across the grid
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -618,13 +620,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* status = args.status;
 
-  // cluster rank (pairs share the B panel); a stage of a pair is free only
-  // when the MMAs of both CTAs have consumed it
-  const int rank = CL == 2 ? (int)cluster_ctarank() : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), CL);
+      mbar_init(smem_u32(&empty[s]), 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&tfull[s]), 1);
@@ -642,14 +641,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tmem_relinquish();
   }
   tc_fence_before();
-  if constexpr (CL == 2) cluster_sync_all();  // peer barriers initialised before any multicast
-  else __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const TileSched<BN> sched(args.dp, args.sym, CL);
+  const TileSched<BN> sched(args.dp, args.sym);
   const int n_units = args.units != nullptr ? args.n_units : sched.n;
-  const int unit0 = blockIdx.x / CL, unit_step = gridDim.x / CL;
+  const int unit0 = blockIdx.x, unit_step = gridDim.x;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -658,7 +656,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0;
       bool ok = true;
       for (int t = unit0; ok && t < n_units; t += unit_step) {
-        const Unit u = unit_at<BN, CL>(args, sched, t, rank);
+        const Unit u = unit_at<BN, BKE>(args, sched, t);
         if (u.skip) continue;
         const int sa = u.mat * args.a_planes, sb = u.mat * args.b_planes;
         for (int g = 0; ok && g < args.n_groups; ++g) {
@@ -666,16 +664,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int kb = 0; kb < u.n_kb; ++kb) {
               if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, status)) { ok = false; break; }
               const uint32_t fb = smem_u32(&full[stage]);
-              // the full barrier counts all of the stage's bytes, including the
-              // half of B that the peer multicasts into this CTA
               mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
-              tma_load_3d(smem_u32(sA + stage * A_BYTES), &tmA, fb, kb * BK, u.bm * BM, sa + args.pair_a[pi]);
-              if constexpr (CL == 2) {
-                tma_load_3d_mc(smem_u32(sB + stage * B_BYTES + rank * (B_BYTES / 2)), &tmB, fb, kb * BK,
-                               u.bn * BN + rank * (BN / 2), sb + args.pair_b[pi], (uint16_t)0x3);
-              } else {
-                tma_load_3d(smem_u32(sB + stage * B_BYTES), &tmB, fb, kb * BK, u.bn * BN, sb + args.pair_b[pi]);
-              }
+              tma_load_3d(smem_u32(sA + stage * A_BYTES), &tmA, fb, kb * BKE, u.bm * BM, sa + args.pair_a[pi]);
+              tma_load_3d(smem_u32(sB + stage * B_BYTES), &tmB, fb, kb * BKE, u.bn * BN, sb + args.pair_b[pi]);
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
           }
@@ -697,7 +688,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int acc_it = 0;
       bool ok = true;
       for (int t = unit0; ok && t < n_units; t += unit_step) {
-        const Unit u = unit_at<BN, CL>(args, sched, t, rank);
+        const Unit u = unit_at<BN, BKE>(args, sched, t);
         if (u.skip) continue;
         for (int g = 0; ok && g < args.n_groups; ++g) {
           const int acc = acc_it & 1;
@@ -713,13 +704,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               const uint64_t ad = smem_desc_k128(smem_u32(sA + stage * A_BYTES));
               const uint64_t bd = smem_desc_k128(smem_u32(sB + stage * B_BYTES));
 #pragma unroll
-              for (int k = 0; k < BK / 16; ++k) {
-                // advance 16 elements (32 bytes) along K inside the swizzle atom
-                tc_mma_f16(d_tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accumulate);
+              for (int k = 0; k < 4; ++k) {
+                // advance 32 bytes along K inside the swizzle atom (16 FP16 or 32 FP8 elements)
+                if constexpr (F8) tc_mma_f8(d_tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accumulate);
+                else tc_mma_f16(d_tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accumulate);
                 accumulate = 1;
               }
-              if constexpr (CL == 2) tc_commit_mc(smem_u32(&empty[stage]), (uint16_t)0x3);
-              else tc_commit(smem_u32(&empty[stage]));
+              tc_commit(smem_u32(&empty[stage]));
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
           }
@@ -738,7 +729,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int acc_it = 0;
     bool ok = true;
     for (int t = unit0; ok && t < n_units; t += unit_step) {
-      const Unit u = unit_at<BN, CL>(args, sched, t, rank);
+      const Unit u = unit_at<BN, BKE>(args, sched, t);
       if (u.skip) continue;
       const int i = u.bm * BM + r;
       const size_t moff = (size_t)u.mat * (size_t)args.mat_stride;
@@ -792,11 +783,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 
   tc_fence_before();
-  // Every role has drained its own asynchronous work (bounded waits above);
-  // a pair also waits for the peer, whose multicast loads and commits target
-  // this CTA's shared memory, before either CTA leaves.
-  if constexpr (CL == 2) cluster_sync_all();
-  else __syncthreads();
+  // every role has drained its own asynchronous work (bounded waits above)
+  __syncthreads();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
@@ -824,153 +812,113 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+// lp_fmt: 0 FP16, 1 BF16, 2 FP8 E4M3 (bytes)
 bool make_map(CUtensorMap* m, const void* ptr, int dp, int slices, int box_rows, int lp_fmt) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
+  const cuuint64_t esz = lp_fmt == 2 ? 1 : 2;
   const cuuint64_t dims[3] = {(cuuint64_t)dp, (cuuint64_t)dp, (cuuint64_t)slices};
-  const cuuint64_t strides[2] = {(cuuint64_t)dp * 2, (cuuint64_t)dp * dp * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)dp * esz, (cuuint64_t)dp * dp * esz};
+  const cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = enc(m, lp_fmt ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-                         3, const_cast<void*>(ptr), dims, strides, box, es,
+  const CUtensorMapDataType dt = lp_fmt == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : (lp_fmt ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  const CUresult r = enc(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-template <int EPI, typename T, int CL, int BN>
+template <int EPI, typename T, int BN>
 cudaError_t launch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
                    uint32_t idesc, cudaStream_t st) {
   constexpr int SMEM_BYTES = Cfg<BN>::SMEM_BYTES;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<EPI, T, CL, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<EPI, T, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  if (CL > 1) {
-    // as many pairs as the GPCs can hold at once (the schedule is persistent)
-    static int max_clusters = -1;
-    static std::once_flag occ;
-    std::call_once(occ, [] {
-      cudaLaunchConfig_t q = {};
-      q.gridDim = dim3(2 * 64, 1, 1);
-      q.blockDim = dim3(NUM_THREADS, 1, 1);
-      q.dynamicSmemBytes = SMEM_BYTES;
-      cudaLaunchAttribute qa[1];
-      qa[0].id = cudaLaunchAttributeClusterDimension;
-      qa[0].val.clusterDim.x = CL;
-      qa[0].val.clusterDim.y = 1;
-      qa[0].val.clusterDim.z = 1;
-      q.attrs = qa;
-      q.numAttrs = 1;
-      int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<EPI, T, CL, BN>, &q) != cudaSuccess) {
-        cudaGetLastError();
-        n = 0;
-      }
-      max_clusters = n;
-    });
-    if (max_clusters > 0 && grid > CL * max_clusters) grid = CL * max_clusters;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid, 1, 1);
-  cfg.blockDim = dim3(NUM_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<EPI, T, CL, BN>, ma, mb, a, idesc);
+  tc_gemm_kernel<EPI, T, BN><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, a, idesc);
+  return cudaGetLastError();
 }
 
-template <typename T, int CL>
+template <typename T>
 cudaError_t dispatch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
                      uint32_t idesc, cudaStream_t st) {
   switch (a.epi) {
-    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T, CL, 256>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, CL, 256>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, CL, 256>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, CL, 256>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_OZAKI: return launch<TC_EPI_OZAKI, T, CL, 256>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_TANGENT: return launch<TC_EPI_TANGENT, T, CL, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_OZAKI: return launch<TC_EPI_OZAKI, T, 256>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_TANGENT: return launch<TC_EPI_TANGENT, T, 256>(a, ma, mb, grid, idesc, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-// grouped launches: one CTA per SM at most, no clusters, BN = 128 or 256
+// grouped launches: one CTA per SM at most, BN = 128 or 256
 template <typename T, int BN>
 cudaError_t dispatch_grouped(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid,
                              uint32_t idesc, cudaStream_t st) {
   switch (a.epi) {
-    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T, 1, BN>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, 1, BN>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, 1, BN>(a, ma, mb, grid, idesc, st);
-    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, 1, BN>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_F32: return launch<TC_EPI_STORE_F32, T, BN>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_STORE_LP: return launch<TC_EPI_STORE_LP, T, BN>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_SYRK: return launch<TC_EPI_NS_SYRK, T, BN>(a, ma, mb, grid, idesc, st);
+    case TC_EPI_NS_UPDATE: return launch<TC_EPI_NS_UPDATE, T, BN>(a, ma, mb, grid, idesc, st);
     case TC_EPI_OZAKI:
-      if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value)
-        return launch<TC_EPI_OZAKI, T, 1, BN>(a, ma, mb, grid, idesc, st);
+      if constexpr (std::is_same<T, __half>::value)
+        return launch<TC_EPI_OZAKI, T, BN>(a, ma, mb, grid, idesc, st);
       else
-        return cudaErrorInvalidValue;  // digit planes are FP16
+        return cudaErrorInvalidValue;  // digit planes are FP16 or FP8 (dispatched apart)
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-int tc_num_tiles(int dp, int sym) { return TileSched<256>(dp, sym, 1).n; }
+int tc_num_tiles(int dp, int sym) { return TileSched<256>(dp, sym).n; }
 
-int tc_tile_order(int dp, int sym, int cl, int* bm, int* bn) {
-  const TileSched<256> sc(dp, sym, cl == 2 ? 2 : 1);
-  for (int t = 0; t < sc.n; ++t)
-    for (int rk = 0; rk < sc.cl; ++rk) sc.decode(t, rk, bm[t * sc.cl + rk], bn[t * sc.cl + rk]);
-  return sc.n * sc.cl;
-}
-
-static int g_default_cluster = 2;
-int tc_set_default_cluster(int cl) {
-  const int prev = g_default_cluster;
-  g_default_cluster = (cl == 1) ? 1 : 2;
-  return prev;
+int tc_tile_order(int dp, int sym, int* bm, int* bn) {
+  const TileSched<256> sc(dp, sym);
+  for (int t = 0; t < sc.n; ++t) sc.decode(t, bm[t], bn[t]);
+  return sc.n;
 }
 
 cudaError_t tc_gemm(const TcGemmArgs& args, const void* A, int a_slices, const void* B, int b_slices,
                     int lp_fmt, int num_sms, cudaStream_t st) {
   if (args.units != nullptr || args.dp % 256 != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
-      args.group_start[args.n_groups] > kTcMaxPairs)
+      args.group_start[args.n_groups] > kTcMaxPairs || lp_fmt < 0 || lp_fmt > 2)
     return cudaErrorInvalidValue;
-  // cluster pairs (B panel multicast) unless args.cluster == 1
-  const int cl = args.cluster == 0 ? g_default_cluster : (args.cluster == 1 ? 1 : 2);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) ||
-      !make_map(&mb, B, args.dp, b_slices, 256 / cl, lp_fmt))
+  if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) || !make_map(&mb, B, args.dp, b_slices, 256, lp_fmt))
     return cudaErrorInvalidValue;
-  const int units = TileSched<256>(args.dp, args.sym, cl).n;
-  const int max_units = num_sms / cl;
-  const int grid = cl * (units < max_units ? units : max_units);
+  const int units = TileSched<256>(args.dp, args.sym).n;
+  const int grid = units < num_sms ? units : num_sms;
+  if (lp_fmt == 2)  // FP8 E4M3 digit planes (format field 0 of kind::f8f6f4)
+    return args.epi == TC_EPI_OZAKI
+               ? launch<TC_EPI_OZAKI, __nv_fp8_e4m3, 256>(args, ma, mb, grid, idesc_f16(0u, BM, 256), st)
+               : cudaErrorInvalidValue;
   const uint32_t idesc = idesc_f16(lp_fmt ? 1u : 0u, BM, 256);
-  if (cl == 2)
-    return lp_fmt ? dispatch<__nv_bfloat16, 2>(args, ma, mb, grid, idesc, st)
-                  : dispatch<__half, 2>(args, ma, mb, grid, idesc, st);
-  return lp_fmt ? dispatch<__nv_bfloat16, 1>(args, ma, mb, grid, idesc, st)
-                : dispatch<__half, 1>(args, ma, mb, grid, idesc, st);
+  return lp_fmt ? dispatch<__nv_bfloat16>(args, ma, mb, grid, idesc, st)
+                : dispatch<__half>(args, ma, mb, grid, idesc, st);
 }
 
 cudaError_t tc_gemm_grouped(const TcGemmArgs& args, int bn, const void* A, int a_slices, const void* B,
                             int b_slices, int lp_fmt, int num_sms, cudaStream_t st) {
   if (args.units == nullptr || args.n_units < 1 || args.mat_dp == nullptr || args.mat_d == nullptr ||
       (bn != 128 && bn != 256) || args.dp % 256 != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
-      args.group_start[args.n_groups] > kTcMaxPairs || (args.epi == TC_EPI_OZAKI && lp_fmt != 0))
+      args.group_start[args.n_groups] > kTcMaxPairs || (args.epi == TC_EPI_OZAKI && lp_fmt == 1) ||
+      (args.epi != TC_EPI_OZAKI && lp_fmt == 2) || lp_fmt < 0 || lp_fmt > 2)
     return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) || !make_map(&mb, B, args.dp, b_slices, bn, lp_fmt))
     return cudaErrorInvalidValue;
   const int grid = args.n_units < num_sms ? args.n_units : num_sms;
+  if (lp_fmt == 2)
+    return bn == 128 ? launch<TC_EPI_OZAKI, __nv_fp8_e4m3, 128>(args, ma, mb, grid, idesc_f16(0u, BM, 128), st)
+                     : launch<TC_EPI_OZAKI, __nv_fp8_e4m3, 256>(args, ma, mb, grid, idesc_f16(0u, BM, 256), st);
   const uint32_t idesc = idesc_f16(lp_fmt ? 1u : 0u, BM, bn);
   if (bn == 128)
     return lp_fmt ? dispatch_grouped<__nv_bfloat16, 128>(args, ma, mb, grid, idesc, st)

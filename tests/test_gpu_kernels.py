@@ -51,21 +51,16 @@ def test_tc_gemm_symmetric_schedule(dp, fmt):
     _check_fp32_accumulation(torch, out, ref, X.float().abs() @ X.float().abs(), dp)
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
 @pytest.mark.parametrize("dp,sym", [(512, 0), (1536, 1), (4096, 0), (4096, 1)])
-def test_tc_gemm_cluster_variants_agree(cluster, dp, sym):
-    # independent CTAs and cluster pairs (B panel multicast) give identical bits
+def test_tc_gemm_repeats_bit_for_bit(dp, sym):
+    # the persistent schedule is static: two launches on the same operands
+    # give identical bits (and match FP32 accumulation)
     torch = cuda_or_skip()
     rs = lib_or_fail()
     X = _rand(torch, dp, torch.float16, 99 + dp, sym=bool(sym))
     Y = X if sym else _rand(torch, dp, torch.float16, 98 + dp)
-    prev = rs.dbg_set_tc_cluster(cluster)
-    try:
-        out, status = rs.dbg_tc_gemm(X, Y, fmt=0, sym=sym)
-        rs.dbg_set_tc_cluster(3 - cluster)
-        out2, status2 = rs.dbg_tc_gemm(X, Y, fmt=0, sym=sym)
-    finally:
-        rs.dbg_set_tc_cluster(prev)
+    out, status = rs.dbg_tc_gemm(X, Y, fmt=0, sym=sym)
+    out2, status2 = rs.dbg_tc_gemm(X, Y, fmt=0, sym=sym)
     torch.cuda.synchronize()
     assert int(status.item()) == 0 and int(status2.item()) == 0
     assert torch.equal(out, out2)
@@ -116,6 +111,70 @@ def test_fp64grade_product_matches_fp64(dp, d_real, sym):
     assert ((out - ref).abs() - bound).max().item() <= 0.0
     if sym:
         assert (out - out.T).abs().max().item() == 0.0
+
+
+@pytest.mark.parametrize("dp,d_real,sym,kind", [(256, 200, 1, "random"), (1024, 1000, 0, "random"),
+                                                (2048, 2048, 1, "coherent"), (4096, 4096, 0, "random"),
+                                                (8192, 8192, 1, "coherent"), (8192, 8192, 0, "random"),
+                                                (16384, 16384, 1, "coherent")])
+def test_fp8_digit_planes_give_the_fp16_bits(dp, d_real, sym, kind):
+    # The 5-bit balanced digits (|d| <= 16) are exact in E4M3 and each level
+    # group sums to an integer below 2^24, so the kind::f8f6f4 product must
+    # reproduce the kind::f16 product bit for bit.  "coherent" operands have
+    # every off-diagonal entry in [1.5, 2) (leading digits 12..16, all of one
+    # sign): each level sum comes near its 2^24 bound, where an accumulator
+    # narrower than 24 bits would drop bits.
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    g = torch.Generator(device="cuda").manual_seed(11 * dp + d_real)
+    A = torch.zeros((dp, dp), device="cuda", dtype=torch.float64)
+    if kind == "coherent":
+        a = 1.5 + 0.5 * torch.rand((d_real, d_real), generator=g, device="cuda", dtype=torch.float64)
+    else:
+        a = torch.randn((d_real, d_real), generator=g, device="cuda", dtype=torch.float64)
+    A[:d_real, :d_real] = 0.5 * (a + a.T)
+    A.diagonal()[:d_real] += 3.0
+    if sym:
+        B = A
+    else:
+        B = torch.zeros_like(A)
+        b = torch.randn((d_real, d_real), generator=g, device="cuda", dtype=torch.float64)
+        B[:d_real, :d_real] = 0.5 * (b + b.T)
+    prev = rs.dbg_set_digit_fp8(0)
+    try:
+        out16 = rs.dbg_fp64grade_gemm(A, B, d_real=d_real, sym=sym)
+        rs.dbg_set_digit_fp8(1)
+        out8 = rs.dbg_fp64grade_gemm(A, B, d_real=d_real, sym=sym)
+    finally:
+        rs.dbg_set_digit_fp8(prev)
+    torch.cuda.synchronize()
+    assert torch.equal(out8, out16)
+    ref = A @ B
+    rmax = (A - torch.diag(torch.diagonal(A))).abs().amax(dim=1, keepdim=True)
+    cmax = (B - torch.diag(torch.diagonal(B))).abs().amax(dim=1, keepdim=True).T
+    bound = 1e-9 * (d_real ** 0.5) * rmax * cmax + 1e-13 * (A.abs() @ B.abs())
+    assert ((out8 - ref).abs() - bound).max().item() <= 0.0
+
+
+@pytest.mark.parametrize("d,k", [(1024, 16), (3000, 40), (8192, 16)])
+def test_refinement_with_fp8_digits_gives_the_same_reflector(d, k):
+    # the whole FP16_REFINE call with FP8 and with FP16 digit planes: the same bits
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    import workloads
+    H, lam, Q = workloads.controlled_spectrum_torch(d, k, 1e-2, seed=3 * d + k)
+    outs = []
+    prev = rs.dbg_set_digit_fp8(0)
+    try:
+        for f8 in (0, 1):
+            rs.dbg_set_digit_fp8(f8)
+            R, info, st = rs.reflector(H, k, 0.0, tol=1e-6, policy=rs.Policy.FP16_REFINE, check=False)
+            assert st == rs.Status.OK, (st, info.as_dict())
+            outs.append(R.clone())
+    finally:
+        rs.dbg_set_digit_fp8(prev)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1])
 
 
 @pytest.mark.parametrize("dp,d_real,sym", [(256, 200, 1), (512, 512, 0), (1024, 1000, 1), (8192, 8192, 1)])
@@ -213,7 +272,7 @@ def test_commutator_check_matches_fp64_power_steps(d, dp):
 @pytest.mark.parametrize("d,k", [(1024, 16), (1280, 640)])
 def test_refinement_products_same_bits_on_both_tile_widths(d, k):
     # the FP64-grade products are exact integer level sums converted once, so
-    # the 128-wide (int64 sums in TMEM) and 256-wide (cluster pairs, sums in
+    # the 128-wide (int64 sums in TMEM) and 256-wide (sums in
     # global memory) launches give the same reflector bit for bit
     torch = cuda_or_skip()
     rs = lib_or_fail()

@@ -146,17 +146,21 @@ def test_diagonal_input_exact():
 
 
 @pytest.mark.parametrize("nv", [1, 3, 16])
-def test_apply_matches_numpy(nv):
+def test_apply_matches_the_oracle_product(nv):
+    # out = R V (Eq. discrete_step directions) against the oracle's plain FP64
+    # triple loop; |error| <= 2 d u sum_k |R_ik V_kj| per entry
     torch = cuda_or_skip()
     rs = lib_or_fail()
     d = 777
     rng = np.random.default_rng(nv)
     Rm = rng.standard_normal((d, d))
     V = rng.standard_normal((d, nv))
+    want = oracle.matmul(Rm, V)
+    bound = 2.0 * d * np.finfo(np.float64).eps * oracle.matmul(np.abs(Rm), np.abs(V))
     out = rs.apply(torch.from_numpy(Rm).cuda(), torch.from_numpy(V).cuda()).cpu().numpy()
-    assert np.max(np.abs(out - Rm @ V)) < 1e-11
+    assert np.all(np.abs(out - want) <= bound)
     out_h = rs.apply(Rm, V)  # host buffers
-    assert np.max(np.abs(out_h - Rm @ V)) < 1e-11
+    assert np.all(np.abs(out_h - want) <= bound)
 
 
 def test_direction_error_bound():
@@ -210,6 +214,30 @@ def test_auto_shift_plain_method_d256():
     assert abs(info.lam_k1_est - lk1) <= info.shift_eps + 1e-12
     assert 0 < info.margin_lb <= oracle.margin(info.shift, lk, lk1) + 1e-12
     assert info.lanczos_iters > 0 and info.steps_pred > 0
+
+
+@pytest.mark.parametrize("d,k,delta,policy,tol", [(256, 4, None, "FP64", 1e-12), (512, 3, 2e-2, "FP16_REFINE", 1e-7),
+                                                   (1000, 990, 5e-2, "FP64", 1e-10)])
+def test_auto_shift_step_prediction_matches_the_oracle(d, k, delta, policy, tol):
+    # Prop. 3.6 / Eq. pm: the predicted depth m* = min m with eps_m(gamma_hat) <= tol,
+    # gamma_hat = alpha (m_hat - eps) from the certified margin, equals the
+    # oracle's scalar recurrence at the reported gamma_hat; and since the
+    # certified margin is a lower bound of the true one (Prop. 4.2), the true
+    # gamma needs no more steps than predicted
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    if delta is None:
+        spec = workloads.split_spectrum_config(seed=0)
+    else:
+        spec = workloads.controlled_spectrum(d, k, delta, seed=910 + d + k)
+    R, info, st = _run(rs, torch, spec.H, k, float("nan"), rs.Policy[policy], tol=tol)
+    assert st == rs.Status.OK and info.cert_ok == 1, (st, info.as_dict())
+    assert info.gamma_est == pytest.approx(info.alpha * info.margin_lb, rel=1e-15)
+    assert info.steps_pred == oracle.ns_steps(info.gamma_est, tol)
+    assert oracle.eps_m(info.gamma_est, info.steps_pred) <= tol < oracle.eps_m(info.gamma_est, info.steps_pred - 1)
+    true_gamma = info.alpha * oracle.margin(info.shift, *spec.gap)
+    assert info.gamma_est <= true_gamma
+    assert oracle.ns_steps(true_gamma, tol) <= info.steps_pred
 
 
 @pytest.mark.parametrize("d,k,delta", [(300, 290, 5e-2), (512, 3, 2e-2)])
@@ -494,7 +522,8 @@ def test_power_of_two_scaling_gives_the_same_bits(policy, e):
 
 
 def test_apply_full_size_sampled_rows():
-    # out = R V at d = 8192, nv = 16 (device buffers): 64 seeded rows against numpy
+    # out = R V at d = 8192, nv = 16 (device buffers): 64 seeded rows against
+    # the oracle's triple-loop product of those rows
     torch = cuda_or_skip()
     rs = lib_or_fail()
     d, nv = 8192, 16
@@ -507,4 +536,6 @@ def test_apply_full_size_sampled_rows():
     Rh = Rm[torch.from_numpy(rows).cuda()].cpu().numpy()
     Vh = V.cpu().numpy()
     got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
-    assert np.max(np.abs(got - Rh @ Vh)) < 1e-10
+    want = oracle.matmul(Rh, Vh)
+    bound = 2.0 * d * np.finfo(np.float64).eps * oracle.matmul(np.abs(Rh), np.abs(Vh))
+    assert np.all(np.abs(got - want) <= bound)
