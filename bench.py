@@ -52,6 +52,14 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 Newton-Schulz comparator")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-plain", action="store_true", help="skip the margin-free (plain steps) figure")
+    p.add_argument("--split-steps", type=int, default=-2,
+                   help="REFINE stage 1: iterates X_0..X_{n-1} as hi/lo pairs, later ones single planes "
+                        "(-1 all pairs, 0 none; -2 the library default)")
+    p.add_argument("--low-split", type=int, default=1, choices=[0, 1],
+                   help="REFINE stage 1 hi/lo pairs at all (0: single planes throughout)")
+    p.add_argument("--max-sweeps", type=int, default=4)
+    p.add_argument("--oz-tile", type=int, default=-1, choices=[-1, 0, 128, 256],
+                   help="tile width of the FP64-grade products (128: level sums in TMEM; -1 the library default)")
     p.add_argument("--digit-fp8", type=int, default=-1, choices=[-1, 0, 1],
                    help="digit planes of the FP64-grade products: 1 FP8 E4M3, 0 FP16, -1 the library default")
     p.add_argument("--no-batched", action="store_true", help="skip the batched-workload figure")
@@ -293,6 +301,10 @@ def run_rsign(args):
     rs.load()
     if args.digit_fp8 >= 0:
         rs.dbg_set_digit_fp8(args.digit_fp8)
+    if args.split_steps >= -1:
+        rs.dbg_set_split_steps(args.split_steps)
+    if args.oz_tile >= 0:
+        rs.dbg_set_ozaki_tile(args.oz_tile)
     policy = rs.Policy[args.policy]
     seed = workloads.controlled_seed(args.d, 1, 1) + rank
     H, lam, Q = workloads.controlled_spectrum_torch(args.d, args.k, args.delta, seed, device=dev)
@@ -302,7 +314,8 @@ def run_rsign(args):
     margin = float(min(s - lam_h[args.k - 1], lam_h[args.k] - s))
     opt = rs.default_options(alpha_mode=int(rs.AlphaMode.POWER if args.alpha == "power" else rs.AlphaMode.INF),
                              ns_scaling=1 if args.engine == "scaled" else 0, margin=margin,
-                             engine=int(rs.Engine.NS5 if args.engine == "ns5" else rs.Engine.NS3))
+                             engine=int(rs.Engine.NS5 if args.engine == "ns5" else rs.Engine.NS3),
+                             low_split=args.low_split, max_sweeps=args.max_sweeps)
     stream = torch.cuda.current_stream(dev)
 
     def call(Hin, Rout, pol=policy, tol=args.tol):

@@ -120,13 +120,25 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
 
 /*
  * Storage of the 5-bit digit planes of the FP64-grade products (the
- * refinement's R A and R^2, and rsign_dbg_fp64grade_gemm): 1 = FP8 E4M3
- * bytes multiplied on the kind::f8f6f4 tensor cores, 0 = FP16 on kind::f16.
+ * refinement's R A and R^2, and rsign_dbg_fp64grade_gemm): 1 (the default)
+ * = FP8 E4M3 bytes multiplied on the kind::f8f6f4 tensor cores, 0 = FP16 on
+ * kind::f16.
  * The digits (|d| <= 16) are exact in both formats and every level sum is
  * the same integer, so the two settings give the same bits.  Other values
  * leave the setting unchanged.  Process-wide; returns the previous setting.
  */
 int32_t rsign_dbg_set_digit_fp8(int32_t on);
+
+/*
+ * Low-precision stage of the *_REFINE policies: the iterates X_0 .. X_{n-1}
+ * are carried as hi/lo pairs of FP16/BF16 planes (three pair products per
+ * launch), later ones as single planes (one product per launch, the plain
+ * format's rounding).  n = -1 (the default) carries every iterate as a pair;
+ * n = 0 none.  Values below -1 leave the setting unchanged.  Process-wide;
+ * returns the previous setting.  For measurements of the trade-off between
+ * the stage's cost and the refinement sweeps its rounding leaves to do.
+ */
+int32_t rsign_dbg_set_split_steps(int32_t n);
 
 /*
  * Failure path of the bounded pipeline waits (the mbarrier waits of every

@@ -196,6 +196,8 @@ def load():
     lib.rsign_dbg_set_refine_levels.restype = i32
     lib.rsign_dbg_set_ozaki_tile.argtypes = [i32]
     lib.rsign_dbg_set_ozaki_tile.restype = i32
+    lib.rsign_dbg_set_split_steps.argtypes = [i32]
+    lib.rsign_dbg_set_split_steps.restype = i32
     lib.rsign_dbg_set_digit_fp8.argtypes = [i32]
     lib.rsign_dbg_set_digit_fp8.restype = i32
     lib.rsign_dbg_bounded_wait.argtypes = [i32, i64, vp, vp]
@@ -589,6 +591,12 @@ def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def dbg_set_split_steps(n):
+    """REFINE stage 1: iterates X_0..X_{n-1} as hi/lo pairs, later ones single planes (-1: all pairs);
+    returns the previous setting."""
+    return int(load().rsign_dbg_set_split_steps(int(n)))
 
 
 def dbg_set_digit_fp8(on):

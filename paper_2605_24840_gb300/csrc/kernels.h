@@ -89,6 +89,8 @@ struct TcGemmArgs {
   const int* skip;         // optional: kernel returns at once when *skip != 0
   int split;               // TC_EPI_NS_*: operands/outputs are hi/lo pairs of planes
                            // (plane stride dp*dp); out = hi + lo carries ~2x the bits
+  int single_out;          // with split: write the result's hi plane only (the step
+                           // after this one runs on single planes)
   // TC_EPI_OZAKI with diagonal-free digit planes: the first group adds the
   // exact FP64 diagonal terms d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
   const double* a_full;    // FP64 A (dp x dp), or nullptr

@@ -40,12 +40,19 @@ __device__ __forceinline__ uint32_t e4m3_of_int(int n) {
   return (n < 0 ? 0x80u : 0u) | ((uint32_t)(e + 7) << 3) | mant;
 }
 
-// Two digits of one plane at columns k, k + 1 as FP16 (half2) or FP8 (two bytes)
-__device__ __forceinline__ void store_digit_pair(__half* planes, size_t idx, int d0, int d1) {
-  *reinterpret_cast<__half2*>(planes + idx) = __halves2half2(__int2half_rn(d0), __int2half_rn(d1));
+// Four digits of one plane at columns k .. k + 3 as FP16 (one 8-byte store)
+// or FP8 E4M3 (one 4-byte store)
+__device__ __forceinline__ void store_digit_quad(__half* planes, size_t idx, const int* dg) {
+  const __half2 a = __halves2half2(__int2half_rn(dg[0]), __int2half_rn(dg[1]));
+  const __half2 b = __halves2half2(__int2half_rn(dg[2]), __int2half_rn(dg[3]));
+  uint2 w;
+  w.x = *reinterpret_cast<const uint32_t*>(&a);
+  w.y = *reinterpret_cast<const uint32_t*>(&b);
+  *reinterpret_cast<uint2*>(planes + idx) = w;
 }
-__device__ __forceinline__ void store_digit_pair(uint8_t* planes, size_t idx, int d0, int d1) {
-  *reinterpret_cast<uint16_t*>(planes + idx) = (uint16_t)(e4m3_of_int(d0) | (e4m3_of_int(d1) << 8));
+__device__ __forceinline__ void store_digit_quad(uint8_t* planes, size_t idx, const int* dg) {
+  *reinterpret_cast<uint32_t*>(planes + idx) =
+      e4m3_of_int(dg[0]) | (e4m3_of_int(dg[1]) << 8) | (e4m3_of_int(dg[2]) << 16) | (e4m3_of_int(dg[3]) << 24);
 }
 
 // Digit planes of one row per warp (8 rows per block; grid.y = matrix).
@@ -55,8 +62,8 @@ __device__ __forceinline__ void store_digit_pair(uint8_t* planes, size_t idx, in
 // fixed-point integer n = round(M_ik 2^(62 - ex)), |n| < 2^61, by a shift of
 // its significand, and the balanced base-2^beta digits are peeled off with
 // shifts; the FP64 pipe of this GPU is far slower than its integer pipe.
-// Lane l handles the column pairs 2 l + 64 t, 2 l + 64 t + 1 (half2 or
-// two-byte stores).
+// Lane l handles the columns 4 l + 128 t .. 4 l + 128 t + 3 (two 16-byte
+// loads, one 8- or 4-byte store per plane); row lengths are multiples of 128.
 template <typename D>
 __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrows, D* __restrict__ planes,
                                   double* __restrict__ sigma, double* __restrict__ diag, int n_planes,
@@ -69,10 +76,15 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrow
   const size_t slot = (size_t)ld * ld;
   const long long* row = reinterpret_cast<const long long*>(M + (size_t)m * slot + (size_t)i * ld);
   long long mx = 0;
-  for (int k = 2 * lane; k < ncols; k += 64) {
-    const long long b0 = row[k] & 0x7FFFFFFFFFFFFFFFll, b1 = row[k + 1] & 0x7FFFFFFFFFFFFFFFll;
-    if (k != i || keep_diag) mx = b0 > mx ? b0 : mx;
-    if (k + 1 != i || keep_diag) mx = b1 > mx ? b1 : mx;
+  for (int k = 4 * lane; k < ncols; k += 128) {
+    const longlong2 a = *reinterpret_cast<const longlong2*>(row + k);
+    const longlong2 b = *reinterpret_cast<const longlong2*>(row + k + 2);
+    const long long bb[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const long long mag = bb[h] & 0x7FFFFFFFFFFFFFFFll;
+      if (k + h != i || keep_diag) mx = mag > mx ? mag : mx;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -92,11 +104,14 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrow
     diag[(size_t)m * ld + i] = __longlong_as_double(row[i]);
   }
   D* pl = planes + (size_t)m * n_planes * slot + (size_t)i * ld;
-  for (int k = 2 * lane; k < ncols; k += 64) {
-    long long n[2];
+  for (int k = 4 * lane; k < ncols; k += 128) {
+    const longlong2 a = *reinterpret_cast<const longlong2*>(row + k);
+    const longlong2 b = *reinterpret_cast<const longlong2*>(row + k + 2);
+    const long long bb[4] = {a.x, a.y, b.x, b.y};
+    long long n[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const long long bits = row[k + h];
+    for (int h = 0; h < 4; ++h) {
+      const long long bits = bb[h];
       long long v = 0;
       if ((k + h != i || keep_diag) && (bits & 0x7FFFFFFFFFFFFFFFll) != 0) {  // diagonal kept apart unless keep_diag
         unsigned long long mant;
@@ -113,13 +128,14 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrow
     }
     for (int p = 0; p < n_planes; ++p) {
       const int sh = 62 - beta * (p + 1);  // weight of digit p: 2^sh
-      long long dg[2];
+      int dg[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        dg[h] = (n[h] + (1ll << (sh - 1))) >> sh;  // nearest, |dg| <= 2^(beta-1)
-        n[h] -= dg[h] * (1ll << sh);               // |n| <= 2^(sh-1)
+      for (int h = 0; h < 4; ++h) {
+        const long long q = (n[h] + (1ll << (sh - 1))) >> sh;  // nearest, |q| <= 2^(beta-1)
+        n[h] -= q * (1ll << sh);                              // |n| <= 2^(sh-1)
+        dg[h] = (int)q;
       }
-      store_digit_pair(pl, (size_t)p * slot + k, (int)dg[0], (int)dg[1]);
+      store_digit_quad(pl, (size_t)p * slot + k, dg);
     }
   }
 }

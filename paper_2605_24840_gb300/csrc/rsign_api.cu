@@ -357,10 +357,17 @@ constexpr int kExactDiagMin = 1024;
 // the index is small against d (measured at d = 8192, k = 16), else six.
 int g_levels_polish = 0, g_levels_ra0 = 0, g_levels_ra = kSlices;
 // Digit planes of the refinement's FP64-grade products as FP8 E4M3 bytes on
-// the kind::f8f6f4 tensor cores (1) or as FP16 (0).  The 5-bit balanced
-// digits (|digit| <= 16) are exact in E4M3, the level sums are the same
-// integers either way, so both give the same bits.
-int g_digit_fp8 = 0;
+// the kind::f8f6f4 tensor cores (1, the default) or as FP16 (0).  The 5-bit
+// balanced digits (|digit| <= 16) are exact in E4M3 and the level sums are
+// the same integers either way, so both give the same bits; FP8 has twice
+// the tensor rate and half the operand bytes (measured at d = 8192: the two
+// products of a FP16_REFINE call 18.4 -> 12.1 ms).
+int g_digit_fp8 = 1;
+// Stage-1 iterates carried as hi/lo pairs by the *_REFINE policies: X_0 ..
+// X_{S-1} with S = g_split_steps, every iterate for S < 0 (the default).
+// Later steps run on single FP16/BF16 planes (three times fewer pair
+// products per launch, at the plain format's rounding).
+int g_split_steps = -1;
 int levels_for(int set, double tol, int d, int k) {
   if (set > 0) return set;
   const bool few = 32 * std::min(k, d - k) <= d;
@@ -936,6 +943,10 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     // calls, d <= 1024, stay bitwise equal to one-matrix calls)
     float* rowsq = nullptr;
     if (d > kExactDiagMin && mem.alloc((void**)&rowsq, (size_t)dp * 4) != cudaSuccess) return fail_cuda();
+    // iterate X_m as a hi/lo pair (refinement: the leading g_split_steps only
+    // when that is set), and the floors of the stop test for its format
+    auto x_split = [&](int mi) { return split && (!refine || g_split_steps < 0 || mi < g_split_steps); };
+    const double u1 = unit_roundoff(fmt);
     int m = 0;
     bool stopped = false;
     while (m <= opt.max_steps && !stopped) {
@@ -945,28 +956,33 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         void* em = slot_e(mm);
         void* xn = (mm < opt.max_steps) ? slot_x(mm + 1) : xm;
         if (!xm || !em || !xn) return fail_cuda();
+        const bool sp = x_split(mm);
+        const double um = sp ? u : u1;
         TcGemmArgs sy{};
         sy.dp = dp; sy.d_real = d; sy.sym = 1; sy.epi = TC_EPI_NS_SYRK; sy.n_groups = 1;
         sy.group_start[0] = 0; sy.pair_a[0] = 0; sy.pair_b[0] = 0;
-        if (split) {  // hi*hi + hi*lo + lo*hi in one accumulator
+        if (sp) {  // hi*hi + hi*lo + lo*hi in one accumulator
           sy.pair_a[1] = 0; sy.pair_b[1] = 1; sy.pair_a[2] = 1; sy.pair_b[2] = 0;
           sy.group_start[1] = 3;
         } else {
           sy.group_start[1] = 1;
         }
-        sy.split = split ? 1 : 0;
+        sy.split = sp ? 1 : 0;
         sy.group_scale[0] = 1.0; sy.scale = 1.0f; sy.out = em; sy.partials = partials;
         sy.status = &ctl->status; sy.skip = &ctl->done_low;
         const double am = mm < (int)coef.size() ? coef[mm] : 1.0;
         sy.ns_c2 = (float)(am * am);
         sy.ns_c1 = (float)am;
         sy.ns_diag = rowsq;
-        if (rowsq && !c.ok(row_sumsq(xm, fmt, split ? 1 : 0, dp, d, rowsq, &ctl->done_low, st))) return fail_cuda();
+        if (rowsq && !c.ok(row_sumsq(xm, fmt, sp ? 1 : 0, dp, d, rowsq, &ctl->done_low, st))) return fail_cuda();
         if (!c.ok(tc_gemm(sy, xm, planes, xm, planes, fmt, c.num_sms, st))) return fail_cuda();
         const bool floors = mm >= m_min;
-        if (!c.ok(ns_check(partials, nt * 4, hist_low, mm, 0.0, floors ? floor_lo : -1.0, floors ? floor_hi : -1.0,
+        const double fl_lo = sp ? floor_lo : 2.0 * um * std::sqrt((double)d);
+        const double fl_hi = sp ? floor_hi : 16.0 * um * std::sqrt((double)d);
+        const double tr_tol_m = sp ? tr_tol : 0.5 + 2.0 * um * std::sqrt((double)d);
+        if (!c.ok(ns_check(partials, nt * 4, hist_low, mm, 0.0, floors ? fl_lo : -1.0, floors ? fl_hi : -1.0,
                            0.5, &ctl->done_low, &ctl->steps_low, st, mm >= 1 ? tr_part : nullptr, nt * 4,
-                           (double)(d - 2 * k), tr_tol)))
+                           (double)(d - 2 * k), tr_tol_m)))
           return fail_cuda();
         if (mm == opt.max_steps) break;
         void* bm = em;
@@ -980,6 +996,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         }
         TcGemmArgs up = sy;
         up.epi = TC_EPI_NS_UPDATE; up.out = xn; up.xin = xm; up.partials = tr_part;
+        up.single_out = (sp && !x_split(mm + 1)) ? 1 : 0;
         if (!c.ok(tc_gemm(up, xm, planes, bm, planes, fmt, c.num_sms, st))) return fail_cuda();
       }
       if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -990,7 +1007,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       m = m_end;
     }
     steps_low = stopped ? ctl_h.steps_low : opt.max_steps;
-    if (split) {
+    if (x_split(steps_low)) {
       if (!c.ok(split_to_f64(slot_x(steps_low), fmt, dd, xb64[0], st))) return fail_cuda();
     } else {
       if (!c.ok(to_f64(slot_x(steps_low), fmt, dd, xb64[0], st))) return fail_cuda();
@@ -1670,6 +1687,12 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
   if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
   cudaGetLastError();
   return res;
+}
+
+int32_t rsign_dbg_set_split_steps(int32_t n) {
+  const int prev = g_split_steps;
+  if (n >= -1) g_split_steps = n;
+  return prev;
 }
 
 int32_t rsign_dbg_set_digit_fp8(int32_t on) {

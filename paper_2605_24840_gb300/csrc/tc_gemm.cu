@@ -332,24 +332,27 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
           if (j0 + jj == i) {
             const T h = from_f32<T>(v[jj]);
             acc1 += (double)to_f32<T>(h);
-            if (a.split) acc1 += (double)to_f32<T>(from_f32<T>(v[jj] - to_f32<T>(h)));
+            if (a.split && !a.single_out) acc1 += (double)to_f32<T>(from_f32<T>(v[jj] - to_f32<T>(h)));
           }
       }
     }
+    // the result is written as a hi/lo pair when the operands were (unless
+    // single_out asks for the hi plane alone: the next step runs unsplit)
+    const bool lo_out = a.split && !a.single_out;
     float lo[32];
-    if (a.split) {
+    if (lo_out) {
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) lo[jj] = v[jj] - to_f32<T>(from_f32<T>(v[jj]));
     }
     store32_lp<T>(out + row + j0, v);
-    if (a.split) store32_lp<T>(out + plane + row + j0, lo);
+    if (lo_out) store32_lp<T>(out + plane + row + j0, lo);
     if (!above) __syncwarp();
     {
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         if (!above && j0 + jj <= i) continue;
         out[(size_t)(j0 + jj) * ld + i] = from_f32<T>(v[jj]);
-        if (a.split) out[plane + (size_t)(j0 + jj) * ld + i] = from_f32<T>(lo[jj]);
+        if (lo_out) out[plane + (size_t)(j0 + jj) * ld + i] = from_f32<T>(lo[jj]);
       }
     }
   } else if constexpr (EPI == TC_EPI_TANGENT) {
