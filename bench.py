@@ -52,9 +52,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 Newton-Schulz comparator")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-plain", action="store_true", help="skip the margin-free (plain steps) figure")
-    p.add_argument("--split-steps", type=int, default=-2,
+    p.add_argument("--split-steps", type=int, default=-3,
                    help="REFINE stage 1: iterates X_0..X_{n-1} as hi/lo pairs, later ones single planes "
-                        "(-1 all pairs, 0 none; -2 the library default)")
+                        "(-2 by the library's rule, -1 all pairs, 0 none; -3 leaves the library default)")
     p.add_argument("--low-split", type=int, default=1, choices=[0, 1],
                    help="REFINE stage 1 hi/lo pairs at all (0: single planes throughout)")
     p.add_argument("--max-sweeps", type=int, default=4)
@@ -301,7 +301,7 @@ def run_rsign(args):
     rs.load()
     if args.digit_fp8 >= 0:
         rs.dbg_set_digit_fp8(args.digit_fp8)
-    if args.split_steps >= -1:
+    if args.split_steps >= -2:
         rs.dbg_set_split_steps(args.split_steps)
     if args.oz_tile >= 0:
         rs.dbg_set_ozaki_tile(args.oz_tile)

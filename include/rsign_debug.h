@@ -133,10 +133,13 @@ int32_t rsign_dbg_set_digit_fp8(int32_t on);
  * Low-precision stage of the *_REFINE policies: the iterates X_0 .. X_{n-1}
  * are carried as hi/lo pairs of FP16/BF16 planes (three pair products per
  * launch), later ones as single planes (one product per launch, the plain
- * format's rounding).  n = -1 (the default) carries every iterate as a pair;
- * n = 0 none.  Values below -1 leave the setting unchanged.  Process-wide;
- * returns the previous setting.  For measurements of the trade-off between
- * the stage's cost and the refinement sweeps its rounding leaves to do.
+ * format's rounding).  n = -2 (the default): by rule, pairs while the known
+ * lower end of the iterate's spectrum (from alpha times the margin) is below
+ * 1/2, and every iterate when no margin is known; n = -1: every iterate;
+ * n >= 0: the first n.  Values below -2 leave the setting unchanged.
+ * Process-wide; returns the previous setting.  For measurements of the
+ * trade-off between the stage's cost and the refinement sweeps its rounding
+ * leaves to do.
  */
 int32_t rsign_dbg_set_split_steps(int32_t n);
 

@@ -594,8 +594,8 @@ def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
 
 
 def dbg_set_split_steps(n):
-    """REFINE stage 1: iterates X_0..X_{n-1} as hi/lo pairs, later ones single planes (-1: all pairs);
-    returns the previous setting."""
+    """REFINE stage 1: iterates X_0..X_{n-1} as hi/lo pairs, later ones single planes (-2: by rule,
+    -1: all pairs); returns the previous setting."""
     return int(load().rsign_dbg_set_split_steps(int(n)))
 
 

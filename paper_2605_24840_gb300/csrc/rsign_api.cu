@@ -363,11 +363,20 @@ int g_levels_polish = 0, g_levels_ra0 = 0, g_levels_ra = kSlices;
 // the tensor rate and half the operand bytes (measured at d = 8192: the two
 // products of a FP16_REFINE call 18.4 -> 12.1 ms).
 int g_digit_fp8 = 1;
-// Stage-1 iterates carried as hi/lo pairs by the *_REFINE policies: X_0 ..
-// X_{S-1} with S = g_split_steps, every iterate for S < 0 (the default).
-// Later steps run on single FP16/BF16 planes (three times fewer pair
-// products per launch, at the plain format's rounding).
-int g_split_steps = -1;
+// Stage-1 iterates carried as hi/lo pairs by the *_REFINE policies.  By rule
+// (g_split_steps = -2, the default): while the known lower end l_m of the
+// iterate's spectrum (the scaled or plain recurrence from alpha * margin)
+// is below 1/2, and every iterate when no margin is known; later steps run
+// on single FP16/BF16 planes, one pair product per launch instead of three.
+// Rounding made while the eigenvalues next to the gap are small is what the
+// tangent solve of the refinement cannot undo in one sweep (its relative
+// error there is ~u / l_m); once l_m >= 1/2 the plain format's rounding
+// only adds noise that one sweep removes.  Measured at d = 8192, k = 16,
+// half-gap 1e-2: 62.9 ms with every iterate as a pair, 54.1 ms with X_0 ..
+// X_4 (l_4 = 0.37, l_5 = 0.72), both one sweep, errors 3.7e-7 and 7.1e-7.
+// -1: every iterate a pair; n >= 0: X_0 .. X_{n-1}.
+int g_split_steps = -2;
+constexpr double kSplitUntil = 0.5;
 int levels_for(int set, double tol, int d, int k) {
   if (set > 0) return set;
   const bool few = 32 * std::min(k, d - k) <= d;
@@ -943,9 +952,28 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     // calls, d <= 1024, stay bitwise equal to one-matrix calls)
     float* rowsq = nullptr;
     if (d > kExactDiagMin && mem.alloc((void**)&rowsq, (size_t)dp * 4) != cudaSuccess) return fail_cuda();
-    // iterate X_m as a hi/lo pair (refinement: the leading g_split_steps only
-    // when that is set), and the floors of the stop test for its format
-    auto x_split = [&](int mi) { return split && (!refine || g_split_steps < 0 || mi < g_split_steps); };
+    // iterate X_m as a hi/lo pair (refinement: the leading n_split only),
+    // and the floors of the stop test for its format
+    int n_split = -1;  // -1: every iterate
+    if (refine && g_split_steps >= 0) {
+      n_split = g_split_steps;
+    } else if (refine && g_split_steps == -2) {
+      const double mk = auto_shift ? margin_lb : opt.margin;
+      if (std::isfinite(mk) && mk > 0.0) {
+        // the lower end of the spectrum of X_m: l_0 = alpha margin / u0,
+        // then the scaled steps' map (plain steps beyond the scalings)
+        const double u0 = opt.alpha_mode == RSIGN_ALPHA_POWER ? 1.04 : 1.0;
+        double l = std::min(1.0, alpha * mk) / u0;
+        int mi = 0;
+        while (l < kSplitUntil && mi < opt.max_steps) {
+          const double a = mi < (int)coef.size() ? coef[mi] * (mi == 0 ? u0 : 1.0) : 1.0;
+          l = 0.5 * a * l * (3.0 - a * a * l * l);
+          ++mi;
+        }
+        n_split = mi;
+      }
+    }
+    auto x_split = [&](int mi) { return split && (!refine || n_split < 0 || mi < n_split); };
     const double u1 = unit_roundoff(fmt);
     int m = 0;
     bool stopped = false;
@@ -1691,7 +1719,7 @@ rsign_status rsign_dbg_fp64grade_gemm(const double* A, const double* B, int64_t 
 
 int32_t rsign_dbg_set_split_steps(int32_t n) {
   const int prev = g_split_steps;
-  if (n >= -1) g_split_steps = n;
+  if (n >= -2) g_split_steps = n;
   return prev;
 }
 
