@@ -58,6 +58,10 @@ def parse():
     p.add_argument("--low-split", type=int, default=1, choices=[0, 1],
                    help="REFINE stage 1 hi/lo pairs at all (0: single planes throughout)")
     p.add_argument("--max-sweeps", type=int, default=4)
+    p.add_argument("--host-mapped", type=int, default=-1, choices=[-1, 0, 1],
+                   help="e2e: page-locked host buffers read/written in place (1) or staged (0); -1 the default")
+    p.add_argument("--tangent-cut", type=int, default=-1, choices=[-1, 0, 1],
+                   help="leave out tangent steps at converged iterates (1), run all (0), -1 the library default")
     p.add_argument("--oz-tile", type=int, default=-1, choices=[-1, 0, 128, 256],
                    help="tile width of the FP64-grade products (128: level sums in TMEM; -1 the library default)")
     p.add_argument("--digit-fp8", type=int, default=-1, choices=[-1, 0, 1],
@@ -305,6 +309,10 @@ def run_rsign(args):
         rs.dbg_set_split_steps(args.split_steps)
     if args.oz_tile >= 0:
         rs.dbg_set_ozaki_tile(args.oz_tile)
+    if args.tangent_cut >= 0:
+        rs.dbg_set_tangent_cut(args.tangent_cut)
+    if args.host_mapped >= 0:
+        rs.dbg_set_host_mapped(args.host_mapped)
     policy = rs.Policy[args.policy]
     seed = workloads.controlled_seed(args.d, 1, 1) + rank
     H, lam, Q = workloads.controlled_spectrum_torch(args.d, args.k, args.delta, seed, device=dev)

@@ -144,6 +144,39 @@ int32_t rsign_dbg_set_digit_fp8(int32_t on);
 int32_t rsign_dbg_set_split_steps(int32_t n);
 
 /*
+ * Tangent solve of the refinement: 1 (the default) leaves out the tangent
+ * steps at stored iterates whose known lower end of the spectrum (from alpha
+ * times the margin) is within 1e-3 of 1, where the step's derivative is the
+ * identity on the error's anticommuting part; 0 runs a tangent step for
+ * every stored iterate.  Other values leave the setting unchanged.
+ * Process-wide; returns the previous setting.
+ */
+int32_t rsign_dbg_set_tangent_cut(int32_t on);
+
+/*
+ * Host buffers of rsign_reflector[_ex]: 0 (the default) copies H in and R
+ * out through staging device buffers on the copy engines; 1 lets the ingest
+ * and output kernels read and write page-locked host buffers (cudaHostAlloc
+ * or cudaHostRegister memory) in place over the CPU-GPU link (other host
+ * memory is still staged).  Other values leave the setting unchanged.
+ * Process-wide; returns the previous setting.
+ */
+int32_t rsign_dbg_set_host_mapped(int32_t on);
+
+/*
+ * Host routine of the REFINE stage plan (runs on the CPU, no GPU needed):
+ * the lower end l_m of the normalised spectrum of X_m, m = 0 .. max_steps
+ * (l_0 = min(1, alpha_margin) / u0, then the scaled steps' map when scaled,
+ * the map of Eq. NS beyond them or when not scaled) into lower_end
+ * (nullable, max_steps + 1 doubles); *n_split = the number of leading
+ * iterates carried as hi/lo pairs (first m with l_m >= 1/2); *m_tangent = the
+ * number of tangent steps run for a stage of steps_low steps (first m with
+ * l_m >= 1 - 1e-3, at least 1, else steps_low).
+ */
+rsign_status rsign_dbg_stage_plan(double alpha_margin, double u0, int32_t scaled, int32_t max_steps,
+                                  int32_t steps_low, double* lower_end, int32_t* n_split, int32_t* m_tangent);
+
+/*
  * Failure path of the bounded pipeline waits (the mbarrier waits of every
  * tcgen05 kernel, which give up after a wall-clock limit instead of hanging):
  * one kernel initialises an mbarrier for one arrival and waits for its first

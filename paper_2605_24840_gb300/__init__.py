@@ -196,6 +196,12 @@ def load():
     lib.rsign_dbg_set_refine_levels.restype = i32
     lib.rsign_dbg_set_ozaki_tile.argtypes = [i32]
     lib.rsign_dbg_set_ozaki_tile.restype = i32
+    lib.rsign_dbg_stage_plan.argtypes = [dbl, dbl, i32, i32, i32, dp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.rsign_dbg_stage_plan.restype = ctypes.c_int
+    lib.rsign_dbg_set_host_mapped.argtypes = [i32]
+    lib.rsign_dbg_set_host_mapped.restype = i32
+    lib.rsign_dbg_set_tangent_cut.argtypes = [i32]
+    lib.rsign_dbg_set_tangent_cut.restype = i32
     lib.rsign_dbg_set_split_steps.argtypes = [i32]
     lib.rsign_dbg_set_split_steps.restype = i32
     lib.rsign_dbg_set_digit_fp8.argtypes = [i32]
@@ -591,6 +597,31 @@ def dbg_fp64grade_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def dbg_stage_plan(alpha_margin, u0=1.0, scaled=True, max_steps=100, steps_low=None):
+    """(lower ends l_0..l_max_steps, n_split, m_tangent) of the REFINE stage plan (host only)."""
+    lib = load()
+    steps_low = max_steps if steps_low is None else steps_low
+    le = np.empty(max_steps + 1)
+    ns, mt = ctypes.c_int32(0), ctypes.c_int32(0)
+    st = Status(lib.rsign_dbg_stage_plan(float(alpha_margin), float(u0), int(bool(scaled)), int(max_steps),
+                                         int(steps_low), le.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.byref(ns), ctypes.byref(mt)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return le, int(ns.value), int(mt.value)
+
+
+def dbg_set_host_mapped(on):
+    """Host buffers read/written in place by the kernels (1) or staged through copies (0); returns the
+    previous setting."""
+    return int(load().rsign_dbg_set_host_mapped(int(on)))
+
+
+def dbg_set_tangent_cut(on):
+    """Leave out tangent steps at converged stored iterates (1) or run them all (0); returns the previous setting."""
+    return int(load().rsign_dbg_set_tangent_cut(int(on)))
 
 
 def dbg_set_split_steps(n):

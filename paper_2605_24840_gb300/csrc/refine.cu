@@ -336,6 +336,26 @@ __global__ void polish_update_kernel(double* __restrict__ R, const float* __rest
     R[e] += ic_f2d(f * P[e]);
 }
 
+// Weight of the quintic polish step, as the FP16 operand sigma W with
+// W = E + 3/4 E^2: dst = FP16(sigma E + 3/4 Q / sigma), Q = (sigma E)^2
+// (FP32, from the tensor cores); four elements per thread and iteration
+__global__ void polish_weight_kernel(const float* __restrict__ E, const float* __restrict__ Q, size_t n,
+                                     const float* sigma, __half* __restrict__ dst) {
+  const float sg = sigma[0], q = 0.75f / sigma[0];
+  const size_t n4 = n >> 2;
+  const float4* e4 = reinterpret_cast<const float4*>(E);
+  const float4* q4 = reinterpret_cast<const float4*>(Q);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = e4[i], b = q4[i];
+    const __half2 lo = __floats2half2_rn(fmaf(q, b.x, sg * a.x), fmaf(q, b.y, sg * a.y));
+    const __half2 hi = __floats2half2_rn(fmaf(q, b.z, sg * a.z), fmaf(q, b.w, sg * a.w));
+    uint2 w;
+    w.x = *reinterpret_cast<const uint32_t*>(&lo);
+    w.y = *reinterpret_cast<const uint32_t*>(&hi);
+    reinterpret_cast<uint2*>(dst)[i] = w;
+  }
+}
+
 // dst = FP16(src) by way of the nearest float (integer rounding, then the
 // float -> half conversion): two elements per thread and iteration
 __global__ void to_f16_kernel(const double* __restrict__ src, size_t n, __half* __restrict__ dst) {
@@ -1107,6 +1127,12 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
 cudaError_t to_f16(const double* src, size_t n, void* dst, cudaStream_t st) {
   if (n & 1) return cudaErrorInvalidValue;
   to_f16_kernel<<<grid_for(n / 2), 256, 0, st>>>(src, n, (__half*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t polish_weight(const float* E, const float* Q, size_t n, const float* sigma, void* dst, cudaStream_t st) {
+  if (n & 3) return cudaErrorInvalidValue;
+  polish_weight_kernel<<<grid_for(n / 4), 256, 0, st>>>(E, Q, n, sigma, (__half*)dst);
   return cudaGetLastError();
 }
 

@@ -169,6 +169,35 @@ def test_scaled_step_coefficients_match_the_oracle(rs, oracle_mod, l0, u0):
         assert got == []  # an involution needs no scaled step
 
 
+@pytest.mark.parametrize("l0,u0", [(1e-2, 1.04), (2e-3, 1.0), (0.2, 1.04), (0.7, 1.0)])
+def test_refine_stage_plan_follows_the_oracle_iterates(rs, oracle_mod, l0, u0):
+    # the lower end of the spectrum that the REFINE stage plan tracks: the
+    # oracle's scaled iterates of a diagonal X_0 (eigenvalues from l0 to u0)
+    # have smallest |entry| equal to the library's l_m for m >= 1 (l_0 is
+    # normalised by u0); hi/lo pairs until l_m >= 1/2, tangent steps until
+    # l_m >= 1 - 1e-3 (Sec. 3.5 reading of the scaled steps)
+    steps = 40
+    le, n_split, m_tan = rs.dbg_stage_plan(l0, u0, scaled=True, max_steps=steps, steps_low=steps)
+    coef = oracle_mod.scaled_ns_coeffs(min(1.0, l0), u0)
+    X0 = np.diag(np.array([l0, -l0, 0.5 * (l0 + u0), -u0, u0]))
+    its = oracle_mod.scaled_ns_iterates(X0, coef, steps)
+    assert le[0] * u0 == pytest.approx(min(1.0, l0), rel=1e-15)
+    for m in range(1, 12):
+        assert le[m] == pytest.approx(np.abs(np.diag(its[m])).min(), rel=1e-11, abs=1e-15)
+    assert n_split == next(m for m in range(steps + 1) if le[m] >= 0.5)
+    assert all(le[m] < 0.5 for m in range(n_split))
+    first_conv = next(m for m in range(steps) if le[m] >= 1.0 - 1e-3)
+    assert m_tan == max(1, first_conv)
+    # a stage that stopped before the cut runs every tangent step
+    _, _, m_short = rs.dbg_stage_plan(l0, u0, scaled=True, max_steps=steps, steps_low=min(first_conv, 3))
+    assert m_short == min(first_conv, 3)
+    # plain steps (no scaling): l_m = p_m(l0 / u0) (Eq. pm), the conservative end
+    le_p, n_p, _ = rs.dbg_stage_plan(l0, u0, scaled=False, max_steps=steps, steps_low=steps)
+    for m in range(0, 20):
+        assert le_p[m] == pytest.approx(float(oracle_mod.p_m(min(1.0, l0) / u0, m)), rel=1e-11, abs=1e-15)
+    assert n_p >= n_split
+
+
 @pytest.mark.parametrize("m", [0, 1, 5, 12, 30])
 def test_margin_bound_from_steps_is_the_root_of_p_m(rs, oracle_mod, m):
     # gamma with p_m(gamma) = 0.9 (Eq. pm), from the oracle's polynomial

@@ -114,6 +114,28 @@ def test_host_pointers_roundtrip():
     assert spec_norm_sym(R - oracle.reflector_from_basis(spec.Q, 3)) < 1e-12
 
 
+@pytest.mark.parametrize("mapped", [0, 1])
+def test_pinned_host_buffers_give_the_device_bits(mapped):
+    # page-locked host H and R (staged through copies, or read and written in
+    # place by the kernels): the same bits as device buffers
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 700, 9
+    spec = workloads.controlled_spectrum(d, k, 5e-2, seed=33)
+    Hh = torch.from_numpy(spec.H).pin_memory()
+    Rh = torch.empty((d, d), dtype=torch.float64).pin_memory()
+    Rd, info_d, st_d = rs.reflector(Hh.cuda(), k, 0.0, tol=1e-6, policy=rs.Policy.FP16_REFINE)
+    prev = rs.dbg_set_host_mapped(mapped)
+    try:
+        _, info_h, st_h = rs.reflector(Hh.numpy(), k, 0.0, tol=1e-6, policy=rs.Policy.FP16_REFINE, out=Rh.numpy())
+    finally:
+        rs.dbg_set_host_mapped(prev)
+    torch.cuda.synchronize()
+    assert st_d == rs.Status.OK and st_h == rs.Status.OK
+    assert np.array_equal(Rd.cpu().numpy(), Rh.numpy())
+    assert spec_norm_sym(Rh.numpy() - oracle.reflector_from_basis(spec.Q, k)) <= 1e-6
+
+
 def test_shift_outside_gap_fails_certificate():
     torch = cuda_or_skip()
     rs = lib_or_fail()
