@@ -144,10 +144,10 @@ int32_t rsign_dbg_set_digit_fp8(int32_t on);
 int32_t rsign_dbg_set_split_steps(int32_t n);
 
 /*
- * Tangent solve of the refinement: 1 (the default) leaves out the tangent
- * steps at stored iterates whose known lower end of the spectrum (from alpha
- * times the margin) is within 1e-3 of 1, where the step's derivative is the
- * identity on the error's anticommuting part; 0 runs a tangent step for
+ * Tangent solve of the refinement: 1 leaves out the tangent steps at stored
+ * iterates whose known lower end of the spectrum (from alpha times the
+ * margin) is within 1e-3 of 1, where the step's derivative is the identity
+ * on the error's anticommuting part; 0 (the default) runs a tangent step for
  * every stored iterate.  Other values leave the setting unchanged.
  * Process-wide; returns the previous setting.
  */

@@ -91,6 +91,9 @@ struct TcGemmArgs {
                            // (plane stride dp*dp); out = hi + lo carries ~2x the bits
   int single_out;          // with split: write the result's hi plane only (the step
                            // after this one runs on single planes)
+  int pair_out;            // TC_EPI_NS_UPDATE without split: write the result as a hi/lo
+                           // pair all the same (the next step reads hi only; the pair
+                           // keeps the FP32 value if this is the last iterate)
   // TC_EPI_OZAKI with diagonal-free digit planes: the first group adds the
   // exact FP64 diagonal terms d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
   const double* a_full;    // FP64 A (dp x dp), or nullptr

@@ -91,7 +91,12 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrow
     const long long t = __shfl_xor_sync(0xffffffffu, mx, o);
     mx = t > mx ? t : mx;
   }
-  int ex = 0;
+  // a row without off-diagonal entries (a padding row, or a diagonal row)
+  // has zero digits; its scale is the smallest normal power of two, so that
+  // the largest row scale, which the refinement's level rule reads, is that
+  // of the rows that have digits (a scale of 1 here made that rule depend on
+  // the magnitude of H at padded orders)
+  int ex = -1022;
   if (mx != 0) {
     unsigned long long mant;
     int e2;

@@ -386,9 +386,11 @@ int g_digit_fp8 = 1;
 int g_split_steps = -2;
 constexpr double kSplitUntil = 0.5;
 // Tangent steps of the refinement at iterates whose known lower end is within
-// kTangentCut of 1 are left out (g_tangent_cut = 1, the default; 0 runs all).
+// kTangentCut of 1 are left out with g_tangent_cut = 1; 0, the default, runs
+// them all (measured at d = 8192: leaving out the last step made the error
+// estimate after the first sweep miss the tolerance, 56 -> 95 ms per call).
 constexpr double kTangentCut = 1e-3;
-int g_tangent_cut = 1;
+int g_tangent_cut = 0;
 int levels_for(int set, double tol, int d, int k) {
   if (set > 0) return set;
   const bool few = 32 * std::min(k, d - k) <= d;
@@ -1080,7 +1082,13 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         }
         TcGemmArgs up = sy;
         up.epi = TC_EPI_NS_UPDATE; up.out = xn; up.xin = xm; up.partials = tr_part;
-        up.single_out = (sp && !x_split(mm + 1)) ? 1 : 0;
+        // single-plane steps of a split policy still store the lo plane of
+        // their result: the next step reads the hi plane only, but the
+        // iterate the stage ends on keeps its FP32 value (an FP16 rounding of
+        // the last iterate would leave noise ~u16 inside the eigenspaces,
+        // which the polish's FP16 products can only reduce to ~u16^2)
+        up.single_out = 0;
+        up.pair_out = (split && !sp) ? 1 : 0;
         if (!c.ok(tc_gemm(up, xm, planes, bm, planes, fmt, c.num_sms, st))) return fail_cuda();
       }
       if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1091,7 +1099,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       m = m_end;
     }
     steps_low = stopped ? ctl_h.steps_low : opt.max_steps;
-    if (x_split(steps_low)) {
+    if (split) {  // every iterate of a split policy keeps a lo plane (X_0 and the pairs, pair_out after)
       if (!c.ok(split_to_f64(slot_x(steps_low), fmt, dd, xb64[0], st))) return fail_cuda();
     } else {
       if (!c.ok(to_f64(slot_x(steps_low), fmt, dd, xb64[0], st))) return fail_cuda();

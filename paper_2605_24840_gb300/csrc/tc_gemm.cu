@@ -332,13 +332,14 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
           if (j0 + jj == i) {
             const T h = from_f32<T>(v[jj]);
             acc1 += (double)to_f32<T>(h);
-            if (a.split && !a.single_out) acc1 += (double)to_f32<T>(from_f32<T>(v[jj] - to_f32<T>(h)));
+            if ((a.split && !a.single_out) || a.pair_out)
+              acc1 += (double)to_f32<T>(from_f32<T>(v[jj] - to_f32<T>(h)));
           }
       }
     }
     // the result is written as a hi/lo pair when the operands were (unless
-    // single_out asks for the hi plane alone: the next step runs unsplit)
-    const bool lo_out = a.split && !a.single_out;
+    // single_out asks for the hi plane alone) or when pair_out asks for it
+    const bool lo_out = (a.split && !a.single_out) || a.pair_out;
     float lo[32];
     if (lo_out) {
 #pragma unroll
