@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--low-split", type=int, default=1, choices=[0, 1],
                    help="REFINE stage 1 hi/lo pairs at all (0: single planes throughout)")
     p.add_argument("--max-sweeps", type=int, default=4)
+    p.add_argument("--split-until", type=float, default=-1.0,
+                   help="threshold of the stage-1 split rule (pairs while l_m < this); -1 the library default")
     p.add_argument("--host-mapped", type=int, default=-1, choices=[-1, 0, 1],
                    help="e2e: page-locked host buffers read/written in place (1) or staged (0); -1 the default")
     p.add_argument("--tangent-cut", type=int, default=-1, choices=[-1, 0, 1],
@@ -82,6 +84,8 @@ def parse():
     p.add_argument("--sweep-fp64-max", type=int, default=4096,
                    help="sweep: largest d run with the FP64 policy (the headline point always runs)")
     p.add_argument("--sweep-out", default=None, help="sweep: also append the JSON lines to this file")
+    p.add_argument("--sweep-error-steps", type=int, default=1, choices=[0, 1],
+                   help="sweep: also record error vs steps of the FP64 policy at d=4096")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-policy", default="FP16_POLISH")
     p.add_argument("--no-loop", action="store_true", help="batched: skip the per-matrix call loop")
@@ -303,16 +307,7 @@ def run_rsign(args):
     if ws > 1:
         tdist.init_process_group("nccl", device_id=dev)
     rs.load()
-    if args.digit_fp8 >= 0:
-        rs.dbg_set_digit_fp8(args.digit_fp8)
-    if args.split_steps >= -2:
-        rs.dbg_set_split_steps(args.split_steps)
-    if args.oz_tile >= 0:
-        rs.dbg_set_ozaki_tile(args.oz_tile)
-    if args.tangent_cut >= 0:
-        rs.dbg_set_tangent_cut(args.tangent_cut)
-    if args.host_mapped >= 0:
-        rs.dbg_set_host_mapped(args.host_mapped)
+    apply_switches(args, rs)
     policy = rs.Policy[args.policy]
     seed = workloads.controlled_seed(args.d, 1, 1) + rank
     H, lam, Q = workloads.controlled_spectrum_torch(args.d, args.k, args.delta, seed, device=dev)
@@ -484,11 +479,41 @@ def batched_figure(args, rs, torch, dev, stream, seed):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     loop_ms = e0.elapsed_time(e1)
+    # the same batch refined to 1e-6 (BF16_REFINE): one-matrix calls spread
+    # over worker streams inside the batched call
+    rt, rinfos, rst = [], None, None
+    for i in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, rinfos, rst = rs.reflector_batched(Hs, ks, ss, tol=1e-6, policy=rs.Policy.BF16_REFINE, outs=Rs)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if i >= 1:
+            rt.append(e0.elapsed_time(e1))
+    refine = {"ms": statistics.median(rt), "policy": "BF16_REFINE", "tol": 1e-6, "status": rst.name,
+              "certified": sum(int(i.cert_ok) for i in rinfos)}
     return {"ms": statistics.median(times), "unit": "ms per batch", "count": len(items),
             "policy": args.batch_policy, "certified": sum(int(i.cert_ok) for i in infos), "status": st.name,
+            "refine": refine,
             "per_matrix_loop_ms": loop_ms, "tile": infos[0].batch_tile,
             "workload": "batched controlled spectra: d uniform in {32,...,512}, k in 1..8, delta log-uniform in "
                         "[1e-3, 1e-1], own midpoint shifts, Gershgorin alpha"}
+
+
+def apply_switches(args, rs):
+    """The library's measurement switches named on the command line."""
+    if args.digit_fp8 >= 0:
+        rs.dbg_set_digit_fp8(args.digit_fp8)
+    if args.split_steps >= -2:
+        rs.dbg_set_split_steps(args.split_steps)
+    if args.split_until > 0:
+        rs.dbg_set_split_until(args.split_until)
+    if args.oz_tile >= 0:
+        rs.dbg_set_ozaki_tile(args.oz_tile)
+    if args.tangent_cut >= 0:
+        rs.dbg_set_tangent_cut(args.tangent_cut)
+    if args.host_mapped >= 0:
+        rs.dbg_set_host_mapped(args.host_mapped)
 
 
 def run_batched(args):
@@ -632,6 +657,7 @@ def run_sweep(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     rs.load()
+    apply_switches(args, rs)
     stream = torch.cuda.current_stream(dev)
     pk, pk_kind = peaks()
     peak = float(pk.get("bf16_tflops", 1900.0))
@@ -667,6 +693,10 @@ def run_sweep(args):
                             out.flush()
                 del H, Q, R
                 torch.cuda.empty_cache()
+    if not args.sweep_error_steps:
+        if out:
+            out.close()
+        return 0
     # error vs steps (Prop. 3.6): FP64 policy stopped after m steps, plain and
     # scaled engines, d = 4096, k = 16, delta = 1e-2, midpoint shift; the
     # scalar bound eps_m(gamma) of the plain recurrence beside it

@@ -272,8 +272,12 @@ rsign_status rsign_apply(const double* R, int64_t d, const double* V, int64_t nv
  *   replayed as one CUDA graph.  alpha_i is the Gershgorin bound of each
  *   matrix (Sec. 4.3).  Each matrix gets the same result as its own
  *   rsign_reflector call with the same policy and RSIGN_ALPHA_INF.
- *   Other matrices (s[i] = NaN for the automatic shift, REFINE policies,
- *   d[i] > 1024) are computed one by one with rsign_reflector_ex.
+ *   Other matrices (s[i] = NaN for the automatic shift, REFINE policies and
+ *   FP32, d[i] > 1024) are computed with rsign_reflector_ex calls that up
+ *   to 16 library-owned host threads run concurrently, each on a stream of
+ *   its own that first waits for `stream`; each result equals that
+ *   matrix's lone rsign_reflector_ex call bit for bit.  The call returns
+ *   once every matrix is done.
  */
 rsign_status rsign_reflector_batched(int32_t n, const double* const* H, const int64_t* d,
                                      const int32_t* k, const double* s, double tol,

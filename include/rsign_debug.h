@@ -164,6 +164,14 @@ int32_t rsign_dbg_set_tangent_cut(int32_t on);
 int32_t rsign_dbg_set_host_mapped(int32_t on);
 
 /*
+ * Threshold of the stage-1 split rule (rsign_dbg_set_split_steps(-2)): the
+ * iterates whose known lower end of the spectrum is below l are carried as
+ * hi/lo pairs.  l in (0, 1]; other values leave it unchanged.  Process-wide;
+ * returns the previous threshold.
+ */
+double rsign_dbg_set_split_until(double l);
+
+/*
  * Host routine of the REFINE stage plan (runs on the CPU, no GPU needed):
  * the lower end l_m of the normalised spectrum of X_m, m = 0 .. max_steps
  * (l_0 = min(1, alpha_margin) / u0, then the scaled steps' map when scaled,

@@ -198,6 +198,8 @@ def load():
     lib.rsign_dbg_set_ozaki_tile.restype = i32
     lib.rsign_dbg_stage_plan.argtypes = [dbl, dbl, i32, i32, i32, dp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.rsign_dbg_stage_plan.restype = ctypes.c_int
+    lib.rsign_dbg_set_split_until.argtypes = [dbl]
+    lib.rsign_dbg_set_split_until.restype = dbl
     lib.rsign_dbg_set_host_mapped.argtypes = [i32]
     lib.rsign_dbg_set_host_mapped.restype = i32
     lib.rsign_dbg_set_tangent_cut.argtypes = [i32]
@@ -611,6 +613,12 @@ def dbg_stage_plan(alpha_margin, u0=1.0, scaled=True, max_steps=100, steps_low=N
     if st != Status.OK:
         raise RsignError(st)
     return le, int(ns.value), int(mt.value)
+
+
+def dbg_set_split_until(l):
+    """Threshold of the stage-1 split rule (pairs while the known lower end is below l); returns the
+    previous threshold."""
+    return float(load().rsign_dbg_set_split_until(float(l)))
 
 
 def dbg_set_host_mapped(on):

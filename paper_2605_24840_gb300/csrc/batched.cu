@@ -31,16 +31,19 @@
 #include "rsign.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 namespace rsign {
 namespace {
 
 constexpr int kBatchMaxD = 1024;  // larger matrices take the one-matrix path
+constexpr int kRestWorkers = 16;  // host threads running one-matrix calls concurrently
 constexpr int kBatchChunk = 8;    // steps per chunk (even: the ping-pong parity repeats)
 constexpr double kEps64 = 2.220446049250313e-16;
 
@@ -839,10 +842,59 @@ rsign_status batched_impl(int32_t n, const double* const* H, const int64_t* d, c
     if (cudaGetLastError() != cudaSuccess) return RSIGN_ERR_CUDA;
   }
 
-  // ---- the rest, one by one
-  for (int i : rest) {
-    stat[i] = rsign_reflector_ex(H[i], d[i], k[i], s[i], tol, policy, &opt, R[i], infos ? &infos[i] : nullptr,
-                                 (void*)st);
+  // ---- the rest: one-matrix calls (the refinement policies, automatic
+  // shifts, orders above kBatchMaxD), run concurrently by worker threads,
+  // each on a stream of its own that first waits for the caller's stream.
+  // Each call is the same computation as a lone rsign_reflector_ex call on
+  // that matrix (same kernels, same order: the same bits); small matrices
+  // leave most SMs idle, so several calls in flight fill the GPU.
+  if (!rest.empty()) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RSIGN_ERR_CUDA;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nw = (int)std::min<size_t>({rest.size(), (size_t)kRestWorkers, (size_t)hw});
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, st) != cudaSuccess) {
+      if (ready) cudaEventDestroy(ready);
+      cudaGetLastError();
+      return RSIGN_ERR_CUDA;
+    }
+    std::atomic<size_t> next(0);
+    auto worker = [&]() {
+      cudaStream_t ws = nullptr;
+      if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (ws) cudaStreamDestroy(ws);
+        return;
+      }
+      for (size_t q; (q = next++) < rest.size();) {
+        const int i = rest[q];
+        stat[i] = rsign_reflector_ex(H[i], d[i], k[i], s[i], tol, policy, &opt, R[i],
+                                     infos ? &infos[i] : nullptr, (void*)ws);
+      }
+      cudaStreamSynchronize(ws);
+      cudaStreamDestroy(ws);
+    };
+    if (nw <= 1) {
+      for (int i : rest)
+        stat[i] = rsign_reflector_ex(H[i], d[i], k[i], s[i], tol, policy, &opt, R[i],
+                                     infos ? &infos[i] : nullptr, (void*)st);
+    } else {
+      std::vector<std::thread> pool;
+      pool.reserve(nw);
+      for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+      for (auto& t : pool) t.join();
+      // a worker that could not set up its stream left matrices undone: the
+      // caller's stream finishes them
+      for (size_t q; (q = next++) < rest.size();) {
+        const int i = rest[q];
+        stat[i] = rsign_reflector_ex(H[i], d[i], k[i], s[i], tol, policy, &opt, R[i],
+                                     infos ? &infos[i] : nullptr, (void*)st);
+      }
+    }
+    cudaEventDestroy(ready);
   }
   for (int i = 0; i < n; ++i)
     if (stat[i] != RSIGN_OK) return stat[i];

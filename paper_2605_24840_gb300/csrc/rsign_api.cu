@@ -384,7 +384,7 @@ int g_digit_fp8 = 1;
 // X_4 (l_4 = 0.37, l_5 = 0.72), both one sweep, errors 3.7e-7 and 7.1e-7.
 // -1: every iterate a pair; n >= 0: X_0 .. X_{n-1}.
 int g_split_steps = -2;
-constexpr double kSplitUntil = 0.5;
+double g_split_until = 0.5;
 // Tangent steps of the refinement at iterates whose known lower end is within
 // kTangentCut of 1 are left out with g_tangent_cut = 1; 0, the default, runs
 // them all (measured at d = 8192: leaving out the last step made the error
@@ -455,7 +455,7 @@ std::vector<double> lower_end_sequence(double alpha_margin, double u0, const std
 // at least 1), given steps_low stage-1 steps.
 void refine_stage_plan(const std::vector<double>& lower_end, int steps_low, int* n_split, int* m_tangent) {
   int ns = 0;
-  while (ns < (int)lower_end.size() && lower_end[ns] < kSplitUntil) ++ns;
+  while (ns < (int)lower_end.size() && lower_end[ns] < g_split_until) ++ns;
   *n_split = ns;
   int mt = steps_low;
   for (int mi = 0; mi < steps_low && mi < (int)lower_end.size(); ++mi)
@@ -1806,6 +1806,12 @@ rsign_status rsign_dbg_stage_plan(double alpha_margin, double u0, int32_t scaled
   *n_split = ns;
   *m_tangent = mt;
   return RSIGN_OK;
+}
+
+double rsign_dbg_set_split_until(double l) {
+  const double prev = g_split_until;
+  if (l > 0.0 && l <= 1.0) g_split_until = l;
+  return prev;
 }
 
 int32_t rsign_dbg_set_host_mapped(int32_t on) {

@@ -169,6 +169,32 @@ def test_full_batched_workload_certifies_and_samples_match():
         assert err <= 2e-3 / (lam[0] / np.max(np.abs(sp.lam - items[j][1]))) + 1e-6, (j, err)
 
 
+@pytest.mark.parametrize("policy", ["BF16_REFINE", "FP16_REFINE"])
+def test_full_batched_workload_refined_to_1e6(policy):
+    """The 512-matrix workload with a REFINE policy to tol 1e-6: the matrices
+    take one-matrix calls run concurrently on worker streams; every matrix is
+    certified and within 1e-6 of its exact reflector (the oracle's I - 2 Q_k
+    Q_k^T), and a sample equals its lone one-matrix call bit for bit."""
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    items = workloads.batched_workload(512)
+    pol = rs.Policy[policy]
+    Rb, infos, st = _run(rs, torch, items, pol, tol=1e-6)
+    assert st == rs.Status.OK, st
+    assert sum(i.cert_ok for i in infos) == 512
+    worst = 0.0
+    for (sp, s), R in zip(items, Rb):
+        D = R - _exact(sp)
+        worst = max(worst, float(np.abs(np.linalg.eigvalsh(0.5 * (D + D.T))).max()))
+    assert worst <= 1e-6, worst
+    for j in range(0, 512, 64):
+        sp, s = items[j]
+        R1, inf1, st1 = rs.reflector(torch.from_numpy(sp.H).cuda(), sp.k, s, tol=1e-6, policy=pol, check=False)
+        torch.cuda.synchronize()
+        assert st1 == rs.Status.OK
+        assert np.array_equal(R1.cpu().numpy(), Rb[j]), j
+
+
 def test_sharded_batch_on_one_rank_equals_the_batched_call():
     # the multi-GPU batched path at world size 1: its share is the whole batch
     # and its outputs are those of one batched call, bit for bit
