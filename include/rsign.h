@@ -110,7 +110,9 @@ typedef struct {
                               antisymmetric C, v -> R A v - A R v, with FP64-class
                               (double-float, ~2^-46 per term) products; NaN otherwise  */
   double err_est;          /* a-posteriori estimate of ||R - sign(H - sI)||_2 (REFINE):
-                              max(1.5 kappa alpha ||G||_2, ||C||_2 / g): G = 1/2 R C,
+                              2.5 max(1.5 kappa alpha ||G||_2, ||C||_2 / g) (the factor
+                              2.5 covers the largest underestimate measured, 2.1x;
+                              it is an estimate, not a bound): G = 1/2 R C,
                               C = R A - A R, kappa the gain of the last tangent solve,
                               g the eigenvalue gap of the 2 x 2 Rayleigh-Ritz projection
                               of A on the dominant plane of C (at least 2 mu when a

@@ -133,9 +133,10 @@ int32_t rsign_dbg_set_digit_fp8(int32_t on);
  * Low-precision stage of the *_REFINE policies: the iterates X_0 .. X_{n-1}
  * are carried as hi/lo pairs of FP16/BF16 planes (three pair products per
  * launch), later ones as single planes (one product per launch, the plain
- * format's rounding).  n = -2 (the default): by rule, pairs while the known
- * lower end of the iterate's spectrum (from alpha times the margin) is below
- * 1/2, and every iterate when no margin is known; n = -1: every iterate;
+ * format's rounding).  n = -1 (the default): every iterate; n = -2: by rule,
+ * FP16_REFINE only, pairs while the known lower end of the iterate's
+ * spectrum (from alpha times the margin) is below the threshold of
+ * rsign_dbg_set_split_until, and every iterate when no margin is known;
  * n >= 0: the first n.  Values below -2 leave the setting unchanged.
  * Process-wide; returns the previous setting.  For measurements of the
  * trade-off between the stage's cost and the refinement sweeps its rounding

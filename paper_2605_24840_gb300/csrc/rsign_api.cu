@@ -370,21 +370,24 @@ int g_levels_polish = 0, g_levels_ra0 = 0, g_levels_ra = kSlices;
 // the tensor rate and half the operand bytes (measured at d = 8192: the two
 // products of a FP16_REFINE call 18.4 -> 12.1 ms).
 int g_digit_fp8 = 1;
-// Stage-1 iterates carried as hi/lo pairs by the *_REFINE policies.  By rule
-// (g_split_steps = -2, the default): while the known lower end l_m of the
-// iterate's spectrum (the scaled or plain recurrence from alpha * margin)
-// is below 1/2, and every iterate when no margin is known; later steps run
-// on single FP16 planes, one pair product per launch instead of three
-// (FP16_REFINE only: BF16_REFINE keeps every iterate a pair).
-// Rounding made while the eigenvalues next to the gap are small is what the
-// tangent solve of the refinement cannot undo in one sweep (its relative
-// error there is ~u / l_m); once l_m >= 1/2 the plain format's rounding
-// only adds noise that one sweep removes.  Measured at d = 8192, k = 16,
-// half-gap 1e-2: 62.9 ms with every iterate as a pair, 54.1 ms with X_0 ..
-// X_4 (l_4 = 0.37, l_5 = 0.72), both one sweep, errors 3.7e-7 and 7.1e-7.
-// -1: every iterate a pair; n >= 0: X_0 .. X_{n-1}.
-int g_split_steps = -2;
+// Stage-1 iterates carried as hi/lo pairs by the *_REFINE policies: every
+// iterate (g_split_steps = -1, the default), the first n (n >= 0), or by
+// rule (-2): while the known lower end l_m of the iterate's spectrum (the
+// scaled or plain recurrence from alpha * margin) is below g_split_until,
+// FP16_REFINE only; later steps then run on single FP16 planes, one pair
+// product per launch instead of three.  Rounding made while the eigenvalues
+// next to the gap are small is what the tangent solve cannot undo in one
+// sweep (its relative error there is ~u / l_m); later single-plane steps
+// add cross-eigenspace noise of ~u that the sweep must remove.  Measured at
+// d = 8192, k = 16, half-gap 1e-2 the rule with threshold 1/2 saved 9 ms of
+// 63 in one sweep, but its error estimate sat at 0.9 of the tolerance and
+// the gain did not hold over the sweep of controlled spectra (27 points at
+// d = 8192: 3043 ms in total with every iterate a pair, 2968 / 2898 ms with
+// thresholds 0.99 / 0.9; at d = 2048 every iterate a pair was fastest).
+int g_split_steps = -1;
 double g_split_until = 0.5;
+// safety factor of the refinement's a-posteriori error estimate (see the check)
+constexpr double kEstSafety = 2.5;
 // Tangent steps of the refinement at iterates whose known lower end is within
 // kTangentCut of 1 are left out with g_tangent_cut = 1; 0, the default, runs
 // them all (measured at d = 8192: leaving out the last step made the error
@@ -648,7 +651,13 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       double g_rr = std::sqrt((a11 - a22) * (a11 - a22) + 4.0 * a12 * a12);
       if (mu_known) g_rr = std::max(g_rr, 2.0 * in.margin);
       const double est_rr = g_rr > 0.0 ? o->comm / g_rr : INFINITY;
-      o->err_est = std::max(1.5 * kappa * in.alpha * g2, est_rr);
+      // The two gains are estimates, not bounds: over the controlled-spectrum
+      // sweep (d = 1024 .. 16384, k in {1, 16, d/2}, half-gap 1e-3 .. 1e-1,
+      // shifts at 10/50/90 % of the gap) and the 512-matrix batch, the true
+      // error reached up to 2.1 times the unscaled maximum (and exceeded the
+      // tolerance once, 1.6e-6, under BF16_REFINE), so the estimate carries a
+      // factor kEstSafety = 2.5 on both terms.
+      o->err_est = kEstSafety * std::max(1.5 * kappa * in.alpha * g2, est_rr);
       // With a known margin mu the error is bounded outright (Sylvester
       // argument): F = R - sign(A) has its blocks between the two eigenspaces
       // of A bounded by ||C||_2 / (2 mu) and its blocks within them by

@@ -97,9 +97,9 @@ def test_timed_workload_every_entry_matches_the_oracle():
     assert abs(info.trace - (8192 - 2 * k)) < 1e-6
     R_ex, _ = _exact(8192, "16", 1e-2)
     err_2, err_fro = _check_against_oracle(R, R_ex, 1e-6)
-    # the library's own error estimate is not below the true error by more
-    # than the 1.5 safety factor it carries
-    assert info.err_est >= err_2 / 1.5, (info.err_est, err_2)
+    # the library's own error estimate (with its safety factor) is not below
+    # the true error
+    assert info.err_est >= err_2, (info.err_est, err_2)
     # the whole difference, not only its largest direction: the Frobenius
     # norm bounds every singular value at once
     assert err_fro <= 4e-6, err_fro
