@@ -414,6 +414,9 @@ cudaError_t alpha_from_rho(const double* nrm, double c, double* scal, int kscale
 // dst (FP16) = src (FP64) rounded by way of the nearest float (integer
 // operations; may differ from a direct rounding at exact FP16 ties); n even.
 cudaError_t to_f16(const double* src, size_t n, void* dst, cudaStream_t st);
+// dst (FP16) = hi + lo of a BF16 pair of planes (plane stride n; hi alone when
+// pair == 0), summed in FP32 and rounded once; n even.
+cudaError_t bf16_pair_to_f16(const void* src, size_t n, int pair, void* dst, cudaStream_t st);
 // dst (FP16) = sigma E + 3/4 Q / sigma, Q = (sigma E)^2: sigma W, W = E + 3/4 E^2,
 // the weight of the quintic polish step R <- R + 1/2 R W; n a multiple of 4.
 cudaError_t polish_weight(const float* E, const float* Q, size_t n, const float* sigma, void* dst, cudaStream_t st);

@@ -50,9 +50,14 @@ __device__ __forceinline__ void store_digit_quad(__half* planes, size_t idx, con
   w.y = *reinterpret_cast<const uint32_t*>(&b);
   *reinterpret_cast<uint2*>(planes + idx) = w;
 }
-__device__ __forceinline__ void store_digit_quad(uint8_t* planes, size_t idx, const int* dg) {
-  *reinterpret_cast<uint32_t*>(planes + idx) =
-      e4m3_of_int(dg[0]) | (e4m3_of_int(dg[1]) << 8) | (e4m3_of_int(dg[2]) << 16) | (e4m3_of_int(dg[3]) << 24);
+// FP8: the E4M3 bytes of the 33 digit values -16 .. 16 come from a table in
+// shared memory (filled by the block from e4m3_of_int before use)
+__device__ __forceinline__ void store_digit_quad(uint8_t* planes, size_t idx, const int* dg, const uint8_t* tbl) {
+  *reinterpret_cast<uint32_t*>(planes + idx) = (uint32_t)tbl[dg[0] + 16] | ((uint32_t)tbl[dg[1] + 16] << 8) |
+                                               ((uint32_t)tbl[dg[2] + 16] << 16) | ((uint32_t)tbl[dg[3] + 16] << 24);
+}
+__device__ __forceinline__ void store_digit_quad(__half* planes, size_t idx, const int* dg, const uint8_t*) {
+  store_digit_quad(planes, idx, dg);
 }
 
 // Digit planes of one row per warp (8 rows per block; grid.y = matrix).
@@ -68,6 +73,9 @@ template <typename D>
 __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrows, D* __restrict__ planes,
                                   double* __restrict__ sigma, double* __restrict__ diag, int n_planes,
                                   int beta, const int* __restrict__ mat_dp, int keep_diag) {
+  __shared__ uint8_t tbl[33];
+  if (threadIdx.x < 33) tbl[threadIdx.x] = (uint8_t)e4m3_of_int((int)threadIdx.x - 16);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int m = blockIdx.y;
@@ -140,7 +148,7 @@ __global__ void split_rows_kernel(const double* __restrict__ M, int ld, int nrow
         n[h] -= q * (1ll << sh);                              // |n| <= 2^(sh-1)
         dg[h] = (int)q;
       }
-      store_digit_quad(pl, (size_t)p * slot + k, dg);
+      store_digit_quad(pl, (size_t)p * slot + k, dg, tbl);
     }
   }
 }
@@ -358,6 +366,25 @@ __global__ void polish_weight_kernel(const float* __restrict__ E, const float* _
     w.x = *reinterpret_cast<const uint32_t*>(&lo);
     w.y = *reinterpret_cast<const uint32_t*>(&hi);
     reinterpret_cast<uint2*>(dst)[i] = w;
+  }
+}
+
+// dst (FP16) = hi + lo of a BF16 pair of planes (plane stride n), or hi
+// alone: the sum is exact in FP32, then rounded to FP16 once; two elements
+// per thread and iteration
+__global__ void bf16_pair_to_f16_kernel(const __nv_bfloat16* __restrict__ src, size_t n, int pair,
+                                        __half* __restrict__ dst) {
+  const size_t n2 = n >> 1;
+  const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(src);
+  const __nv_bfloat162* l2 = reinterpret_cast<const __nv_bfloat162*>(src + n);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    float2 v = __bfloat1622float2(h2[i]);
+    if (pair) {
+      const float2 w = __bfloat1622float2(l2[i]);
+      v.x += w.x;
+      v.y += w.y;
+    }
+    reinterpret_cast<__half2*>(dst)[i] = __floats2half2_rn(v.x, v.y);
   }
 }
 
@@ -1132,6 +1159,12 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
 cudaError_t to_f16(const double* src, size_t n, void* dst, cudaStream_t st) {
   if (n & 1) return cudaErrorInvalidValue;
   to_f16_kernel<<<grid_for(n / 2), 256, 0, st>>>(src, n, (__half*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t bf16_pair_to_f16(const void* src, size_t n, int pair, void* dst, cudaStream_t st) {
+  if (n & 1) return cudaErrorInvalidValue;
+  bf16_pair_to_f16_kernel<<<grid_for(n / 2), 256, 0, st>>>((const __nv_bfloat16*)src, n, pair, (__half*)dst);
   return cudaGetLastError();
 }
 

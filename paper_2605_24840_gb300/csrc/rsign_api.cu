@@ -340,6 +340,7 @@ struct RefineIn {
   double* R64;          // in: stage-1 result; out: refined reflector
   void* const* X;       // X_0 .. X_{M-1} (operand type)
   void* const* Et;      // I - a_m^2 X_m^2, m = 0 .. M-1 (operand type)
+  bool pairs;           // X and Et slots hold hi/lo pairs of planes (plane stride dp^2)
   const double* a;      // step scalings a_m of the stage-1 trajectory (nullptr: all 1)
   int n_a;              // entries of a (steps beyond use 1)
   double margin;        // lower bound of min |lam_i(A)| (NaN: unknown)
@@ -623,6 +624,23 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   // operand of the checks: A 2^kA, 2^kA ~ alpha ~ 1/||A|| (results scaled back)
   const int kA = std::ilogb(in.alpha);
   RS_TRY(c.ok(split_f32(in.A64, dd, A_hi, A_lo, kA, nullptr, st)) ? cudaSuccess : c.err);
+  // Operands of the tangent solve, always FP16 (11-bit significands): the
+  // stored FP16 iterates themselves (their hi planes), or, for BF16 stage-1
+  // iterates, FP16 copies of hi + lo made once here.  The BF16 tangent solve
+  // (8-bit significands) stopped contracting once the margin fell to ~2e-4
+  // of ||H||; its relative error there is ~u / (scaled margin).
+  std::vector<void*> X_t(in.X, in.X + in.M), Et_t(in.Et, in.Et + in.M);
+  if (in.fmt == 1) {
+    for (int m = 0; m < in.M_tangent; ++m) {
+      void *xc = nullptr, *ec = nullptr;
+      RS_TRY(mem.alloc(&xc, dd * 2));
+      RS_TRY(mem.alloc(&ec, dd * 2));
+      RS_TRY(c.ok(bf16_pair_to_f16(in.X[m], dd, in.pairs ? 1 : 0, xc, st)) ? cudaSuccess : c.err);
+      RS_TRY(c.ok(bf16_pair_to_f16(in.Et[m], dd, in.pairs ? 1 : 0, ec, st)) ? cudaSuccess : c.err);
+      X_t[m] = xc;
+      Et_t[m] = ec;
+    }
+  }
   double kappa = NAN;
   for (int sw = 0; sw <= in.max_sweeps; ++sw) {
     if (sw >= 1) {
@@ -714,10 +732,10 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     // recursion: E grows by at most ~2.6 per step, well inside the FP16 range
     // (FP16's relative precision does not depend on the scale), so each
     // step's epilogue writes the next step's operand directly.
-    if (!c.ok(scale_to_lp(E32, dd, fs + 5, Elp, in.fmt, st))) return c.err;
+    if (!c.ok(scale_to_lp(E32, dd, fs + 5, Elp, 0, st))) return c.err;
     for (int m = 0; m < in.M_tangent; ++m) {
-      if (!c.ok(tc(Elp, in.Et[m], in.fmt, 0, TC_EPI_STORE_F32, P32))) return c.err;   // E Et
-      if (!c.ok(tc(in.X[m], Elp, in.fmt, 0, TC_EPI_STORE_LP, Qlp))) return c.err;     // X E
+      if (!c.ok(tc(Elp, Et_t[m], 0, 0, TC_EPI_STORE_F32, P32))) return c.err;   // E Et
+      if (!c.ok(tc(X_t[m], Elp, 0, 0, TC_EPI_STORE_LP, Qlp))) return c.err;     // X E
       // (X E) X with the tangent step fused into its epilogue (E updated in place)
       TcGemmArgs tg{};
       tg.dp = dp; tg.d_real = d; tg.sym = 1; tg.epi = TC_EPI_TANGENT; tg.n_groups = 1;
@@ -726,7 +744,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       tg.tg_E = E32; tg.tg_P = P32; tg.tg_sigma = fs + 5; tg.tg_max = bmax;
       tg.tg_a = (in.a != nullptr && m < in.n_a) ? (float)in.a[m] : 1.0f;
       tg.tg_Elp = (m + 1 < in.M_tangent) ? Elp : nullptr;
-      if (!c.ok(tc_gemm(tg, Qlp, 1, in.X[m], 1, in.fmt, c.num_sms, st))) return c.err;
+      if (!c.ok(tc_gemm(tg, Qlp, 1, X_t[m], 1, 0, c.num_sms, st))) return c.err;
     }
     // ||E||_2 on the side stream (after ||E_0||_2 there), beside the
     // correction and the polish, which only read E
@@ -1136,7 +1154,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         int ns_unused = 0;
         refine_stage_plan(lower_end, steps_low, &ns_unused, &in.M_tangent);
       }
-      in.A64 = A64; in.R64 = xb64[0]; in.X = xs.data(); in.Et = es.data();
+      in.A64 = A64; in.R64 = xb64[0]; in.X = xs.data(); in.Et = es.data(); in.pairs = split;
       in.a = coef.empty() ? nullptr : coef.data(); in.n_a = (int)coef.size();
       in.max_sweeps = std::max(1, opt.max_sweeps);
       in.margin = auto_shift ? margin_lb : opt.margin;
