@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--max-sweeps", type=int, default=4)
     p.add_argument("--split-until", type=float, default=-1.0,
                    help="threshold of the stage-1 split rule (pairs while l_m < this); -1 the library default")
+    p.add_argument("--copy-streams", type=int, default=-1,
+                   help="e2e: staged host copies split over this many streams (-1 the library default)")
     p.add_argument("--host-mapped", type=int, default=-1, choices=[-1, 0, 1],
                    help="e2e: page-locked host buffers read/written in place (1) or staged (0); -1 the default")
     p.add_argument("--tangent-cut", type=int, default=-1, choices=[-1, 0, 1],
@@ -514,6 +516,8 @@ def apply_switches(args, rs):
         rs.dbg_set_tangent_cut(args.tangent_cut)
     if args.host_mapped >= 0:
         rs.dbg_set_host_mapped(args.host_mapped)
+    if args.copy_streams >= 1:
+        rs.dbg_set_copy_streams(args.copy_streams)
 
 
 def run_batched(args):

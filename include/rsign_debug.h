@@ -165,6 +165,15 @@ int32_t rsign_dbg_set_tangent_cut(int32_t on);
 int32_t rsign_dbg_set_host_mapped(int32_t on);
 
 /*
+ * Staged host copies of rsign_reflector[_ex] (H in, R out, each at least
+ * 64 MiB) split over n streams (1 .. 8) that fork from and join back into
+ * the call's stream, so that several copy engines share the link; 1 (the
+ * default) copies on the call's stream alone.  Other values leave the
+ * setting unchanged.  Process-wide; returns the previous setting.
+ */
+int32_t rsign_dbg_set_copy_streams(int32_t n);
+
+/*
  * Threshold of the stage-1 split rule (rsign_dbg_set_split_steps(-2)): the
  * iterates whose known lower end of the spectrum is below l are carried as
  * hi/lo pairs.  l in (0, 1]; other values leave it unchanged.  Process-wide;

@@ -200,6 +200,8 @@ def load():
     lib.rsign_dbg_stage_plan.restype = ctypes.c_int
     lib.rsign_dbg_set_split_until.argtypes = [dbl]
     lib.rsign_dbg_set_split_until.restype = dbl
+    lib.rsign_dbg_set_copy_streams.argtypes = [i32]
+    lib.rsign_dbg_set_copy_streams.restype = i32
     lib.rsign_dbg_set_host_mapped.argtypes = [i32]
     lib.rsign_dbg_set_host_mapped.restype = i32
     lib.rsign_dbg_set_tangent_cut.argtypes = [i32]
@@ -619,6 +621,11 @@ def dbg_set_split_until(l):
     """Threshold of the stage-1 split rule (pairs while the known lower end is below l); returns the
     previous threshold."""
     return float(load().rsign_dbg_set_split_until(float(l)))
+
+
+def dbg_set_copy_streams(n):
+    """Staged host copies split over n streams (1..8); returns the previous setting."""
+    return int(load().rsign_dbg_set_copy_streams(int(n)))
 
 
 def dbg_set_host_mapped(on):

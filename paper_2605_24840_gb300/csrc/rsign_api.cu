@@ -86,6 +86,44 @@ bool is_device_ptr(const void* p) {
 // boxes, ~150 ms slower on a third; the copy engines are the steadier path.
 int g_host_mapped = 0;
 
+// Staged host copies of H and R split over this many streams (1 = one copy
+// on the call's stream; more lets several copy engines share the link).
+int g_copy_streams = 1;
+
+// dst <- src (bytes, a staged host copy) on `st`: split over g_copy_streams
+// streams that fork from and join back into `st` (stream-ordered for every
+// caller of `st`).  Parts are whole multiples of 1 MiB but the last.
+cudaError_t staged_copy(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
+  const int n = std::max(1, std::min(g_copy_streams, 8));
+  if (n == 1 || bytes < ((size_t)64 << 20)) return cudaMemcpyAsync(dst, src, bytes, kind, st);
+  cudaStream_t hs[8] = {};
+  cudaEvent_t fork = nullptr, join[8] = {};
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+  const size_t part = ((bytes / n) + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+  for (int q = 1; q < n && e == cudaSuccess; ++q) {
+    const size_t off = part * q;
+    if (off >= bytes) break;
+    const size_t len = std::min(part, bytes - off);
+    if ((e = cudaStreamCreateWithFlags(&hs[q], cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(hs[q], fork, 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, len, kind,
+                             hs[q])) != cudaSuccess)
+      break;
+    e = cudaEventRecord(join[q], hs[q]);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, std::min(part, bytes), kind, st);
+  for (int q = 1; q < n; ++q)
+    if (join[q] && e == cudaSuccess) e = cudaStreamWaitEvent(st, join[q], 0);
+  for (int q = 1; q < n; ++q) {
+    if (join[q]) cudaEventDestroy(join[q]);
+    if (hs[q]) cudaStreamDestroy(hs[q]);  // released once its work is done
+  }
+  if (fork) cudaEventDestroy(fork);
+  return e;
+}
+
 // Device address of page-locked host memory (cudaHostAlloc / cudaHostRegister:
 // mapped into the device's address space), or nullptr for any other pointer.
 // Kernels read and write such memory directly over the CPU-GPU link, with
@@ -853,7 +891,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
       Hd = const_cast<double*>(h_map);
     } else {
       if (mem.alloc((void**)&Hd, (size_t)d * d * 8) != cudaSuccess) return fail_cuda();
-      if (cudaMemcpyAsync(Hd, H, (size_t)d * d * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      if (staged_copy(Hd, H, (size_t)d * d * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return fail_cuda();
     }
   }
@@ -1207,7 +1245,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
   // ---- certificate and output
   if (!c.ok(trace_f64(Rfinal, dp, d, ctl->scal + 2, st))) return fail_cuda();
   if (!c.ok(copy_unpad(Rfinal, dp, Rd, d, st))) return fail_cuda();
-  if (!r_dev && !r_map && cudaMemcpyAsync(R, Rd, (size_t)d * d * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (!r_dev && !r_map && staged_copy(R, Rd, (size_t)d * d * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return fail_cuda();
   if (opt.timing) cudaEventRecord(ev[3], st);
   if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1838,6 +1876,12 @@ rsign_status rsign_dbg_stage_plan(double alpha_margin, double u0, int32_t scaled
 double rsign_dbg_set_split_until(double l) {
   const double prev = g_split_until;
   if (l > 0.0 && l <= 1.0) g_split_until = l;
+  return prev;
+}
+
+int32_t rsign_dbg_set_copy_streams(int32_t n) {
+  const int prev = g_copy_streams;
+  if (n >= 1 && n <= 8) g_copy_streams = n;
   return prev;
 }
 

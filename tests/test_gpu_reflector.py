@@ -136,6 +136,27 @@ def test_pinned_host_buffers_give_the_device_bits(mapped):
     assert spec_norm_sym(Rh.numpy() - oracle.reflector_from_basis(spec.Q, k)) <= 1e-6
 
 
+@pytest.mark.parametrize("streams", [1, 4])
+def test_staged_host_copies_over_several_streams_give_the_device_bits(streams):
+    # host H and R of 128 MiB each, copied in and out in parts on several
+    # streams that fork from and join the call's stream: the device bits
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    d, k = 4096, 16
+    H, lam, Q = workloads.controlled_spectrum_torch(d, k, 1e-2, seed=4097)
+    Rd, _, st_d = rs.reflector(H, k, 0.0, tol=1e-6, policy=rs.Policy.FP16_REFINE)
+    Hh = H.cpu().numpy()
+    Rh = np.empty((d, d))
+    prev = rs.dbg_set_copy_streams(streams)
+    try:
+        _, info_h, st_h = rs.reflector(Hh, k, 0.0, tol=1e-6, policy=rs.Policy.FP16_REFINE, out=Rh)
+    finally:
+        rs.dbg_set_copy_streams(prev)
+    torch.cuda.synchronize()
+    assert st_d == rs.Status.OK and st_h == rs.Status.OK
+    assert np.array_equal(Rd.cpu().numpy(), Rh)
+
+
 def test_shift_outside_gap_fails_certificate():
     torch = cuda_or_skip()
     rs = lib_or_fail()
