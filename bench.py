@@ -120,13 +120,14 @@ def job_ms_per_unit(elapsed_max_ms, steps, ws):
     return elapsed_max_ms / (steps * ws)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per stage-1
-# tcgen05 launch, mean over the SYRK and symmetric-update launches of one call,
-# from the ncu launch list summarised under profiles/ (same kernel source and
-# workload); empty until counters of the current kernel are taken.
-# Algorithmic bytes of one launch: read X (hi + lo, 4 d^2) and write the result
-# (hi + lo, 4 d^2) = 8 d^2 = 0.54 GB at d = 8192.
-MEASURED_TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one stage-1
+# tcgen05 launch at d = 8192, from a one-launch ncu capture of the hi/lo SYRK
+# (same kernel source and operand layout; summarised under profiles/), keyed
+# by (d, policy, hi/lo stage 1).  Algorithmic bytes of that launch: read X
+# (hi + lo, 4 d^2) and write the result (hi + lo, 4 d^2) = 8 d^2 = 0.54 GB.
+MEASURED_TRAFFIC = {
+    (8192, "FP16_REFINE", 1): 1.792353e9 + 0.236274e9,
+}
 
 
 def peaks():
