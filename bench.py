@@ -120,13 +120,15 @@ def job_ms_per_unit(elapsed_max_ms, steps, ws):
     return elapsed_max_ms / (steps * ws)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one stage-1
-# tcgen05 launch at d = 8192, from a one-launch ncu capture of the hi/lo SYRK
-# (same kernel source and operand layout; summarised under profiles/), keyed
-# by (d, policy, hi/lo stage 1).  Algorithmic bytes of that launch: read X
-# (hi + lo, 4 d^2) and write the result (hi + lo, 4 d^2) = 8 d^2 = 0.54 GB.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per stage-1
+# tcgen05 launch at d = 8192, the mean of one-launch ncu captures of the hi/lo
+# SYRK (2.029 GB) and the hi/lo symmetric update (2.348 GB), same kernel
+# source and operand layout (summarised under profiles/), keyed by (d,
+# policy, hi/lo stage 1).  Algorithmic bytes of a launch: read X (hi + lo,
+# 4 d^2) and write the result (hi + lo, 4 d^2) = 8 d^2 = 0.54 GB; the update
+# also reads the current iterate (another 4 d^2).
 MEASURED_TRAFFIC = {
-    (8192, "FP16_REFINE", 1): 1.792353e9 + 0.236274e9,
+    (8192, "FP16_REFINE", 1): 0.5 * ((1.792353e9 + 0.236274e9) + (2.111479e9 + 0.236453e9)),
 }
 
 

@@ -480,30 +480,45 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
         }
         continue;
       }
+      // Last group, eight elements at a time: every input of the eight is
+      // loaded before the first of their stores.  The stores go to `out`,
+      // which the compiler cannot tell apart from the FP64 inputs, so a load
+      // placed after a store waits for it: one DRAM round trip per element
+      // instead of one per eight.
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int jj = hh + q;
-      const int j = j0 + jj;
-      const bool mirror = a.sym && j > i;
-      if (a.sym && j < i) continue;
-      const size_t e = row + j;
-      const long long vv = pv[q];
-      double x = oz_value(a, vv, pk[q], ei + pow2_exp(cs[j]));
-      if (with_diag) {
-        // exact diagonal terms: d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
-        const double dbj = a.b_diag[voff + j];
-        x += dai * b_full[e] + a_full[e] * dbj - (i == j ? dai * dbj : 0.0);
+      for (int o = 0; o < 16; o += 8) {
+        const int jb = j0 + hh + o;
+        const size_t eb = row + jb;
+        int ce[8];
+        double af[8], bf[8], db[8], xi[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          ce[q] = pow2_exp(cs[jb + q]);
+          af[q] = with_diag ? a_full[eb + q] : 0.0;
+          bf[q] = with_diag ? b_full[eb + q] : 0.0;
+          db[q] = with_diag ? a.b_diag[voff + jb + q] : 0.0;
+          xi[q] = a.xin64 != nullptr ? a.xin64[moff + eb + q] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = jb + q;
+          const bool mirror = a.sym && j > i;
+          if (a.sym && j < i) continue;
+          const size_t e = eb + q;
+          double x = oz_value(a, pv[o + q], pk[o + q], ei + ce[q]);
+          // exact diagonal terms: d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
+          if (with_diag) x += dai * bf[q] + af[q] * db[q] - (i == j ? dai * db[q] : 0.0);
+          if (a.xin64 != nullptr) x = xi[q] + x;
+          if (a.oz_ident) {
+            const bool real = i < d_real && j < d_real;
+            x = real ? ((i == j) ? 1.0 - x : -x) : 0.0;
+            const float xf = (float)x;
+            if (real) accf = fmaf(mirror ? 2.0f * xf : xf, xf, accf);
+          }
+          out[e] = x;
+          if (mirror) out[(size_t)j * ld + i] = x;
+        }
       }
-      if (a.xin64 != nullptr) x = a.xin64[moff + e] + x;
-      if (a.oz_ident) {
-        const bool real = i < d_real && j < d_real;
-        x = real ? ((i == j) ? 1.0 - x : -x) : 0.0;
-        const float xf = (float)x;
-        if (real) accf = fmaf(mirror ? 2.0f * xf : xf, xf, accf);
-      }
-      out[e] = x;
-      if (mirror) out[(size_t)j * ld + i] = x;
-    }
     }
     acc1 += (double)accf;
   }
@@ -569,26 +584,42 @@ __device__ __forceinline__ void epilogue_oz_tmem(const TcGemmArgs& a, int i, int
   const double* a_full = with_diag ? a.a_full + moff : nullptr;
   const double* b_full = with_diag ? a.b_full + moff : nullptr;
   float accf = 0.0f;
-#pragma unroll 4
-  for (int jj = 0; jj < 32; ++jj) {
-    const int j = j0 + jj;
-    const bool mirror = a.sym && j > i;
-    if (a.sym && j < i) continue;
-    const size_t e = row + j;
-    double x = oz_value(a, V[jj], two ? park[e] : 0ll, ei + pow2_exp(cs[j]));
-    if (with_diag) {
-      const double dbj = a.b_diag[voff + j];
-      x += dai * b_full[e] + a_full[e] * dbj - (i == j ? dai * dbj : 0.0);
+  // eight elements at a time, every input loaded before the first of their
+  // stores (a load after a store to `out` would wait for it)
+#pragma unroll
+  for (int o = 0; o < 32; o += 8) {
+    const int jb = j0 + o;
+    const size_t eb = row + jb;
+    int ce[8];
+    long long pk[8];
+    double af[8], bf[8], db[8], xi[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      ce[q] = pow2_exp(cs[jb + q]);
+      pk[q] = two ? park[eb + q] : 0ll;
+      af[q] = with_diag ? a_full[eb + q] : 0.0;
+      bf[q] = with_diag ? b_full[eb + q] : 0.0;
+      db[q] = with_diag ? a.b_diag[voff + jb + q] : 0.0;
+      xi[q] = a.xin64 != nullptr ? a.xin64[moff + eb + q] : 0.0;
     }
-    if (a.xin64 != nullptr) x = a.xin64[moff + e] + x;
-    if (a.oz_ident) {
-      const bool real = i < d_real && j < d_real;
-      x = real ? ((i == j) ? 1.0 - x : -x) : 0.0;
-      const float xf = (float)x;
-      if (real) accf = fmaf(mirror ? 2.0f * xf : xf, xf, accf);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = jb + q;
+      const bool mirror = a.sym && j > i;
+      if (a.sym && j < i) continue;
+      const size_t e = eb + q;
+      double x = oz_value(a, V[o + q], pk[q], ei + ce[q]);
+      if (with_diag) x += dai * bf[q] + af[q] * db[q] - (i == j ? dai * db[q] : 0.0);
+      if (a.xin64 != nullptr) x = xi[q] + x;
+      if (a.oz_ident) {
+        const bool real = i < d_real && j < d_real;
+        x = real ? ((i == j) ? 1.0 - x : -x) : 0.0;
+        const float xf = (float)x;
+        if (real) accf = fmaf(mirror ? 2.0f * xf : xf, xf, accf);
+      }
+      out[e] = x;
+      if (mirror) out[(size_t)j * ld + i] = x;
     }
-    out[e] = x;
-    if (mirror) out[(size_t)j * ld + i] = x;
   }
   acc1 += (double)accf;
 }
