@@ -38,7 +38,16 @@ namespace {
 // One pipeline stage holds 128 bytes of K per operand row (one 128-byte
 // swizzle row): BK = 64 FP16/BF16 elements, or 128 FP8 elements (kBK8).
 constexpr int BM = 128, BK = 64, kBK8 = 128;
-constexpr int NUM_THREADS = 192;
+// Epilogue warps: four (one per TMEM lane quadrant), or eight for the FP8
+// digit-plane products on 256-column tiles, two per quadrant, each taking
+// half of the tile's 32-column chunks.  Their conversion epilogue (int64 level sums to FP64
+// with the exact diagonal terms, once per element) is a long dependent
+// chain per element; a second warp per quadrant doubles the instructions in
+// flight.
+template <int EPI, typename T, int BN>
+constexpr int tc_epi_warps() { return (EPI == TC_EPI_OZAKI && sizeof(T) == 1 && BN == 256) ? 8 : 4; }
+template <int EPI, typename T, int BN>
+constexpr int tc_threads() { return 64 + 32 * tc_epi_warps<EPI, T, BN>(); }
 
 template <int BN>
 struct Cfg {
@@ -227,13 +236,32 @@ __device__ __forceinline__ double i128_scaled(__int128 v, int e) {
   return __longlong_as_double((long long)bits);
 }
 
+// v 2^e rounded to the nearest binary64 (ties to even) for a 64-bit v: one
+// hardware conversion (correctly rounded), then the exponent moved by e with
+// integer operations; the same value as i128_scaled((__int128)v, e), at a
+// small fraction of its instructions (the conversion epilogue of a tile runs
+// once per element on four warps, so its instruction count is what shows).
+__device__ __forceinline__ double i64_scaled(long long v, int e) {
+  if (v == 0) return 0.0;
+  const double f = __ll2double_rn(v);
+  const long long b = __double_as_longlong(f);
+  const int eb = (int)((b >> 52) & 0x7FF) + e;
+  if (eb <= 0 || eb >= 2047) return ldexp(f, e);  // outside the normal range
+  return __longlong_as_double(b + ((long long)e << 52));
+}
+
 // Final value of one element: the super-group sums V1 (last) and V0 combined
-// exactly in 128 bits, converted, scaled by sigma_i sigma_j 2^unit_exp (and
-// xin_mult when an FP64 input is added) through the exponent.
+// exactly in 128 bits (one sum: 64 bits), converted, scaled by
+// sigma_i sigma_j 2^unit_exp (and xin_mult when an FP64 input is added)
+// through the exponent.
+// F8: FP8 digit planes (5-bit digits, at most seven levels), whose launches
+// have one sum and no FP64 input (checked on the host).
+template <bool F8>
 __device__ __forceinline__ double oz_value(const TcGemmArgs& a, long long V1, long long V0, int e_ij) {
-  __int128 t = (__int128)V1;
-  if (a.n_sg == 2) t += ((__int128)V0) << a.oz_sh01;
-  return i128_scaled(t, e_ij + a.oz_unit_exp + (a.xin64 != nullptr ? a.xin_mult_exp : 0));
+  const int e = e_ij + a.oz_unit_exp + (!F8 && a.xin64 != nullptr ? a.xin_mult_exp : 0);
+  if (F8 || a.n_sg != 2) return i64_scaled(V1, e);
+  const __int128 t = (__int128)V1 + (((__int128)V0) << a.oz_sh01);
+  return i128_scaled(t, e);
 }
 
 // Epilogue for one 32-column chunk held by one thread (row i, columns j0..j0+31).
@@ -409,7 +437,9 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
     // (upper) element is carried between groups; the mirror is written once.
     double* out = reinterpret_cast<double*>(a.out) + moff;
     long long* outi = reinterpret_cast<long long*>(out);
-    const bool two = a.n_sg == 2;
+    constexpr bool F8 = sizeof(T) == 1;
+    const bool two = !F8 && a.n_sg == 2;
+    const bool use_xin = !F8 && a.xin64 != nullptr;
     const int sg = two ? a.group_sg[g] : 0;
     long long* accp = (two && sg == 0) ? a.acc64 + moff : outi;
     const bool first = two ? (a.group_first[g] != 0) : (g == 0);
@@ -497,7 +527,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
           af[q] = with_diag ? a_full[eb + q] : 0.0;
           bf[q] = with_diag ? b_full[eb + q] : 0.0;
           db[q] = with_diag ? a.b_diag[voff + jb + q] : 0.0;
-          xi[q] = a.xin64 != nullptr ? a.xin64[moff + eb + q] : 0.0;
+          xi[q] = use_xin ? a.xin64[moff + eb + q] : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -505,11 +535,11 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
           const bool mirror = a.sym && j > i;
           if (a.sym && j < i) continue;
           const size_t e = eb + q;
-          double x = oz_value(a, pv[o + q], pk[o + q], ei + ce[q]);
+          double x = oz_value<F8>(a, pv[o + q], pk[o + q], ei + ce[q]);
           // exact diagonal terms: d^A_i B_ij + A_ij d^B_j - [i == j] d^A_i d^B_j
           if (with_diag) x += dai * bf[q] + af[q] * db[q] - (i == j ? dai * db[q] : 0.0);
-          if (a.xin64 != nullptr) x = xi[q] + x;
-          if (a.oz_ident) {
+          if (use_xin) x = xi[q] + x;
+          if (!F8 && a.oz_ident) {
             const bool real = i < d_real && j < d_real;
             x = real ? ((i == j) ? 1.0 - x : -x) : 0.0;
             const float xf = (float)x;
@@ -533,12 +563,14 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
 // FP64 (times its weight) and parked in acc64 (as FP64) for the last group.
 // The TMEM loads and stores are warp-collective; every flag that selects
 // them depends on the group only.
+template <bool F8>
 __device__ __forceinline__ void epilogue_oz_tmem(const TcGemmArgs& a, int i, int j0, int g, const float* v,
                                                  double& acc1, size_t moff, size_t voff, int d_real,
                                                  uint32_t vaddr) {
   const int ld = a.dp;
   const size_t row = (size_t)i * ld;
-  const bool two = a.n_sg == 2;
+  const bool two = !F8 && a.n_sg == 2;
+  const bool use_xin = !F8 && a.xin64 != nullptr;
   const int sg = two ? a.group_sg[g] : 0;
   const bool first = two ? (a.group_first[g] != 0) : (g == 0);
   const bool last = (g == a.n_groups - 1);
@@ -600,7 +632,7 @@ __device__ __forceinline__ void epilogue_oz_tmem(const TcGemmArgs& a, int i, int
       af[q] = with_diag ? a_full[eb + q] : 0.0;
       bf[q] = with_diag ? b_full[eb + q] : 0.0;
       db[q] = with_diag ? a.b_diag[voff + jb + q] : 0.0;
-      xi[q] = a.xin64 != nullptr ? a.xin64[moff + eb + q] : 0.0;
+      xi[q] = use_xin ? a.xin64[moff + eb + q] : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -608,10 +640,10 @@ __device__ __forceinline__ void epilogue_oz_tmem(const TcGemmArgs& a, int i, int
       const bool mirror = a.sym && j > i;
       if (a.sym && j < i) continue;
       const size_t e = eb + q;
-      double x = oz_value(a, V[o + q], pk[q], ei + ce[q]);
+      double x = oz_value<F8>(a, V[o + q], pk[q], ei + ce[q]);
       if (with_diag) x += dai * bf[q] + af[q] * db[q] - (i == j ? dai * db[q] : 0.0);
-      if (a.xin64 != nullptr) x = xi[q] + x;
-      if (a.oz_ident) {
+      if (use_xin) x = xi[q] + x;
+      if (!F8 && a.oz_ident) {
         const bool real = i < d_real && j < d_real;
         x = real ? ((i == j) ? 1.0 - x : -x) : 0.0;
         const float xf = (float)x;
@@ -625,7 +657,7 @@ __device__ __forceinline__ void epilogue_oz_tmem(const TcGemmArgs& a, int i, int
 }
 
 template <int EPI, typename T, int BN>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+__global__ void __launch_bounds__(tc_threads<EPI, T, BN>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ TcGemmArgs args, const uint32_t idesc) {
   using C = Cfg<BN>;
@@ -635,6 +667,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   constexpr bool F8 = sizeof(T) == 1;
   constexpr int BKE = F8 ? kBK8 : BK;
   static_assert(!F8 || EPI == TC_EPI_OZAKI, "FP8 operands only for the digit-plane products");
+  constexpr int NEPI = tc_epi_warps<EPI, T, BN>();
+  static_assert(NEPI == 4 || !(EPI == TC_EPI_NS_SYRK || EPI == TC_EPI_NS_UPDATE || EPI == TC_EPI_TANGENT),
+                "per-tile partials assume one epilogue warp per quadrant");
   // 128-column digit-plane products keep their int64 sums in TMEM columns 256..511
   constexpr bool OZ_TMEM = (EPI == TC_EPI_OZAKI && BN == 128);
   constexpr uint32_t TMEM_ALLOC = OZ_TMEM ? 512u : C::TMEM_COLS;
@@ -662,7 +697,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&tfull[s]), 1);
-      mbar_init(smem_u32(&tempty[s]), 128);
+      mbar_init(smem_u32(&tempty[s]), 32 * NEPI);
     }
     mbar_init(smem_u32(drain), 1);
     fence_mbar_init();
@@ -759,7 +794,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else {
     // -------------------------------------------------------------- epilogue
-    const int quad = warp & 3;
+    const int quad = warp & 3;  // the TMEM lane quadrant this warp may access
+    // chunks of this warp: all of them, or one half with two warps per quadrant
+    constexpr int CPW = (BN / 32) / (NEPI / 4);
+    const int c_lo = ((warp - 2) >> 2) * CPW;
     const int r = quad * 32 + lane;
     int acc_it = 0;
     bool ok = true;
@@ -783,7 +821,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN);
         const int wrow0 = u.bm * BM + quad * 32;  // first row of this warp
-        for (int c = 0; c < BN / 32; ++c) {
+        for (int c = c_lo; c < c_lo + CPW; ++c) {
           const int j0 = u.bn * BN + c * 32;
           // symmetric schedule: a chunk wholly below this warp's rows is the
           // mirror image of elements that their row owners write
@@ -794,7 +832,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const bool above = j0 > wrow0 + 31;
           if constexpr (OZ_TMEM) {
             const uint32_t vaddr = tmem_base + ((uint32_t)(quad * 32) << 16) + 256u + (uint32_t)(c * 64);
-            epilogue_oz_tmem(args, i, j0, g, v, acc1, moff, voff, d_real, vaddr);
+            epilogue_oz_tmem<F8>(args, i, j0, g, v, acc1, moff, voff, d_real, vaddr);
           } else {
             epilogue_chunk<EPI, T>(args, i, j0, g, v, above, acc1, moff, voff, d_real);
           }
@@ -875,7 +913,7 @@ cudaError_t launch(const TcGemmArgs& a, const CUtensorMap& ma, const CUtensorMap
                                     SMEM_BYTES);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  tc_gemm_kernel<EPI, T, BN><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, a, idesc);
+  tc_gemm_kernel<EPI, T, BN><<<grid, tc_threads<EPI, T, BN>(), SMEM_BYTES, st>>>(ma, mb, a, idesc);
   return cudaGetLastError();
 }
 
@@ -931,8 +969,11 @@ cudaError_t tc_gemm(const TcGemmArgs& args, const void* A, int a_slices, const v
     return cudaErrorInvalidValue;
   const int units = TileSched<256>(args.dp, args.sym).n;
   const int grid = units < num_sms ? units : num_sms;
-  if (lp_fmt == 2)  // FP8 E4M3 digit planes (format field 0 of kind::f8f6f4)
-    return args.epi == TC_EPI_OZAKI
+  // FP8 E4M3 digit planes (format field 0 of kind::f8f6f4); their kernel has
+  // two epilogue warps per quadrant, no per-tile partials (no oz_ident), one
+  // level sum and no FP64 input
+  if (lp_fmt == 2)
+    return args.epi == TC_EPI_OZAKI && !args.oz_ident && args.n_sg != 2 && args.xin64 == nullptr
                ? launch<TC_EPI_OZAKI, __nv_fp8_e4m3, 256>(args, ma, mb, grid, idesc_f16(0u, BM, 256), st)
                : cudaErrorInvalidValue;
   const uint32_t idesc = idesc_f16(lp_fmt ? 1u : 0u, BM, 256);
@@ -945,7 +986,7 @@ cudaError_t tc_gemm_grouped(const TcGemmArgs& args, int bn, const void* A, int a
   if (args.units == nullptr || args.n_units < 1 || args.mat_dp == nullptr || args.mat_d == nullptr ||
       (bn != 128 && bn != 256) || args.dp % 256 != 0 || args.n_groups < 1 || args.n_groups > kTcMaxGroups ||
       args.group_start[args.n_groups] > kTcMaxPairs || (args.epi == TC_EPI_OZAKI && lp_fmt == 1) ||
-      (args.epi != TC_EPI_OZAKI && lp_fmt == 2) || lp_fmt < 0 || lp_fmt > 2)
+      (args.epi != TC_EPI_OZAKI && lp_fmt == 2) || (lp_fmt == 2 && (args.oz_ident || args.n_sg == 2 || args.xin64 != nullptr)) || lp_fmt < 0 || lp_fmt > 2)
     return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, args.dp, a_slices, BM, lp_fmt) || !make_map(&mb, B, args.dp, b_slices, bn, lp_fmt))
