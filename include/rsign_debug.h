@@ -226,6 +226,19 @@ int32_t rsign_dbg_set_refine_levels(int32_t polish, int32_t ra_first, int32_t ra
 int32_t rsign_dbg_set_ozaki_tile(int32_t bn);
 
 /*
+ * The digit-plane products' final conversion of an exact int64 level sum v to
+ * FP64, v 2^e rounded to the nearest (ties to even), computed two ways on the
+ * device for n values: a[i] by one correctly rounded int64 -> FP64 conversion
+ * whose exponent is then moved by e[i] (the way the products' epilogue does
+ * it), b[i] by 128-bit integer arithmetic (shift, round to 53 bits, compose
+ * the exponent).  Results outside the normal range go through ldexp on both
+ * sides.  v, e, a, b: device arrays of n entries.  Blocking.  RSIGN_ERR_ARG
+ * for null pointers or n outside 1 .. 2^30.
+ */
+rsign_status rsign_dbg_oz_convert(const int64_t* v, const int32_t* e, int64_t n, double* a, double* b,
+                                  void* stream);
+
+/*
  * The order in which the persistent tcgen05 GEMM visits the 128 x 256 tiles of
  * one dp x dp product (host computation, no GPU): entry t is the (bm, bn) of
  * schedule unit t; sym selects the upper triangle.  With bm == NULL returns
@@ -252,6 +265,16 @@ rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, 
  * accumulation on the FP32 pipe, lanes combined in FP64.  y: device FP64.
  */
 rsign_status rsign_dbg_gemv_df(const double* M, const double* x, int64_t dp, double* y, void* stream);
+
+/*
+ * The same product for a symmetric M, read from its upper triangle only (the
+ * form the a-posteriori check uses): every 128 x 128 tile (I, J), I <= J,
+ * adds M_IJ x_J to y_I and, off the diagonal, M_IJ^T x_I to y_J; the partial
+ * sums of each output row are added in a fixed order.  The tiles below the
+ * diagonal tiles are not read (the diagonal tiles are read whole).  Same
+ * arguments and errors as rsign_dbg_gemv_df.
+ */
+rsign_status rsign_dbg_gemv_df_sym(const double* M, const double* x, int64_t dp, double* y, void* stream);
 
 /*
  * The matrix-free check of the refinement on device FP64 A, R (dp x dp, dp a

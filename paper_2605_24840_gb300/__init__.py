@@ -218,6 +218,10 @@ def load():
     lib.rsign_dbg_fp64e_gemm.restype = ctypes.c_int
     lib.rsign_dbg_gemv_df.argtypes = [vp, vp, i64, vp, vp]
     lib.rsign_dbg_gemv_df.restype = ctypes.c_int
+    lib.rsign_dbg_gemv_df_sym.argtypes = [vp, vp, i64, vp, vp]
+    lib.rsign_dbg_gemv_df_sym.restype = ctypes.c_int
+    lib.rsign_dbg_oz_convert.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.rsign_dbg_oz_convert.restype = ctypes.c_int
     lib.rsign_dbg_commutator_check.argtypes = [vp, vp, i64, i64, i32, vp, vp]
     lib.rsign_dbg_commutator_check.restype = ctypes.c_int
     lib.rsign_dbg_tridiag_ritz.argtypes = [dp, dp, i32, i32, dp, dp]
@@ -669,6 +673,21 @@ def dbg_bounded_wait(arrive, limit_ns, status, stream=None):
     return Status(lib.rsign_dbg_bounded_wait(int(arrive), int(limit_ns), status.data_ptr(), _stream_ptr(stream, True)))
 
 
+def dbg_oz_convert(v, e, stream=None):
+    """(a, b): the digit-plane epilogue's int64 -> FP64 conversion v 2^e done two ways on the device
+    (correctly rounded conversion plus exponent shift; 128-bit integer rounding).  v int64, e int32 (CUDA)."""
+    torch = _torch()
+    lib = load()
+    n = int(v.numel())
+    a = torch.empty(n, dtype=torch.float64, device=v.device)
+    b = torch.empty(n, dtype=torch.float64, device=v.device)
+    st = Status(lib.rsign_dbg_oz_convert(v.data_ptr(), e.data_ptr(), n, a.data_ptr(), b.data_ptr(),
+                                         _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return a, b
+
+
 def dbg_tile_order(dp, sym=0):
     """(bm, bn) arrays of the persistent GEMM's tile visiting order (host only)."""
     lib = load()
@@ -693,6 +712,18 @@ def dbg_fp64e_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def dbg_gemv_df_sym(M, x, stream=None):
+    """y = M x for a symmetric device FP64 M read from its upper triangle (double-float arithmetic)."""
+    torch = _torch()
+    lib = load()
+    dp = int(M.shape[0])
+    y = torch.empty(dp, dtype=torch.float64, device=M.device)
+    st = Status(lib.rsign_dbg_gemv_df_sym(M.data_ptr(), x.data_ptr(), dp, y.data_ptr(), _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return y
 
 
 def dbg_gemv_df(M, x, stream=None):

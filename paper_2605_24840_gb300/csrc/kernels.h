@@ -128,6 +128,11 @@ struct TcGemmArgs {
   const float* ns_diag;
 };
 
+// The two int64 -> FP64 conversions of the digit-plane epilogue on n device
+// values: a = the correctly rounded conversion moved by 2^e, b = the 128-bit
+// integer path (debug comparison).
+cudaError_t oz_convert_pair(const long long* v, const int* e, int n, double* a, double* b, cudaStream_t st);
+
 // Number of tiles of the schedule (needed to size `partials`: 4 per tile).
 int tc_num_tiles(int dp, int sym);
 // Host copy of the single-matrix tile order (128 x 256 tiles): (bm, bn) of
@@ -385,6 +390,14 @@ cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, int k_h
 // exponent of *kref) and y = M0 x (the result is scaled back by 2^-e).
 cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y, int dp,
                     cudaStream_t st, const double* kref = nullptr);
+// The same product for a symmetric M from its upper triangle only (half the
+// bytes): every 128 x 128 tile (I, J), I <= J, adds M_IJ x_J to y_I and, off
+// the diagonal, M_IJ^T x_I to y_J; per-tile partial sums land in slots of
+// `part` and are added in slot order (deterministic).  dp a multiple of 128;
+// part: gemv_df_sym_part_bytes(dp) bytes of device scratch.
+size_t gemv_df_sym_part_bytes(int dp);
+cudaError_t gemv_df_sym(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y,
+                        int dp, float2* part, cudaStream_t st);
 // *out = 1 / max_i |x_i| (1 when that is 0 or not finite), a device scalar
 // for split_f32's kref; bits: one device word of scratch.
 cudaError_t inv_maxabs(const double* x, size_t n, unsigned long long* bits, double* out, cudaStream_t st);
@@ -395,13 +408,15 @@ cudaError_t inv_maxabs(const double* x, size_t n, unsigned long long* bits, doub
 // product splitting and TwoSum accumulation per lane, lanes combined in
 // FP64): ~2^-46 relative per term, FP64-class, at HBM speed (GB300's FP64
 // pipe would bound FP64 GEMVs at ~0.6 T FMA/s).
-// A_hi/A_lo: split of A (split_f32); R_hi/R_lo: dp^2-float buffers that
-// receive the split of R.  work: 12 dp doubles; fwork: 12 dp floats.
+// A and R are symmetric: the products read their upper triangles only
+// (gemv_df_sym).  A_hi/A_lo: split of A (split_f32); R_hi/R_lo: dp^2-float
+// buffers that receive the split of R.  work: 12 dp doubles; fwork: 12 dp
+// floats; part: gemv_df_sym_part_bytes(dp) bytes.
 // out[0] = ||G||_2 estimate, out[1] = ||N||_2 estimate, out[2..4] = the 2 x 2
 // Rayleigh-Ritz projection of A on the last plane of the commutator steps.
 cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const double* R, float* R_hi,
                                  float* R_lo, int dp, int d, int iters, double* work, float* fwork,
-                                 double* out, cudaStream_t st);
+                                 float2* part, double* out, cudaStream_t st);
 // Scaling by power steps (Sec. 4.3: alpha close to 1/||H - sI||_2 enlarges the
 // scaled margin gamma): with rho_est = nrm[0] from power steps (a lower bound
 // of rho(A) converging from below), scal[3] = rho_est and scal[1] = alpha =

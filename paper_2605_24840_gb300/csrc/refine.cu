@@ -612,6 +612,205 @@ __global__ void gemv_df_kernel(const GemvDfArgs a) {
   else gemv_df_row<false>(J, r, a.dp, lane, kout);
 }
 
+// ---- the same products over the upper triangle of a symmetric M
+// Every 128 x 128 tile (I, J), I <= J, is read once and serves both halves:
+// y_I += M_IJ x_J (its row sums) and, off the diagonal, y_J += M_IJ^T x_I
+// (its column sums).  Each tile writes its partial sums, as double-float
+// (s, c) pairs, to a slot of its own: the row sums of tile (I, J) to slot J
+// of the rows of block I, the column sums to slot I of the rows of block J,
+// so every output row gets exactly one partial per slot K = 0 .. nb-1.  A
+// second pass adds the nb partials of a row in slot order (deterministic)
+// and writes y like gemv_df_kernel.  Half the matrix bytes of the row
+// kernel; the arithmetic per element is the same.
+constexpr int kSymTile = 128;
+
+// (s, c) += (s2, c2): TwoSum of the leading parts, the rounding error and
+// the compensations into c
+__device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(c2, err));
+}
+
+// tile (I, J) of the upper triangle from its linear index (row-major over I)
+__device__ __forceinline__ void sym_tile(int t, int nb, int& I, int& J) {
+  int r = 0;
+  while (t >= nb - r) {
+    t -= nb - r;
+    ++r;
+  }
+  I = r;
+  J = r + t;
+}
+
+// One CTA per (tile, job): 8 warps x 16 rows, each lane 4 columns (float4).
+// Per row the lane's 4-column partial goes to shared memory (reduced over
+// the 32 lanes after the loop); per column the lane accumulates over its
+// warp's 16 rows in registers (reduced over the 8 warps after the loop).
+// part: per job, NV vectors x nb slots x dp (s, c) pairs.
+template <bool TWO>
+__device__ __forceinline__ void gemv_df_sym_tile(const GemvDfJob& J_, int I, int Jt, int dp, float2* part) {
+  constexpr int NV = TWO ? 2 : 1;
+  // [vec][warp][row][lane] (+1 against bank conflicts), then [vec][warp][column]
+  extern __shared__ float2 sym_smem[];
+  float2 (*rowp)[8][16][33] = reinterpret_cast<float2 (*)[8][16][33]>(sym_smem);
+  float2 (*colp)[8][kSymTile] = reinterpret_cast<float2 (*)[8][kSymTile]>(sym_smem + NV * 8 * 16 * 33);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = I * kSymTile, c0 = Jt * kSymTile;
+  const bool diag = I == Jt;
+  // x_J over this lane's 4 columns (row sums); x_I per row comes by broadcast
+  const float4 xjh = reinterpret_cast<const float4*>(J_.xhi + c0)[lane];
+  const float4 xjl = reinterpret_cast<const float4*>(J_.xlo + c0)[lane];
+  float4 xbjh = make_float4(0.f, 0.f, 0.f, 0.f), xbjl = xbjh;
+  if (TWO) {
+    xbjh = reinterpret_cast<const float4*>(J_.xbhi + c0)[lane];
+    xbjl = reinterpret_cast<const float4*>(J_.xblo + c0)[lane];
+  }
+  float cs[NV][4], cc[NV][4];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cs[v][q] = cc[v][q] = 0.f;
+#pragma unroll
+  for (int rb = 0; rb < 16; rb += 4) {
+    float4 mh[4], ml[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t off = (size_t)(r0 + warp * 16 + rb + u) * dp + c0;
+      mh[u] = __ldcs(reinterpret_cast<const float4*>(J_.mhi + off) + lane);
+      ml[u] = __ldcs(reinterpret_cast<const float4*>(J_.mlo + off) + lane);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int rl = rb + u;
+      const int row = r0 + warp * 16 + rl;
+      // row sum over the lane's 4 columns
+      float s = 0.f, c = 0.f;
+      df_acc(s, c, mh[u].x, ml[u].x, xjh.x, xjl.x);
+      df_acc(s, c, mh[u].y, ml[u].y, xjh.y, xjl.y);
+      df_acc(s, c, mh[u].z, ml[u].z, xjh.z, xjl.z);
+      df_acc(s, c, mh[u].w, ml[u].w, xjh.w, xjl.w);
+      rowp[0][warp][rl][lane] = make_float2(s, c);
+      if (TWO) {
+        float sb = 0.f, cb = 0.f;
+        df_acc(sb, cb, mh[u].x, ml[u].x, xbjh.x, xbjl.x);
+        df_acc(sb, cb, mh[u].y, ml[u].y, xbjh.y, xbjl.y);
+        df_acc(sb, cb, mh[u].z, ml[u].z, xbjh.z, xbjl.z);
+        df_acc(sb, cb, mh[u].w, ml[u].w, xbjh.w, xbjl.w);
+        rowp[NV - 1][warp][rl][lane] = make_float2(sb, cb);
+      }
+      if (!diag) {
+        // column sums: M_IJ^T x_I over this warp's rows
+        const float xih = J_.xhi[row], xil = J_.xlo[row];
+        df_acc(cs[0][0], cc[0][0], mh[u].x, ml[u].x, xih, xil);
+        df_acc(cs[0][1], cc[0][1], mh[u].y, ml[u].y, xih, xil);
+        df_acc(cs[0][2], cc[0][2], mh[u].z, ml[u].z, xih, xil);
+        df_acc(cs[0][3], cc[0][3], mh[u].w, ml[u].w, xih, xil);
+        if (TWO) {
+          const float xbh = J_.xbhi[row], xbl = J_.xblo[row];
+          df_acc(cs[NV - 1][0], cc[NV - 1][0], mh[u].x, ml[u].x, xbh, xbl);
+          df_acc(cs[NV - 1][1], cc[NV - 1][1], mh[u].y, ml[u].y, xbh, xbl);
+          df_acc(cs[NV - 1][2], cc[NV - 1][2], mh[u].z, ml[u].z, xbh, xbl);
+          df_acc(cs[NV - 1][3], cc[NV - 1][3], mh[u].w, ml[u].w, xbh, xbl);
+        }
+      }
+    }
+  }
+  if (!diag) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) colp[v][warp][4 * lane + q] = make_float2(cs[v][q], cc[v][q]);
+  }
+  __syncthreads();
+  const int nb = dp / kSymTile;
+  if (threadIdx.x < kSymTile) {
+    // row t of block I: its 32 lane partials in lane order -> slot Jt
+    const int t = threadIdx.x, w = t >> 4, rl = t & 15;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float s = 0.f, c = 0.f;
+      for (int l = 0; l < 32; ++l) {
+        const float2 p = rowp[v][w][rl][l];
+        df_add(s, c, p.x, p.y);
+      }
+      part[((size_t)v * nb + Jt) * dp + r0 + t] = make_float2(s, c);
+    }
+  } else if (!diag) {
+    // column t of block Jt: its 8 warp partials in warp order -> slot I
+    const int t = threadIdx.x - kSymTile;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float s = 0.f, c = 0.f;
+      for (int w = 0; w < 8; ++w) {
+        const float2 p = colp[v][w][t];
+        df_add(s, c, p.x, p.y);
+      }
+      part[((size_t)v * nb + I) * dp + c0 + t] = make_float2(s, c);
+    }
+  }
+}
+
+// grid.x = tiles of the upper triangle, grid.y = job; 256 threads
+__global__ void __launch_bounds__(256) gemv_df_sym_kernel(const GemvDfArgs a, float2* part) {
+  const int nb = a.dp / kSymTile;
+  int I, Jt;
+  sym_tile(blockIdx.x, nb, I, Jt);
+  const GemvDfJob& J_ = a.job[blockIdx.y];
+  float2* pj = part + (size_t)blockIdx.y * 2 * nb * a.dp;  // room for two vectors per job
+  if (J_.xbhi != nullptr) gemv_df_sym_tile<true>(J_, I, Jt, a.dp, pj);
+  else gemv_df_sym_tile<false>(J_, I, Jt, a.dp, pj);
+}
+
+constexpr int kSymSmem = 2 * (8 * 16 * 33 + 8 * kSymTile) * (int)sizeof(float2);  // two vectors
+
+// y_i = the sum of its nb partials (double-float), then FP64; the outputs as
+// gemv_df_row writes them.  Four consecutive lanes per (job, row), each
+// adding a quarter of the slots in slot order; the quarters are combined in
+// a fixed pattern ((q0 + q1) + (q2 + q3)), so the result does not depend on
+// the launch.
+__global__ void gemv_df_sym_reduce_kernel(const GemvDfArgs a, const float2* part) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gi = gt >> 2, q = gt & 3;
+  const bool live = gi < a.n_jobs * a.dp;  // whole groups of four: the shuffles below stay in step
+  const int jb = live && gi >= a.dp ? 1 : 0;
+  const int r = live ? gi - jb * a.dp : 0;
+  const GemvDfJob& J = a.job[jb];
+  const int nb = a.dp / kSymTile;
+  const int k0 = (q * nb) / 4, k1 = ((q + 1) * nb) / 4;  // the quarters cover 0 .. nb-1
+  const float2* pj = part + (size_t)jb * 2 * nb * a.dp;
+  const bool two = J.xbhi != nullptr;
+  const int kout = live && a.kref != nullptr ? -ic_exponent(a.kref[0]) : 0;
+  for (int v = 0; v < 2; ++v) {
+    float s = 0.f, c = 0.f;
+    if (live && (v == 0 || two))
+      for (int k = k0; k < k1; ++k) {
+        const float2 p = pj[((size_t)v * nb + k) * a.dp + r];
+        df_add(s, c, p.x, p.y);
+      }
+    // (q0 + q1), (q2 + q3), then their sum, in lanes q = 0 and 2, then 0
+    float s1 = __shfl_down_sync(0xffffffffu, s, 1), c1 = __shfl_down_sync(0xffffffffu, c, 1);
+    if ((q & 1) == 0) df_add(s, c, s1, c1);
+    s1 = __shfl_down_sync(0xffffffffu, s, 2);
+    c1 = __shfl_down_sync(0xffffffffu, c, 2);
+    if (q == 0) df_add(s, c, s1, c1);
+    if (!live || q != 0 || (v == 1 && !two)) continue;
+    double t = (double)s + (double)c;
+    if (kout != 0) t = ldexp(t, kout);
+    double* y = v == 0 ? J.y : J.yb;
+    float* yh = v == 0 ? J.yhi : J.ybhi;
+    float* yl = v == 0 ? J.ylo : J.yblo;
+    y[r] = t;
+    if (yh != nullptr) {
+      const float h = __double2float_rn(t);
+      yh[r] = h;
+      yl[r] = __double2float_rn(t - (double)h);
+    }
+  }
+}
+
 // hi + lo = src 2^k (k = k_host, plus the exponent of *kref when given), by
 // integer operations (ic_split_f32): two float2 stores per pair of elements
 __global__ void split_f32_kernel(const double* __restrict__ src, size_t n, float* __restrict__ hi,
@@ -1071,6 +1270,30 @@ cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, con
   return cudaGetLastError();
 }
 
+size_t gemv_df_sym_part_bytes(int dp) { return (size_t)2 * 2 * (dp / kSymTile) * dp * sizeof(float2); }
+
+// One or two jobs of y = M x (symmetric M) over the upper triangle: the tile
+// pass and the slot-order reduction (two launches).
+cudaError_t gemv_df_sym_run(const GemvDfArgs& a, float2* part, cudaStream_t st) {
+  if (a.dp % kSymTile != 0 || a.n_jobs < 1 || a.n_jobs > 2 || part == nullptr) return cudaErrorInvalidValue;
+  static cudaError_t attr = cudaFuncSetAttribute(gemv_df_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kSymSmem);
+  if (attr != cudaSuccess) return attr;
+  const int nb = a.dp / kSymTile;
+  gemv_df_sym_kernel<<<dim3(nb * (nb + 1) / 2, a.n_jobs), 256, kSymSmem, st>>>(a, part);
+  gemv_df_sym_reduce_kernel<<<(4 * a.n_jobs * a.dp + 255) / 256, 256, 0, st>>>(a, part);
+  return cudaGetLastError();
+}
+
+cudaError_t gemv_df_sym(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y,
+                        int dp, float2* part, cudaStream_t st) {
+  GemvDfArgs a{};
+  a.n_jobs = 1;
+  a.dp = dp;
+  a.job[0] = GemvDfJob{M_hi, M_lo, x_hi, x_lo, nullptr, nullptr, y, nullptr, nullptr, nullptr, nullptr, nullptr};
+  return gemv_df_sym_run(a, part, st);
+}
+
 cudaError_t inv_maxabs(const double* x, size_t n, unsigned long long* bits, double* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
@@ -1088,7 +1311,7 @@ cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, int k, 
 
 cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const double* R, float* R_hi,
                                  float* R_lo, int dp, int d, int iters, double* work, float* fwork,
-                                 double* out, cudaStream_t st) {
+                                 float2* part, double* out, cudaStream_t st) {
   if (iters < 1) return cudaErrorInvalidValue;
   // FP64 vectors
   double* vb[2] = {work, work + dp};  // unit vectors of the commutator steps (alternating)
@@ -1114,7 +1337,6 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
   start_vec_f64_kernel<<<(dp + 255) / 256, 256, 0, st>>>(w, d, dp);
   normalize_split_kernel<<<1, 1024, 0, st>>>(w, dp, vb[0], vbh[0], vbl[0], out);
   normalize_split_kernel<<<1, 1024, 0, st>>>(w, dp, z, zh, zl, out + 1);
-  const int blocks2 = (2 * dp + 7) / 8;
   // ||R C v|| = ||C v|| for the (orthogonal to working accuracy) R, so the
   // steps run on the antisymmetric C itself: v <- C v / ||C v|| turns within
   // the dominant invariant plane (eigenvalues +-i mu) and ||C v|| -> mu =
@@ -1127,13 +1349,15 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
     p1.dp = dp;
     p1.job[0] = GemvDfJob{A_hi, A_lo, vbh[cur], vbl[cur], nullptr, nullptr, t1, t1h, t1l, nullptr, nullptr, nullptr};
     p1.job[1] = GemvDfJob{R_hi, R_lo, vbh[cur], vbl[cur], zh, zl, t2, t2h, t2l, t3, t3h, t3l};
-    gemv_df_kernel<<<blocks2, 256, 0, st>>>(p1);  // A v; R v, R z
+    cudaError_t e = gemv_df_sym_run(p1, part, st);  // A v; R v, R z
+    if (e != cudaSuccess) return e;
     GemvDfArgs p2{};
     p2.n_jobs = 2;
     p2.dp = dp;
     p2.job[0] = GemvDfJob{R_hi, R_lo, t1h, t1l, t3h, t3l, y1, nullptr, nullptr, y3, nullptr, nullptr};
     p2.job[1] = GemvDfJob{A_hi, A_lo, t2h, t2l, nullptr, nullptr, y2, nullptr, nullptr, nullptr, nullptr, nullptr};
-    gemv_df_kernel<<<blocks2, 256, 0, st>>>(p2);  // R A v, R R z; A R v
+    e = gemv_df_sym_run(p2, part, st);  // R A v, R R z; A R v
+    if (e != cudaSuccess) return e;
     // v <- C v / ||C v|| (C v = R A v - A R v), z <- N z / ||N z|| (N z = R R z - z)
     diff_normalize2_kernel<<<2, 1024, 0, st>>>(DiffNormJob{y1, y2, vb[nxt], vbh[nxt], vbl[nxt], out},
                                                DiffNormJob{y3, z, w3, zh, zl, out + 1}, dp);
@@ -1149,7 +1373,8 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
   p3.dp = dp;
   p3.job[0] = GemvDfJob{A_hi, A_lo, vbh[last], vbl[last], nullptr, nullptr, t4, nullptr, nullptr, nullptr, nullptr,
                         nullptr};
-  gemv_df_kernel<<<(dp + 7) / 8, 256, 0, st>>>(p3);
+  cudaError_t e = gemv_df_sym_run(p3, part, st);
+  if (e != cudaSuccess) return e;
   dot3_kernel<<<1, 1024, 0, st>>>(vb[prev], t1, vb[last], t1, vb[last], t4, dp, out + 2);
   // out[0] = ||C v_prev|| = 2 ||G v_prev|| (G = 1/2 R C): halve it
   scale_scalar_kernel<<<1, 1, 0, st>>>(out, 0.5);

@@ -655,6 +655,8 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   float *cfwork = nullptr, *A_hi = nullptr, *A_lo = nullptr, *R_hi = nullptr, *R_lo = nullptr;
   RS_TRY(mem.alloc((void**)&cwork, (size_t)12 * dp * 8));
   RS_TRY(mem.alloc((void**)&cfwork, (size_t)12 * dp * 4));
+  float2* cpart = nullptr;
+  RS_TRY(mem.alloc((void**)&cpart, gemv_df_sym_part_bytes(dp)));
   RS_TRY(mem.alloc((void**)&A_hi, dd * 4));
   RS_TRY(mem.alloc((void**)&A_lo, dd * 4));
   RS_TRY(mem.alloc((void**)&R_hi, dd * 4));
@@ -684,10 +686,10 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     if (sw >= 1) {
       // a-posteriori check of the current R (matrix free, FP64 GEMVs):
       // err ~ 1.5 kappa alpha ||G||_2 with kappa the gain of the last tangent solve
-      if (!c.ok(commutator_gain_norm(A_hi, A_lo, in.R64, R_hi, R_lo, dp, d, kCheckIters, cwork, cfwork, red + 9,
-                                     st)))
+      if (!c.ok(commutator_gain_norm(A_hi, A_lo, in.R64, R_hi, R_lo, dp, d, kCheckIters, cwork, cfwork, cpart,
+                                     red + 9, st)))
         return c.err;
-      c.launches += 3 * kCheckIters + 7;
+      c.launches += 5 * kCheckIters + 8;
       RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
       RS_TRY(cudaStreamSynchronize(st));
       const double g2 = std::ldexp(h_red[9], -kA);
@@ -1995,6 +1997,20 @@ rsign_status rsign_dbg_fp64e_plan(int32_t n_planes, int32_t beta, int32_t levels
   return RSIGN_OK;
 }
 
+rsign_status rsign_dbg_oz_convert(const int64_t* v, const int32_t* e, int64_t n, double* a, double* b,
+                                  void* stream) {
+  if (!v || !e || !a || !b || n < 1 || n > (int64_t)1 << 30) return RSIGN_ERR_ARG;
+  int sms = 0;
+  rsign_status ds = (rsign_status)check_device(&sms);
+  if (ds != RSIGN_OK) return ds;
+  cudaStream_t st = (cudaStream_t)stream;
+  rsign_status res = RSIGN_OK;
+  if (oz_convert_pair((const long long*)v, (const int*)e, (int)n, a, b, st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  cudaGetLastError();
+  return res;
+}
+
 int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t* bm, int32_t* bn) {
   if (dp < 256 || dp % 256 || dp > 16384) return -1;
   const int n = tc_num_tiles((int)dp, sym ? 1 : 0);
@@ -2045,6 +2061,32 @@ rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, 
   return res;
 }
 
+rsign_status rsign_dbg_gemv_df_sym(const double* M, const double* x, int64_t dp, double* y, void* stream) {
+  if (!M || !x || !y || dp < 256 || dp % 256 || dp > 16384) return RSIGN_ERR_ARG;
+  int sms = 0;
+  rsign_status ds = (rsign_status)check_device(&sms);
+  if (ds != RSIGN_OK) return ds;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf mem;
+  mem.st = st;
+  const size_t dd = (size_t)dp * dp;
+  float *mh = nullptr, *ml = nullptr, *xh = nullptr, *xl = nullptr;
+  float2* pt = nullptr;
+  rsign_status res = RSIGN_OK;
+  if (mem.alloc((void**)&mh, dd * 4) != cudaSuccess || mem.alloc((void**)&ml, dd * 4) != cudaSuccess ||
+      mem.alloc((void**)&xh, (size_t)dp * 4) != cudaSuccess || mem.alloc((void**)&xl, (size_t)dp * 4) != cudaSuccess ||
+      mem.alloc((void**)&pt, gemv_df_sym_part_bytes((int)dp)) != cudaSuccess ||
+      split_f32(M, dd, mh, ml, 0, nullptr, st) != cudaSuccess ||
+      split_f32(x, (size_t)dp, xh, xl, 0, nullptr, st) != cudaSuccess ||
+      gemv_df_sym(mh, ml, xh, xl, y, (int)dp, pt, st) != cudaSuccess)
+    res = RSIGN_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  mem.release();
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  cudaGetLastError();
+  return res;
+}
+
 rsign_status rsign_dbg_gemv_df(const double* M, const double* x, int64_t dp, double* y, void* stream) {
   if (!M || !x || !y || dp < 256 || dp % 256 || dp > 16384) return RSIGN_ERR_ARG;
   int sms = 0;
@@ -2081,6 +2123,7 @@ rsign_status rsign_dbg_commutator_check(const double* A, const double* R, int64_
   mem.st = st;
   const size_t dd = (size_t)dp * dp;
   float *ah = nullptr, *al = nullptr, *rh = nullptr, *rl = nullptr, *fw = nullptr;
+  float2* pt = nullptr;
   double *w = nullptr, *o = nullptr;
   rsign_status res = RSIGN_OK;
   if (mem.alloc((void**)&ah, dd * 4) != cudaSuccess || mem.alloc((void**)&al, dd * 4) != cudaSuccess ||
@@ -2088,7 +2131,8 @@ rsign_status rsign_dbg_commutator_check(const double* A, const double* R, int64_
       mem.alloc((void**)&fw, (size_t)12 * dp * 4) != cudaSuccess ||
       mem.alloc((void**)&w, (size_t)12 * dp * 8) != cudaSuccess || mem.alloc((void**)&o, 8 * 8) != cudaSuccess ||
       split_f32(A, dd, ah, al, 0, nullptr, st) != cudaSuccess ||
-      commutator_gain_norm(ah, al, R, rh, rl, (int)dp, (int)d, iters, w, fw, o, st) != cudaSuccess ||
+      mem.alloc((void**)&pt, gemv_df_sym_part_bytes((int)dp)) != cudaSuccess ||
+      commutator_gain_norm(ah, al, R, rh, rl, (int)dp, (int)d, iters, w, fw, pt, o, st) != cudaSuccess ||
       cudaMemcpyAsync(out, o, 5 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     res = RSIGN_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;

@@ -949,7 +949,22 @@ cudaError_t dispatch_grouped(const TcGemmArgs& a, const CUtensorMap& ma, const C
   }
 }
 
+// Both conversions of the digit-plane epilogue side by side (debug entry):
+// a[i] = i64_scaled(v[i], e[i]), b[i] = i128_scaled(v[i], e[i]).
+__global__ void oz_convert_kernel(const long long* v, const int* e, int n, double* a, double* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  a[i] = i64_scaled(v[i], e[i]);
+  b[i] = i128_scaled((__int128)v[i], e[i]);
+}
+
 }  // namespace
+
+cudaError_t oz_convert_pair(const long long* v, const int* e, int n, double* a, double* b, cudaStream_t st) {
+  if (n < 1) return cudaErrorInvalidValue;
+  oz_convert_kernel<<<(n + 255) / 256, 256, 0, st>>>(v, e, n, a, b);
+  return cudaGetLastError();
+}
 
 int tc_num_tiles(int dp, int sym) { return TileSched<256>(dp, sym).n; }
 

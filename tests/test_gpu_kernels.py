@@ -226,6 +226,32 @@ def test_gemv_df_is_fp64_accurate(dp, scale_spread):
     assert float(((y - ref).abs() - 2.0 ** -44 * scale).max()) <= 0.0
 
 
+@pytest.mark.parametrize("dp,scale_spread", [(256, 0), (768, 2), (1024, 8), (8192, 4)])
+def test_symmetric_gemv_df_reads_the_upper_triangle_only(dp, scale_spread):
+    # the check's symmetric form: the same bound as the row kernel, with every
+    # 128 x 128 tile below the diagonal tiles set to NaN (never read; the
+    # diagonal tiles are read whole)
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    g = torch.Generator(device="cuda").manual_seed(23 + dp)
+    M = torch.randn((dp, dp), generator=g, device="cuda", dtype=torch.float64)
+    M = 0.5 * (M + M.T)
+    if scale_spread:  # symmetric scaling D M D over 2^(+-spread)
+        e = torch.randint(-scale_spread, scale_spread + 1, (dp,), generator=g, device="cuda").double()
+        M = M * torch.pow(2.0, e)[:, None] * torch.pow(2.0, e)[None, :]
+    x = torch.randn(dp, generator=g, device="cuda", dtype=torch.float64)
+    ref = M @ x
+    scale = M.abs() @ x.abs()
+    Mu = M.clone()
+    blk = torch.arange(dp, device="cuda") // 128
+    Mu[blk[:, None] > blk[None, :]] = float("nan")
+    y = rs.dbg_gemv_df_sym(Mu, x)
+    assert bool(torch.isfinite(y).all())
+    assert float(((y - ref).abs() - 2.0 ** -44 * scale).max()) <= 0.0
+    y_row = rs.dbg_gemv_df(M, x)
+    assert float(((y - y_row).abs() - 2.0 ** -43 * scale).max()) <= 0.0
+
+
 @pytest.mark.parametrize("d,dp", [(512, 512), (700, 768), (1000, 1024)])
 def test_commutator_check_matches_fp64_power_steps(d, dp):
     # the matrix-free check against the same power steps in FP64 (torch), on a
@@ -310,3 +336,35 @@ def test_polish_products_same_bits_on_both_tile_widths(d):
     finally:
         rs.dbg_set_ozaki_tile(prev)
     assert torch.equal(outs[0], outs[1])
+
+
+def test_digit_sum_conversion_matches_128_bit_rounding_and_numpy():
+    # The digit-plane products turn each exact int64 level sum v into
+    # v 2^e in FP64 (round to nearest, ties to even).  The epilogue does it with
+    # one correctly rounded conversion and an exponent shift; the 128-bit
+    # integer path rounds the significand itself.  Both must give numpy's
+    # ldexp(float64(v), e) bit for bit: normal results, ties at 2^53 + 1 and
+    # beyond, the full int64 range, and exponents that underflow or overflow.
+    import numpy as np
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    rng = np.random.default_rng(11)
+    vals = []
+    for bits in range(64):
+        lo, hi = (0, 1) if bits == 0 else (1 << (bits - 1), (1 << bits) - 1)
+        vals.extend(int(x) for x in rng.integers(lo, hi, size=40, endpoint=True, dtype=np.uint64))
+    special = [0, 1, 2 ** 53, 2 ** 53 + 1, 2 ** 53 + 3, 2 ** 54 + 2, 2 ** 54 + 6, 2 ** 62 + 2 ** 9,
+               2 ** 62 + 2 ** 9 + 1, 2 ** 63 - 1, 2 ** 63 - 2 ** 10, 2 ** 63 - 2 ** 10 - 1]
+    vals = [v for v in vals if v < 2 ** 63] + special
+    vals = vals + [-v for v in vals] + [-(2 ** 63)]
+    v = np.array(vals, dtype=np.int64)
+    e = rng.integers(-80, 80, size=v.size).astype(np.int32)
+    e[::17] = -1100   # deep underflow: subnormal or zero
+    e[5::17] = -1040  # around the subnormal boundary
+    e[9::17] = 1000   # overflow for the larger v
+    a, b = rs.dbg_oz_convert(torch.from_numpy(v).cuda(), torch.from_numpy(e).cuda())
+    with np.errstate(over="ignore", under="ignore"):
+        ref = np.ldexp(v.astype(np.float64), e)
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert np.array_equal(a.view(np.int64), ref.view(np.int64))
+    assert np.array_equal(b.view(np.int64), ref.view(np.int64))
