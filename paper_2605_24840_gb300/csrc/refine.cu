@@ -487,6 +487,71 @@ __global__ void power_normalize_kernel(const float* __restrict__ w, int n, float
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
 }
 
+// All the power steps of a matrix of order dp <= kPowerFusedMax in one block
+// of 1024 threads: the matrix (<= 1 MB) stays in L2 between the steps and
+// the call costs one launch instead of two per step (the small matrices of a
+// batch run many such calls side by side, where launches, not bytes, bound
+// them).  Same start vector, one warp per row as gemv_f32_kernel, and the
+// same output: ||w|| / ||v0|| after a single step, else ||w|| of the last step
+// (v normalised).
+constexpr int kPowerFusedMax = 512;
+__global__ void __launch_bounds__(1024) power_fused_kernel(const float* __restrict__ M, int dp, int iters,
+                                                           double* out) {
+  __shared__ float4 v4[kPowerFusedMax / 4];
+  __shared__ float w[kPowerFusedMax];
+  __shared__ double red[32];
+  __shared__ float inv_sh;
+  float* v = reinterpret_cast<float*>(v4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n4 = dp >> 2;
+  float s0sq = 0.f;
+  for (int i = threadIdx.x; i < dp; i += blockDim.x) {
+    v[i] = 1.0f + (float)(i % 7) * 0.125f;
+    s0sq = fmaf(v[i], v[i], s0sq);
+  }
+  double t0 = warp_sum((double)s0sq);
+  if (lane == 0) red[warp] = t0;
+  __syncthreads();
+  double nv0 = 0.0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 32; ++q) nv0 += red[q];
+    nv0 = sqrt(nv0);
+  }
+  for (int it = 0; it < iters; ++it) {
+    for (int r = warp; r < dp; r += 32) {
+      const float4* m = reinterpret_cast<const float4*>(M + (size_t)r * dp);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      for (int q = lane; q < n4; q += 32) {
+        const float4 a = m[q], b = v4[q];
+        s0 = fmaf(a.x, b.x, s0);
+        s1 = fmaf(a.y, b.y, s1);
+        s2 = fmaf(a.z, b.z, s2);
+        s3 = fmaf(a.w, b.w, s3);
+      }
+      float s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) w[r] = s;
+    }
+    __syncthreads();
+    float sf = 0.f;
+    for (int i = threadIdx.x; i < dp; i += blockDim.x) sf = fmaf(w[i], w[i], sf);
+    const double t = warp_sum((double)sf);
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int q = 0; q < 32; ++q) tot += red[q];
+      const double nw = sqrt(tot);
+      inv_sh = nw > 0.0 ? (float)(1.0 / nw) : 0.0f;
+      if (it == iters - 1) *out = it == 0 ? nw / nv0 : nw;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < dp; i += blockDim.x) v[i] = w[i] * inv_sh;
+    __syncthreads();
+  }
+}
+
 // ---- double-float GEMVs (FP64-class products on the FP32 pipe)
 // One (matrix, vectors) job: y = M x and optionally y_b = M x_b from the same
 // pass over M's rows; M, x, x_b as hi + lo FP32 pairs; y in FP64 and, when
@@ -1250,8 +1315,15 @@ cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockm
   return cudaGetLastError();
 }
 
+int spectral_norm_launches(int dp, int iters) { return dp <= kPowerFusedMax ? 1 : 2 * iters; }
+
 cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
                               cudaStream_t st) {
+  if (iters < 1) return cudaErrorInvalidValue;
+  if (dp <= kPowerFusedMax) {
+    power_fused_kernel<<<1, 1024, 0, st>>>(M, dp, iters, out);
+    return cudaGetLastError();
+  }
   for (int it = 0; it < iters; ++it) {
     gemv_f32_kernel<<<(dp + 7) / 8, 256, 0, st>>>(M, dp, v, w, it == 0 ? 1 : 0);
     power_normalize_kernel<<<1, 1024, 0, st>>>(w, dp, v, out, it == 0 ? 1 : 0);

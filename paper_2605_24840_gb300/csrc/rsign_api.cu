@@ -766,7 +766,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     RS_TRY(cudaEventRecord(side.ev[0], st));
     RS_TRY(cudaStreamWaitEvent(side.s, side.ev[0], 0));
     if (!c.ok(spectral_norm_f32(Q32, dp, pv, pw, kPowerIters, red + 6, side.s))) return c.err;  // ||E_0||_2
-    c.launches += 2 * kPowerIters;
+    c.launches += spectral_norm_launches(dp, kPowerIters);
     // tangent recursion along the stored iterates.  The operand scale sigma
     // (fs[5], a power of two with |E_0| sigma <= 1) stays fixed along the
     // recursion: E grows by at most ~2.6 per step, well inside the FP16 range
@@ -792,7 +792,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     RS_TRY(cudaStreamWaitEvent(side.s, side.ev[1], 0));
     if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 7, side.s))) return c.err;
     RS_TRY(cudaEventRecord(side.ev[2], side.s));
-    c.launches += 2 * kPowerIters;
+    c.launches += spectral_norm_launches(dp, kPowerIters);
     if (!c.ok(add_correction(in.R64, E32, dp, d, part, st))) return c.err;
     if (!c.ok(sum_partials(part, 1024, red + 2, st))) return c.err;
     RS_TRY(polish());
@@ -963,7 +963,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         !c.ok(spectral_norm_f32(a32, dp, pv, pw, ps, ctl->scal + 4, st)) ||
         !c.ok(alpha_from_rho(ctl->scal + 4, 1.02, ctl->scal, 1, st)))
       return fail_cuda();
-    c.launches += 2 * ps + 2;
+    c.launches += spectral_norm_launches(dp, ps) + 2;
   }
   if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
