@@ -512,9 +512,9 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs& a, int i, int j
       }
       // Last group, eight elements at a time: every input of the eight is
       // loaded before the first of their stores.  The stores go to `out`,
-      // which the compiler cannot tell apart from the FP64 inputs, so a load
-      // placed after a store waits for it: one DRAM round trip per element
-      // instead of one per eight.
+      // which the compiler cannot tell apart from the FP64 inputs, so it
+      // would not move a later element's loads above an earlier store; here
+      // the eight loads are in flight together.
 #pragma unroll
       for (int o = 0; o < 16; o += 8) {
         const int jb = j0 + hh + o;
@@ -617,7 +617,7 @@ __device__ __forceinline__ void epilogue_oz_tmem(const TcGemmArgs& a, int i, int
   const double* b_full = with_diag ? a.b_full + moff : nullptr;
   float accf = 0.0f;
   // eight elements at a time, every input loaded before the first of their
-  // stores (a load after a store to `out` would wait for it)
+  // stores (the compiler would not move a load above a store to `out`)
 #pragma unroll
   for (int o = 0; o < 32; o += 8) {
     const int jb = j0 + o;
