@@ -410,12 +410,14 @@ cudaError_t inv_maxabs(const double* x, size_t n, unsigned long long* bits, doub
 // product splitting and TwoSum accumulation per lane, lanes combined in
 // FP64): ~2^-46 relative per term, FP64-class, at HBM speed (GB300's FP64
 // pipe would bound FP64 GEMVs at ~0.6 T FMA/s).
-// A and R are symmetric: the products read their upper triangles only
-// (gemv_df_sym).  A_hi/A_lo: split of A (split_f32); R_hi/R_lo: dp^2-float
+// A and R are symmetric: above order 1024 the products read their upper
+// triangles only (gemv_df_sym), up to it whole rows (gemv_df, one launch per
+// product); commutator_check_launches gives the kernels it launches.  A_hi/A_lo: split of A (split_f32); R_hi/R_lo: dp^2-float
 // buffers that receive the split of R.  work: 12 dp doubles; fwork: 12 dp
 // floats; part: gemv_df_sym_part_bytes(dp) bytes.
 // out[0] = ||G||_2 estimate, out[1] = ||N||_2 estimate, out[2..4] = the 2 x 2
 // Rayleigh-Ritz projection of A on the last plane of the commutator steps.
+int commutator_check_launches(int dp, int iters);
 cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const double* R, float* R_hi,
                                  float* R_lo, int dp, int d, int iters, double* work, float* fwork,
                                  float2* part, double* out, cudaStream_t st);
@@ -434,6 +436,10 @@ cudaError_t to_f16(const double* src, size_t n, void* dst, cudaStream_t st);
 // dst (FP16) = hi + lo of a BF16 pair of planes (plane stride n; hi alone when
 // pair == 0), summed in FP32 and rounded once; n even.
 cudaError_t bf16_pair_to_f16(const void* src, size_t n, int pair, void* dst, cudaStream_t st);
+// The same for `count` matrices of n elements (src[i] -> dst[i]) in
+// ceil(count / 64) launches.
+cudaError_t bf16_pairs_to_f16(const void* const* src, void* const* dst, int count, size_t n, int pair,
+                              cudaStream_t st);
 // dst (FP16) = sigma E + 3/4 Q / sigma, Q = (sigma E)^2: sigma W, W = E + 3/4 E^2,
 // the weight of the quintic polish step R <- R + 1/2 R W; n a multiple of 4.
 cudaError_t polish_weight(const float* E, const float* Q, size_t n, const float* sigma, void* dst, cudaStream_t st);

@@ -388,6 +388,30 @@ __global__ void bf16_pair_to_f16_kernel(const __nv_bfloat16* __restrict__ src, s
   }
 }
 
+// The same conversion for up to kConvMax matrices in one launch (blockIdx.y
+// picks the matrix): the refinement converts every stored BF16 iterate and
+// residual at once.
+constexpr int kConvMax = 64;
+struct ConvList {
+  const __nv_bfloat16* src[kConvMax];
+  __half* dst[kConvMax];
+};
+__global__ void bf16_pairs_to_f16_kernel(const ConvList L, size_t n, int pair) {
+  const size_t n2 = n >> 1;
+  const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(L.src[blockIdx.y]);
+  const __nv_bfloat162* l2 = reinterpret_cast<const __nv_bfloat162*>(L.src[blockIdx.y] + n);
+  __half2* d2 = reinterpret_cast<__half2*>(L.dst[blockIdx.y]);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    float2 v = __bfloat1622float2(h2[i]);
+    if (pair) {
+      const float2 w = __bfloat1622float2(l2[i]);
+      v.x += w.x;
+      v.y += w.y;
+    }
+    d2[i] = __floats2half2_rn(v.x, v.y);
+  }
+}
+
 // dst = FP16(src) by way of the nearest float (integer rounding, then the
 // float -> half conversion): two elements per thread and iteration
 __global__ void to_f16_kernel(const double* __restrict__ src, size_t n, __half* __restrict__ dst) {
@@ -1381,6 +1405,23 @@ cudaError_t split_f32(const double* src, size_t n, float* hi, float* lo, int k, 
   return cudaGetLastError();
 }
 
+// Above this order the check's products read the upper triangles only (half
+// the bytes, two launches per product); up to it the row kernel (one launch:
+// small matrices are bound by launches, not bytes).
+constexpr int kCheckSymMin = 1024;
+
+// one double-float product pass of the check, by the form its order takes
+static cudaError_t check_pass(const GemvDfArgs& a, float2* part, cudaStream_t st) {
+  if (a.dp > kCheckSymMin) return gemv_df_sym_run(a, part, st);
+  gemv_df_kernel<<<(a.n_jobs * a.dp + 7) / 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+int commutator_check_launches(int dp, int iters) {
+  const int per_pass = dp > kCheckSymMin ? 2 : 1;
+  return 4 + iters * (2 * per_pass + 1) + per_pass + 2;
+}
+
 cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const double* R, float* R_hi,
                                  float* R_lo, int dp, int d, int iters, double* work, float* fwork,
                                  float2* part, double* out, cudaStream_t st) {
@@ -1421,14 +1462,14 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
     p1.dp = dp;
     p1.job[0] = GemvDfJob{A_hi, A_lo, vbh[cur], vbl[cur], nullptr, nullptr, t1, t1h, t1l, nullptr, nullptr, nullptr};
     p1.job[1] = GemvDfJob{R_hi, R_lo, vbh[cur], vbl[cur], zh, zl, t2, t2h, t2l, t3, t3h, t3l};
-    cudaError_t e = gemv_df_sym_run(p1, part, st);  // A v; R v, R z
+    cudaError_t e = check_pass(p1, part, st);  // A v; R v, R z
     if (e != cudaSuccess) return e;
     GemvDfArgs p2{};
     p2.n_jobs = 2;
     p2.dp = dp;
     p2.job[0] = GemvDfJob{R_hi, R_lo, t1h, t1l, t3h, t3l, y1, nullptr, nullptr, y3, nullptr, nullptr};
     p2.job[1] = GemvDfJob{A_hi, A_lo, t2h, t2l, nullptr, nullptr, y2, nullptr, nullptr, nullptr, nullptr, nullptr};
-    e = gemv_df_sym_run(p2, part, st);  // R A v, R R z; A R v
+    e = check_pass(p2, part, st);  // R A v, R R z; A R v
     if (e != cudaSuccess) return e;
     // v <- C v / ||C v|| (C v = R A v - A R v), z <- N z / ||N z|| (N z = R R z - z)
     diff_normalize2_kernel<<<2, 1024, 0, st>>>(DiffNormJob{y1, y2, vb[nxt], vbh[nxt], vbl[nxt], out},
@@ -1445,7 +1486,7 @@ cudaError_t commutator_gain_norm(const float* A_hi, const float* A_lo, const dou
   p3.dp = dp;
   p3.job[0] = GemvDfJob{A_hi, A_lo, vbh[last], vbl[last], nullptr, nullptr, t4, nullptr, nullptr, nullptr, nullptr,
                         nullptr};
-  cudaError_t e = gemv_df_sym_run(p3, part, st);
+  cudaError_t e = check_pass(p3, part, st);
   if (e != cudaSuccess) return e;
   dot3_kernel<<<1, 1024, 0, st>>>(vb[prev], t1, vb[last], t1, vb[last], t4, dp, out + 2);
   // out[0] = ||C v_prev|| = 2 ||G v_prev|| (G = 1/2 R C): halve it
@@ -1462,6 +1503,22 @@ cudaError_t to_f16(const double* src, size_t n, void* dst, cudaStream_t st) {
 cudaError_t bf16_pair_to_f16(const void* src, size_t n, int pair, void* dst, cudaStream_t st) {
   if (n & 1) return cudaErrorInvalidValue;
   bf16_pair_to_f16_kernel<<<grid_for(n / 2), 256, 0, st>>>((const __nv_bfloat16*)src, n, pair, (__half*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t bf16_pairs_to_f16(const void* const* src, void* const* dst, int count, size_t n, int pair,
+                              cudaStream_t st) {
+  if (n & 1) return cudaErrorInvalidValue;
+  for (int b = 0; b < count; b += kConvMax) {
+    ConvList L{};
+    const int m = std::min(kConvMax, count - b);
+    for (int q = 0; q < m; ++q) {
+      L.src[q] = (const __nv_bfloat16*)src[b + q];
+      L.dst[q] = (__half*)dst[b + q];
+    }
+    const int gx = std::max(1, grid_for(n / 2) / std::max(1, m / 4));
+    bf16_pairs_to_f16_kernel<<<dim3(gx, m), 256, 0, st>>>(L, n, pair);
+  }
   return cudaGetLastError();
 }
 

@@ -151,6 +151,12 @@ int check_device(int* num_sms) {
 namespace {
 
 constexpr int kChunk = 8;  // NS steps enqueued between host checks of the stop flag
+// Low-precision stage: the first chunk reaches three steps past m_min (the
+// step from which the floor tests apply; the stop follows within a step or
+// two when the margin is known), later chunks are shorter, so that fewer
+// launches are enqueued past the device-side stop (they return at once, but
+// each still costs a launch).
+constexpr int kChunkLate = 4;
 
 // Control block kept in device memory (one allocation, read back with one copy).
 struct Ctl {
@@ -670,16 +676,24 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
   // (8-bit significands) stopped contracting once the margin fell to ~2e-4
   // of ||H||; its relative error there is ~u / (scaled margin).
   std::vector<void*> X_t(in.X, in.X + in.M), Et_t(in.Et, in.Et + in.M);
-  if (in.fmt == 1) {
+  if (in.fmt == 1 && in.M_tangent > 0) {
+    std::vector<const void*> src;
+    std::vector<void*> dst;
     for (int m = 0; m < in.M_tangent; ++m) {
       void *xc = nullptr, *ec = nullptr;
       RS_TRY(mem.alloc(&xc, dd * 2));
       RS_TRY(mem.alloc(&ec, dd * 2));
-      RS_TRY(c.ok(bf16_pair_to_f16(in.X[m], dd, in.pairs ? 1 : 0, xc, st)) ? cudaSuccess : c.err);
-      RS_TRY(c.ok(bf16_pair_to_f16(in.Et[m], dd, in.pairs ? 1 : 0, ec, st)) ? cudaSuccess : c.err);
+      src.push_back(in.X[m]);
+      dst.push_back(xc);
+      src.push_back(in.Et[m]);
+      dst.push_back(ec);
       X_t[m] = xc;
       Et_t[m] = ec;
     }
+    // all of them in one launch (64 matrices per launch)
+    RS_TRY(c.ok(bf16_pairs_to_f16(src.data(), dst.data(), (int)src.size(), dd, in.pairs ? 1 : 0, st)) ? cudaSuccess
+                                                                                                    : c.err);
+    c.launches += ((int)src.size() + 63) / 64 - 1;  // c.ok counted one
   }
   double kappa = NAN;
   for (int sw = 0; sw <= in.max_sweeps; ++sw) {
@@ -689,7 +703,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
       if (!c.ok(commutator_gain_norm(A_hi, A_lo, in.R64, R_hi, R_lo, dp, d, kCheckIters, cwork, cfwork, cpart,
                                      red + 9, st)))
         return c.err;
-      c.launches += 5 * kCheckIters + 8;
+      c.launches += commutator_check_launches(dp, kCheckIters) - 1;  // c.ok counted one
       RS_TRY(cudaMemcpyAsync(h_red, red, sizeof(h_red), cudaMemcpyDeviceToHost, st));
       RS_TRY(cudaStreamSynchronize(st));
       const double g2 = std::ldexp(h_red[9], -kA);
@@ -766,7 +780,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     RS_TRY(cudaEventRecord(side.ev[0], st));
     RS_TRY(cudaStreamWaitEvent(side.s, side.ev[0], 0));
     if (!c.ok(spectral_norm_f32(Q32, dp, pv, pw, kPowerIters, red + 6, side.s))) return c.err;  // ||E_0||_2
-    c.launches += spectral_norm_launches(dp, kPowerIters);
+    c.launches += spectral_norm_launches(dp, kPowerIters) - 1;
     // tangent recursion along the stored iterates.  The operand scale sigma
     // (fs[5], a power of two with |E_0| sigma <= 1) stays fixed along the
     // recursion: E grows by at most ~2.6 per step, well inside the FP16 range
@@ -792,7 +806,7 @@ cudaError_t refine_sweeps(Ctx& c, DevBuf& mem, const RefineIn& in, Ctl* ctl, Ref
     RS_TRY(cudaStreamWaitEvent(side.s, side.ev[1], 0));
     if (!c.ok(spectral_norm_f32(E32, dp, pv, pw, kPowerIters, red + 7, side.s))) return c.err;
     RS_TRY(cudaEventRecord(side.ev[2], side.s));
-    c.launches += spectral_norm_launches(dp, kPowerIters);
+    c.launches += spectral_norm_launches(dp, kPowerIters) - 1;
     if (!c.ok(add_correction(in.R64, E32, dp, d, part, st))) return c.err;
     if (!c.ok(sum_partials(part, 1024, red + 2, st))) return c.err;
     RS_TRY(polish());
@@ -963,7 +977,7 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
         !c.ok(spectral_norm_f32(a32, dp, pv, pw, ps, ctl->scal + 4, st)) ||
         !c.ok(alpha_from_rho(ctl->scal + 4, 1.02, ctl->scal, 1, st)))
       return fail_cuda();
-    c.launches += spectral_norm_launches(dp, ps) + 2;
+    c.launches += spectral_norm_launches(dp, ps) - 1;  // c.ok counted one per helper
   }
   if (cudaMemcpyAsync(&ctl_h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -1103,7 +1117,8 @@ rsign_status reflector_impl(const double* H, int64_t d64, int32_t k, double s, d
     int m = 0;
     bool stopped = false;
     while (m <= opt.max_steps && !stopped) {
-      const int m_end = std::min(m + kChunk, opt.max_steps + 1);
+      const int chunk = m == 0 ? std::max(kChunk, m_min + 3) : kChunkLate;
+      const int m_end = std::min(m + chunk, opt.max_steps + 1);
       for (int mm = m; mm < m_end; ++mm) {
         void* xm = slot_x(mm);
         void* em = slot_e(mm);
