@@ -277,6 +277,19 @@ rsign_status rsign_dbg_gemv_df(const double* M, const double* x, int64_t dp, dou
 rsign_status rsign_dbg_gemv_df_sym(const double* M, const double* x, int64_t dp, double* y, void* stream);
 
 /*
+ * The power-step estimate of ||M||_2 that the alpha rule and the refinement's
+ * norms use: M (device FP64, symmetric, dp x dp, dp a multiple of 256) is
+ * rounded to FP32, `iters` power steps from the fixed start vector
+ * v_i = 1 + (i mod 7)/8 give *out (host double): ||M v|| / ||v|| after one
+ * step, else ||M v|| of the last step with v normalised.  Up to order 512 the
+ * steps run in one launch; per_step != 0 forces one GEMV and one
+ * normalisation launch per step (the same arithmetic, so the same bits).
+ * Blocking.  RSIGN_ERR_ARG for bad sizes or iters outside 1 .. 1000.
+ */
+rsign_status rsign_dbg_spectral_norm(const double* M, int64_t dp, int32_t iters, int32_t per_step, double* out,
+                                     void* stream);
+
+/*
  * The matrix-free check of the refinement on device FP64 A, R (dp x dp, dp a
  * multiple of 256, logical order d): `iters` power steps on C = R A - A R and
  * on N = R^2 - I from the check's fixed start vector.  out (host, 5 doubles):

@@ -218,6 +218,8 @@ def load():
     lib.rsign_dbg_fp64e_gemm.restype = ctypes.c_int
     lib.rsign_dbg_gemv_df.argtypes = [vp, vp, i64, vp, vp]
     lib.rsign_dbg_gemv_df.restype = ctypes.c_int
+    lib.rsign_dbg_spectral_norm.argtypes = [vp, i64, i32, i32, ctypes.POINTER(ctypes.c_double), vp]
+    lib.rsign_dbg_spectral_norm.restype = ctypes.c_int
     lib.rsign_dbg_gemv_df_sym.argtypes = [vp, vp, i64, vp, vp]
     lib.rsign_dbg_gemv_df_sym.restype = ctypes.c_int
     lib.rsign_dbg_oz_convert.argtypes = [vp, vp, i64, vp, vp, vp]
@@ -712,6 +714,17 @@ def dbg_fp64e_gemm(A, B, d_real=None, sym=0, out=None, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return out
+
+
+def dbg_spectral_norm(M, iters, per_step=False, stream=None):
+    """Power-step estimate of ||M||_2 (M symmetric CUDA float64), as the alpha rule computes it."""
+    lib = load()
+    out = ctypes.c_double(0.0)
+    st = Status(lib.rsign_dbg_spectral_norm(M.data_ptr(), int(M.shape[0]), int(iters), int(bool(per_step)),
+                                            ctypes.byref(out), _stream_ptr(stream, True)))
+    if st != Status.OK:
+        raise RsignError(st)
+    return out.value
 
 
 def dbg_gemv_df_sym(M, x, stream=None):

@@ -375,10 +375,12 @@ cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockm
 // Largest |eigenvalue| of a symmetric FP32 dp x dp matrix by `iters` power
 // steps (a lower bound that converges from below) -> *out (device double).
 // v, w: dp-float work vectors (unused for dp <= 512, where all the steps run
-// in one launch).  spectral_norm_launches: the kernels it launches.
+// in one launch; per_step forces one GEMV and one normalisation launch per
+// step at any order, the same arithmetic).  spectral_norm_launches: the
+// kernels it launches.
 int spectral_norm_launches(int dp, int iters);
 cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
-                              cudaStream_t st);
+                              cudaStream_t st, bool per_step = false);
 // hi + lo = x 2^k to 2^-47 relative (lo nullable), by integer operations
 // (GB300's FP64 conversions run at the FP64 rate): the operand form of the
 // double-float GEMVs below.  k = k_host plus, when kref is given, the

@@ -1342,9 +1342,9 @@ cudaError_t ident_minus(const double* Y, int dp, int d, float* Et, float* blockm
 int spectral_norm_launches(int dp, int iters) { return dp <= kPowerFusedMax ? 1 : 2 * iters; }
 
 cudaError_t spectral_norm_f32(const float* M, int dp, float* v, float* w, int iters, double* out,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool per_step) {
   if (iters < 1) return cudaErrorInvalidValue;
-  if (dp <= kPowerFusedMax) {
+  if (dp <= kPowerFusedMax && !per_step) {
     power_fused_kernel<<<1, 1024, 0, st>>>(M, dp, iters, out);
     return cudaGetLastError();
   }

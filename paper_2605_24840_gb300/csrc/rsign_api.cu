@@ -2076,6 +2076,32 @@ rsign_status rsign_dbg_fp64e_gemm(const double* A, const double* B, int64_t dp, 
   return res;
 }
 
+rsign_status rsign_dbg_spectral_norm(const double* M, int64_t dp, int32_t iters, int32_t per_step, double* out,
+                                     void* stream) {
+  if (!M || !out || dp < 256 || dp % 256 || dp > 16384 || iters < 1 || iters > 1000) return RSIGN_ERR_ARG;
+  int sms = 0;
+  rsign_status ds = (rsign_status)check_device(&sms);
+  if (ds != RSIGN_OK) return ds;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf mem;
+  mem.st = st;
+  const size_t dd = (size_t)dp * dp;
+  float *m32 = nullptr, *v = nullptr, *w = nullptr;
+  double* o = nullptr;
+  rsign_status res = RSIGN_OK;
+  if (mem.alloc((void**)&m32, dd * 4) != cudaSuccess || mem.alloc((void**)&v, (size_t)dp * 4) != cudaSuccess ||
+      mem.alloc((void**)&w, (size_t)dp * 4) != cudaSuccess || mem.alloc((void**)&o, 8) != cudaSuccess ||
+      split_f32(M, dd, m32, nullptr, 0, nullptr, st) != cudaSuccess ||
+      spectral_norm_f32(m32, (int)dp, v, w, iters, o, st, per_step != 0) != cudaSuccess ||
+      cudaMemcpyAsync(out, o, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    res = RSIGN_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  mem.release();
+  if (cudaStreamSynchronize(st) != cudaSuccess) res = RSIGN_ERR_CUDA;
+  cudaGetLastError();
+  return res;
+}
+
 rsign_status rsign_dbg_gemv_df_sym(const double* M, const double* x, int64_t dp, double* y, void* stream) {
   if (!M || !x || !y || dp < 256 || dp % 256 || dp > 16384) return RSIGN_ERR_ARG;
   int sms = 0;

@@ -368,3 +368,25 @@ def test_digit_sum_conversion_matches_128_bit_rounding_and_numpy():
     a, b = a.cpu().numpy(), b.cpu().numpy()
     assert np.array_equal(a.view(np.int64), ref.view(np.int64))
     assert np.array_equal(b.view(np.int64), ref.view(np.int64))
+
+
+@pytest.mark.parametrize("dp", [256, 512, 768])
+def test_power_steps_in_one_launch_give_the_per_step_bits(dp):
+    # up to order 512 the power steps of the alpha rule and of the
+    # refinement's norms run in one launch: the same arithmetic in the same
+    # order as one GEMV and one normalisation launch per step, so the same
+    # bits; above 512 both settings take the per-step path.  The estimate
+    # itself approaches ||M||_2 from below.
+    torch = cuda_or_skip()
+    rs = lib_or_fail()
+    g = torch.Generator(device="cuda").manual_seed(5 + dp)
+    Q, _ = torch.linalg.qr(torch.randn((dp, dp), generator=g, device="cuda", dtype=torch.float64))
+    lam = torch.linspace(-0.5, 1.0, dp, device="cuda", dtype=torch.float64)
+    M = (Q * lam) @ Q.T
+    M = 0.5 * (M + M.T)
+    for iters in (1, 2, 20):
+        a = rs.dbg_spectral_norm(M, iters)
+        b = rs.dbg_spectral_norm(M, iters, per_step=True)
+        assert a == b, (iters, a, b)
+    est = rs.dbg_spectral_norm(M, 200)
+    assert 0.98 <= est <= 1.0 + 1e-5, est
