@@ -239,6 +239,15 @@ rsign_status rsign_dbg_oz_convert(const int64_t* v, const int32_t* e, int64_t n,
                                   void* stream);
 
 /*
+ * The tiles of the check's symmetric double-float product (host computation,
+ * no GPU): block t of its launch handles the 128 x 128 tile (I[t], J[t]) of
+ * the upper triangle, I <= J; its row sums fill slot J of block I's rows and,
+ * off the diagonal, its column sums slot I of block J's rows.  With I == NULL
+ * returns the tile count; otherwise fills I/J and returns it; -1 for a bad dp.
+ */
+int32_t rsign_dbg_sym_gemv_tiles(int64_t dp, int32_t* I, int32_t* J);
+
+/*
  * The order in which the persistent tcgen05 GEMM visits the 128 x 256 tiles of
  * one dp x dp product (host computation, no GPU): entry t is the (bm, bn) of
  * schedule unit t; sym selects the upper triangle.  With bm == NULL returns

@@ -218,6 +218,8 @@ def load():
     lib.rsign_dbg_fp64e_gemm.restype = ctypes.c_int
     lib.rsign_dbg_gemv_df.argtypes = [vp, vp, i64, vp, vp]
     lib.rsign_dbg_gemv_df.restype = ctypes.c_int
+    lib.rsign_dbg_sym_gemv_tiles.argtypes = [i64, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.rsign_dbg_sym_gemv_tiles.restype = i32
     lib.rsign_dbg_spectral_norm.argtypes = [vp, i64, i32, i32, ctypes.POINTER(ctypes.c_double), vp]
     lib.rsign_dbg_spectral_norm.restype = ctypes.c_int
     lib.rsign_dbg_gemv_df_sym.argtypes = [vp, vp, i64, vp, vp]
@@ -688,6 +690,18 @@ def dbg_oz_convert(v, e, stream=None):
     if st != Status.OK:
         raise RsignError(st)
     return a, b
+
+
+def dbg_sym_gemv_tiles(dp):
+    """(I, J) arrays: the upper-triangle tile handled by each block of the check's symmetric GEMV (host only)."""
+    lib = load()
+    n = lib.rsign_dbg_sym_gemv_tiles(int(dp), None, None)
+    if n < 0:
+        raise RsignError(Status.ERR_ARG)
+    I = (ctypes.c_int32 * n)()
+    J = (ctypes.c_int32 * n)()
+    m = lib.rsign_dbg_sym_gemv_tiles(int(dp), I, J)
+    return np.array(I[:m]), np.array(J[:m])
 
 
 def dbg_tile_order(dp, sym=0):

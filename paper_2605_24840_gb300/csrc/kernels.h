@@ -400,6 +400,9 @@ cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, con
 // `part` and are added in slot order (deterministic).  dp a multiple of 128;
 // part: gemv_df_sym_part_bytes(dp) bytes of device scratch.
 size_t gemv_df_sym_part_bytes(int dp);
+// Host copy of the tile order of gemv_df_sym: block t of the launch handles
+// tile (I[t], J[t]); returns the tile count (fills I/J when both are given).
+int gemv_df_sym_tiles(int dp, int* I, int* J);
 cudaError_t gemv_df_sym(const float* M_hi, const float* M_lo, const float* x_hi, const float* x_lo, double* y,
                         int dp, float2* part, cudaStream_t st);
 // *out = 1 / max_i |x_i| (1 when that is 0 or not finite), a device scalar

@@ -724,7 +724,7 @@ __device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
 }
 
 // tile (I, J) of the upper triangle from its linear index (row-major over I)
-__device__ __forceinline__ void sym_tile(int t, int nb, int& I, int& J) {
+__host__ __device__ __forceinline__ void sym_tile(int t, int nb, int& I, int& J) {
   int r = 0;
   while (t >= nb - r) {
     t -= nb - r;
@@ -1364,6 +1364,13 @@ cudaError_t gemv_df(const float* M_hi, const float* M_lo, const float* x_hi, con
   a.job[0] = GemvDfJob{M_hi, M_lo, x_hi, x_lo, nullptr, nullptr, y, nullptr, nullptr, nullptr, nullptr, nullptr};
   gemv_df_kernel<<<(dp + 7) / 8, 256, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+int gemv_df_sym_tiles(int dp, int* I, int* J) {
+  const int nb = dp / kSymTile, n = nb * (nb + 1) / 2;
+  if (I != nullptr && J != nullptr)
+    for (int t = 0; t < n; ++t) sym_tile(t, nb, I[t], J[t]);
+  return n;
 }
 
 size_t gemv_df_sym_part_bytes(int dp) { return (size_t)2 * 2 * (dp / kSymTile) * dp * sizeof(float2); }

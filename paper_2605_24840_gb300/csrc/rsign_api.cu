@@ -2026,6 +2026,11 @@ rsign_status rsign_dbg_oz_convert(const int64_t* v, const int32_t* e, int64_t n,
   return res;
 }
 
+int32_t rsign_dbg_sym_gemv_tiles(int64_t dp, int32_t* I, int32_t* J) {
+  if (dp < 256 || dp % 256 || dp > 16384) return -1;
+  return gemv_df_sym_tiles((int)dp, I, J);
+}
+
 int32_t rsign_dbg_tile_order(int64_t dp, int32_t sym, int32_t* bm, int32_t* bn) {
   if (dp < 256 || dp % 256 || dp > 16384) return -1;
   const int n = tc_num_tiles((int)dp, sym ? 1 : 0);

@@ -156,6 +156,27 @@ def test_tile_order_is_a_permutation_of_the_needed_tiles(rs, dp, sym):
     assert len({c for _, c in head}) <= 16 and len({r for r, _ in head}) <= 40
 
 
+@pytest.mark.parametrize("dp", [256, 768, 1024, 8192, 16384])
+def test_symmetric_check_tiles_fill_every_slot_once(rs, dp):
+    # the check's symmetric GEMV: block t handles upper-triangle tile (I, J);
+    # its row sums fill slot J of block I's rows and, off the diagonal, its
+    # column sums slot I of block J's rows.  Every (block, slot) pair must be
+    # written exactly once, so that the slot-order sum of a row sees each
+    # 128-column block of the matrix once (host computation, no GPU)
+    I, J = rs.dbg_sym_gemv_tiles(dp)
+    nb = dp // 128
+    assert len(I) == nb * (nb + 1) // 2
+    assert all(0 <= i <= j < nb for i, j in zip(I.tolist(), J.tolist()))
+    writes = {}
+    for i, j in zip(I.tolist(), J.tolist()):
+        writes[(i, j)] = writes.get((i, j), 0) + 1      # rows of block i, slot j
+        if i != j:
+            writes[(j, i)] = writes.get((j, i), 0) + 1  # rows of block j, slot i
+    assert writes == {(a, b): 1 for a in range(nb) for b in range(nb)}
+    with pytest.raises(Exception):
+        rs.dbg_sym_gemv_tiles(300)
+
+
 @pytest.mark.parametrize("l0,u0", [(1e-4, 1.0), (3e-3, 1.0), (1e-2, 1.04), (0.3, 1.0), (0.9, 1.04), (2.0, 1.0),
                                    (2.0, 1.04)])
 def test_scaled_step_coefficients_match_the_oracle(rs, oracle_mod, l0, u0):
